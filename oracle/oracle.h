@@ -1,0 +1,108 @@
+/*
+ * oracle.h -- C ABI of the CPU oracle (test infrastructure only).
+ *
+ * The oracle is a plain, slow, single-threaded restatement of the method of
+ * "High-Quality Shared-Memory Graph Partitioning" (Akhremtsev, Sanders, Schulz): size-constrained
+ * label propagation (Section III-A "Clustering", Section IV-A), contraction (Section III-A,
+ * Section IV-A "Parallel Contraction"), initial partitioning by recursive bisection (Section III-B),
+ * projection and label-propagation refinement (Section III-C, Section IV-C), with the deterministic
+ * readings of the points the paper leaves open. It shares no code with the GPU library and is used
+ * only by the tests, the smoke check and the CPU-baseline leg of the benchmark.
+ *
+ * All arrays are host memory owned by the caller. Offsets, vertex weights and edge weights are
+ * int64 here (the Python wrapper widens narrower inputs); a NULL weight array means unit weights.
+ */
+#ifndef GP_ORACLE_H
+#define GP_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct or_graph {
+  int64_t n;
+  int64_t m_dir;          /* directed CSR entries (2|E|) */
+  const int64_t *off;     /* n+1 */
+  const int32_t *adj;     /* m_dir, rows ascending */
+  const int64_t *vw;      /* n or NULL */
+  const int64_t *ew;      /* m_dir or NULL */
+} or_graph;
+
+typedef struct or_lp_stats {
+  int64_t rounds;         /* rounds executed */
+  int64_t moves;          /* admitted moves over all rounds */
+  int64_t visits;         /* active-vertex visits */
+  int64_t edges;          /* CSR entries scanned by visits */
+  int64_t movers;         /* movers proposed (before admission) */
+} or_lp_stats;
+
+typedef struct or_params {
+  int64_t cluster_div;        /* f: U = max(max c(v), floor(Lmax / f)) */
+  int64_t rounds_coarsen;     /* l = 10 */
+  int64_t rounds_refine;      /* 25 */
+  int64_t coarse_min;         /* T = max(coarse_min, coarse_per_k * k) */
+  int64_t coarse_per_k;
+  int64_t stall_pct;          /* stop when 100 n' > stall_pct n */
+  int64_t max_levels;
+  int64_t ip_tries;
+  int64_t repair_rounds;
+} or_params;
+
+typedef struct or_result {
+  int64_t cut;
+  int64_t max_block_weight;
+  int64_t lmax;
+  int64_t imbalanced;
+  int64_t levels;             /* contractions performed */
+  int64_t best_try;
+  int64_t n_isolated;
+  int64_t level_n[65];        /* n of each level graph (after isolated vertices are removed) */
+  int64_t level_m[65];        /* m_dir of each level graph */
+  int64_t try_cut[16];
+  int64_t try_imbalanced[16];
+} or_result;
+
+/* SplitMix64 output function and the keyed hash H(a,b,c) = mix(mix(mix(a)^b)^c). */
+uint64_t or_mix64(uint64_t z);
+uint64_t or_hash3(uint64_t a, uint64_t b, uint64_t c);
+
+/* Lmax = floor((1+eps) * ceil(W/k)), Section II-A. */
+int64_t or_lmax(int64_t total_weight, int64_t k, double eps);
+
+/* One size-constrained LP run (clustering or refinement). labels[n] and lw[nl] are in/out;
+ * q (per CSR entry, or NULL) adds the learned tie-break and admission key. Returns 0 or -1. */
+int or_lp(const or_graph *g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
+          int64_t rounds, uint64_t seed, or_lp_stats *st);
+
+/* Contraction of labels[n] (values in [0,nl)). Outputs sized for the worst case:
+ * off_out[n+1], adj_out[m_dir], vw_out[n], ew_out[m_dir], f2c[n]. Writes n' and m' to *n_out, *m_out. */
+int or_contract(const or_graph *g, const int32_t *labels, int64_t nl, int64_t *n_out, int64_t *m_out,
+                int64_t *off_out, int32_t *adj_out, int64_t *vw_out, int64_t *ew_out, int32_t *f2c);
+
+/* Recursive bisection of one initial-partitioning try (no refinement). part[n] out. */
+int or_bisect(const or_graph *g, int64_t k, uint64_t s_try, int32_t *part);
+
+/* Balance repair rounds; part in/out. Returns the number of rounds run. */
+int64_t or_repair(const or_graph *g, int64_t k, int64_t lmax, int64_t max_rounds, int32_t *part);
+
+/* cut (each undirected edge once) and block weights bw[k]. */
+int64_t or_cut(const or_graph *g, const int32_t *part, int64_t k, int64_t *bw);
+
+/* Full multilevel partition. q_levels: NULL (plain) or one q array per coarsening level. */
+void or_default_params(or_params *p);
+int or_partition(const or_graph *g, int64_t k, double eps, uint64_t seed, const or_params *p,
+                 const int32_t *const *q_levels, int64_t n_q_levels, int32_t *part, or_result *res);
+
+/* Learned edge scorer, FP64: features (8 per CSR entry) and the 8->32->1 MLP. */
+void or_edge_features(const or_graph *g, int64_t level, double *feat);
+void or_mlp_forward(int64_t m, const double *x, const double *w1, const double *b1,
+                    const double *w2, double b2, double *s_out);
+/* Mean binary cross-entropy over m rows and its gradients. */
+double or_mlp_loss_grad(int64_t m, const double *x, const double *y, const double *w1,
+                        const double *b1, const double *w2, double b2, double *gw1, double *gb1,
+                        double *gw2, double *gb2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
