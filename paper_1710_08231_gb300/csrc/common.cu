@@ -1,0 +1,260 @@
+// common.cu -- errors, allocator, device-wide scans and kernel profiling of the partitioner library.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+// ------------------------------------------------------------------------------------------ errors
+static thread_local std::string t_last_error;
+void set_error(const std::string &msg) { t_last_error = msg; }
+const char *last_error() { return t_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------------------ memory
+static gp_alloc_fn g_alloc = nullptr;
+static gp_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+void set_allocator(gp_alloc_fn a, gp_free_fn f, void *ctx) {
+  g_alloc = a;
+  g_free = a ? f : nullptr;
+  g_alloc_ctx = a ? ctx : nullptr;
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (g_alloc) {
+    if (g_free) g_free(p, bytes, s, g_alloc_ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+// ------------------------------------------------------------------------------------------ device
+int device_id() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  const int d = device_id();
+  if (d < 0 || d >= 64) return 148;
+  if (!cached[d]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+    cached[d] = v > 0 ? v : 148;
+  }
+  return cached[d];
+}
+
+// ------------------------------------------------------------------------------------------ scans
+// Three-phase scan: per-block totals, a single-block scan of the totals, per-block rescan.
+namespace {
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
+
+template <class In>
+__global__ void k_scan_reduce(const In *in, int64_t n, int64_t *block_tot) {
+  __shared__ int64_t tmp[32];
+  __shared__ int64_t tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+    if (i < n) s += (int64_t)in[i];
+  }
+  block_excl_scan64(s, tmp, &tot);
+  if (threadIdx.x == 0) block_tot[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tops(int64_t *block_tot, int64_t nb, int64_t *total_dev) {
+  __shared__ int64_t tmp[32];
+  __shared__ int64_t tot;
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t x = i < nb ? block_tot[i] : 0;
+    const int64_t ex = block_excl_scan64(x, tmp, &tot);
+    if (i < nb) block_tot[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total_dev) *total_dev = carry;
+}
+
+template <class In, class Out>
+__global__ void k_scan_final(const In *in, Out *out, int64_t n, const int64_t *block_off) {
+  __shared__ int64_t tmp[32];
+  __shared__ int64_t tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  In vals[kScanItems];
+  int64_t s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+    vals[k] = i < n ? in[i] : (In)0;
+    s += (int64_t)vals[k];
+  }
+  int64_t run = block_excl_scan64(s, tmp, &tot) + block_off[blockIdx.x];
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
+    if (i < n) out[i] = (Out)run;
+    run += (int64_t)vals[k];
+  }
+}
+
+template <class In, class Out>
+int scan_impl(const In *in, Out *out, int64_t n, int64_t *total_dev, Workspace &ws) {
+  cudaStream_t s = ws.stream();
+  if (n <= 0) {
+    if (total_dev) GP_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int64_t), s));
+    return GP_OK;
+  }
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  int64_t *bt;
+  GP_TRY(ws.get(&bt, (size_t)nb));
+  k_scan_reduce<In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bt);
+  k_scan_tops<<<1, 1024, 0, s>>>(bt, nb, total_dev);
+  k_scan_final<In, Out><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bt);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+}  // namespace
+
+int scan_excl_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, Workspace &ws) {
+  return scan_impl<int64_t, int64_t>(in, out, n, total_dev, ws);
+}
+int scan_excl_u32(const uint32_t *in, int32_t *out, int64_t n, int64_t *total_dev, Workspace &ws) {
+  return scan_impl<uint32_t, int32_t>(in, out, n, total_dev, ws);
+}
+
+// ------------------------------------------------------------------------------------------ profile
+namespace {
+struct ProfEntry {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0;
+  int64_t items = 0, edges = 0, bytes = 0;
+};
+struct Pending {
+  int entry;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfEntry> g_entries;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+
+int entry_index(const char *name) {
+  for (size_t i = 0; i < g_entries.size(); i++)
+    if (g_entries[i].name == name) return (int)i;
+  g_entries.push_back(ProfEntry());
+  g_entries.back().name = name;
+  return (int)g_entries.size() - 1;
+}
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+bool profiling() { return g_prof_on; }
+
+ProfScope::ProfScope(const char *nm, cudaStream_t st) : name(nm), s(st), slot(-1) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  Pending p;
+  p.entry = entry_index(nm);
+  p.a = take_event();
+  p.b = take_event();
+  cudaEventRecord(p.a, s);
+  g_pending.push_back(p);
+  slot = (int)g_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_pending[slot].b, s);
+}
+
+void prof_add_counts(const char *name, int64_t items, int64_t edges, int64_t bytes) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfEntry &e = g_entries[entry_index(name)];
+  e.items += items;
+  e.edges += edges;
+  e.bytes += bytes;
+}
+
+int prof_flush(cudaStream_t s) {
+  if (!g_prof_on) return GP_OK;
+  GP_CUDA(cudaStreamSynchronize(s));
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const Pending &p : g_pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_entries[p.entry].ms += ms;
+      g_entries[p.entry].launches += 1;
+    } else {
+      cudaGetLastError();
+    }
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
+  }
+  g_pending.clear();
+  return GP_OK;
+}
+
+int prof_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return GP_OK;
+}
+
+int prof_read(gp_profile_entry *out, int max_entries, int reset) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int n = 0;
+  for (const ProfEntry &e : g_entries) {
+    if (n >= max_entries) break;
+    gp_profile_entry &o = out[n++];
+    std::memset(&o, 0, sizeof(o));
+    std::strncpy(o.name, e.name.c_str(), sizeof(o.name) - 1);
+    o.launches = e.launches;
+    o.ms = e.ms;
+    o.items = e.items;
+    o.edges = e.edges;
+    o.bytes = e.bytes;
+  }
+  if (reset) g_entries.clear();
+  return n;
+}
+
+}  // namespace gp

@@ -1,0 +1,566 @@
+// contract.cu -- contraction of a clustering into the weighted quotient graph on the GPU.
+//
+// Method (Section III-A; Section IV-A "Parallel Contraction"): cluster ids are remapped to
+// [0, n') by a prefix sum over an array holding ones at the used ids; each coarse vertex weighs the
+// sum of its members; each coarse edge (a, b), a != b, weighs the sum of the fine edges between
+// clusters a and b.
+//
+// GPU design: instead of the paper's concurrent hash table, the (cv, cu, omega) pairs are sorted
+// and reduced in two levels. Fine vertices are bucketed by coarse id (a counting sort), which sorts
+// the pairs by cv; within one coarse row the pairs are sorted by cu and equal keys are summed:
+// in registers by one warp (<= 32 pairs), in shared memory by one CTA (<= 4096 pairs), or by a
+// CTA-wide LSD radix sort in global memory for larger rows. Rows come out sorted by neighbour id,
+// so the coarse CSR is canonical and independent of scheduling.
+#include <algorithm>
+#include <climits>
+
+#include "contract.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr int kRowSmall = 32;
+constexpr int kRowMedium = 4096;
+constexpr int kRowThreads = 256;
+
+__global__ void k_mark_used(const int32_t *labels, int64_t n, int64_t nl, uint32_t *used, int *bad) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int L = labels[v];
+    if (L < 0 || L >= nl) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    used[L] = 1;
+  }
+}
+
+__global__ void k_f2c(DGraph g, const int32_t *labels, const int32_t *newid, int32_t *f2c, int64_t *cnt,
+                      int64_t *cw, int64_t *dsum) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int cv = newid[labels[v]];
+    f2c[v] = cv;
+    atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[cv]), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&cw[cv]), (unsigned long long)g.vweight(v));
+    atomicAdd(reinterpret_cast<unsigned long long *>(&dsum[cv]),
+              (unsigned long long)(g.row_begin(v + 1) - g.row_begin(v)));
+  }
+}
+
+__global__ void k_members(int64_t n, const int32_t *f2c, const int64_t *mstart, unsigned *fill, int32_t *members) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int cv = f2c[v];
+    const unsigned pos = atomicAdd(&fill[cv], 1u);
+    members[mstart[cv] + pos] = (int32_t)v;
+  }
+}
+
+__global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2,
+                               unsigned *counts) {
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = base + threadIdx.x;
+    int b = -1;
+    if (c < nc) {
+      const int64_t D = dsum[c];
+      b = D <= kRowSmall ? 0 : (D <= kRowMedium ? 1 : 2);
+    }
+    int32_t *lists[3] = {l0, l1, l2};
+    for (int bb = 0; bb < 3; bb++) {
+      const unsigned m = __ballot_sync(kFull, b == bb);
+      if (!m) continue;
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      unsigned pos = 0;
+      if (lane == leader) pos = atomicAdd(&counts[bb], (unsigned)__popc(m));
+      pos = __shfl_sync(kFull, pos, leader) + __popc(m & lanemask_lt());
+      if (b == bb) lists[bb][pos] = (int32_t)c;
+    }
+  }
+}
+
+struct RowArgs {
+  DGraph g;
+  const int32_t *f2c;
+  const int64_t *mstart;
+  const int32_t *members;
+  const int64_t *tstart;
+  int32_t *okey;
+  int64_t *oval;
+  int64_t *rowcnt;
+  const int32_t *list;
+  const unsigned *count;
+  // large rows
+  const int64_t *lofs;
+  int32_t *ka, *kb;
+  int64_t *va, *vb;
+  int key_bits;
+};
+
+// Rows with at most 32 pairs: one warp gathers them into shared memory, sorts them in registers
+// (bitonic network over the lanes) and sums runs of equal neighbour ids.
+template <int EW>
+__global__ void __launch_bounds__(256) k_row_warp(RowArgs a) {
+  __shared__ int skey[8][32];
+  __shared__ long long sval[8][32];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned cnt = *a.count;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned i = gw; i < cnt; i += nw) {
+    const int cv = a.list[i];
+    const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
+    int P = 0;
+    for (int64_t m = mb; m < me; m++) {
+      const int v = a.members[m];
+      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
+      for (int64_t x = b; x < e; x += 32) {
+        const int64_t j = x + lane;
+        const bool valid = j < e;
+        const int cu = valid ? a.f2c[__ldg(a.g.adj + j)] : -1;
+        const bool keep = valid && cu != cv;
+        const unsigned mask = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int pos = P + __popc(mask & lanemask_lt());
+          skey[wid][pos] = cu;
+          sval[wid][pos] = load_ew<EW>(a.g.ew, j);
+        }
+        P += __popc(mask);
+      }
+    }
+    __syncwarp();
+    int key = lane < P ? skey[wid][lane] : INT_MAX;
+    long long val = lane < P ? sval[wid][lane] : 0;
+    __syncwarp();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int ok = __shfl_xor_sync(kFull, key, j);
+        const long long ov = __shfl_xor_sync(kFull, val, j);
+        const bool up = (lane & k) == 0;
+        const bool lower = (lane & j) == 0;
+        const bool take = lower ? (up ? ok < key : ok > key) : (up ? ok > key : ok < key);
+        if (take) {
+          key = ok;
+          val = ov;
+        }
+      }
+    }
+    long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      const int kj = __shfl_sync(kFull, key, j);
+      const long long vj = __shfl_sync(kFull, val, j);
+      if (kj == key) sum += vj;
+    }
+    const int prev = __shfl_up_sync(kFull, key, 1);
+    const bool head = lane < P && (lane == 0 || prev != key);
+    const unsigned hm = __ballot_sync(kFull, head);
+    if (head) {
+      const int64_t pos = a.tstart[cv] + __popc(hm & lanemask_lt());
+      a.okey[pos] = key;
+      a.oval[pos] = sum;
+    }
+    if (lane == 0) a.rowcnt[cv] = __popc(hm);
+  }
+}
+
+// Stable block-wide scatter of one 8-bit digit, tile by tile (blockDim.x == 256).
+__device__ void block_scatter_pass(const int32_t *ks, const long long *vs, int32_t *kd, long long *vd, int P,
+                                   int shift, unsigned *hist, unsigned *base, unsigned (*wcnt)[256]) {
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < P; t += blockDim.x) atomicAdd(&hist[((unsigned)ks[t] >> shift) & 255], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned acc = 0;
+    for (int t = 0; t < 256; t++) {
+      base[t] = acc;
+      acc += hist[t];
+    }
+  }
+  __syncthreads();
+  const int wid = threadIdx.x >> 5;
+  for (int t0 = 0; t0 < P; t0 += blockDim.x) {
+    const int p = t0 + threadIdx.x;
+    const bool valid = p < P;
+    const int key = valid ? ks[p] : 0;
+    const long long val = valid ? vs[p] : 0;
+    const int dg = valid ? (int)(((unsigned)key >> shift) & 255) : 256;
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) wcnt[k >> 8][k & 255] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(kFull, dg);
+    const int rank = __popc(peers & lanemask_lt());
+    if (valid && rank == 0) wcnt[wid][dg] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned pre = 0;
+      for (int w = 0; w < wid; w++) pre += wcnt[w][dg];
+      const unsigned pos = base[dg] + pre + rank;
+      kd[pos] = key;
+      vd[pos] = val;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      unsigned s = 0;
+      for (int w = 0; w < 8; w++) s += wcnt[w][threadIdx.x];
+      base[threadIdx.x] += s;
+    }
+    __syncthreads();
+  }
+}
+
+// Writes the runs of the sorted pairs (ks, vs)[0, P) as unique (key, sum) into out at `dst`,
+// in key order; returns the number of unique keys (valid in every thread).
+__device__ int block_reduce_runs(const int32_t *ks, const long long *vs, int P, int32_t *okey, int64_t *oval,
+                                 int64_t dst) {
+  __shared__ long long tmp[32];
+  __shared__ long long tot_s;
+  __shared__ long long carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < P; t0 += blockDim.x) {
+    const int p = t0 + threadIdx.x;
+    const bool head = p < P && (p == 0 || ks[p - 1] != ks[p]);
+    const long long ex = block_excl_scan64((long long)(head ? 1 : 0), tmp, &tot_s);
+    if (head) {
+      long long sum = 0;
+      const int key = ks[p];
+      for (int q = p; q < P && ks[q] == key; q++) sum += vs[q];
+      const int64_t pos = dst + carry_s + ex;
+      okey[pos] = key;
+      oval[pos] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += tot_s;
+    __syncthreads();
+  }
+  const int r = (int)carry_s;
+  __syncthreads();
+  return r;
+}
+
+// Rows with 32 < pairs <= 4096: one CTA stages the pairs in shared memory and sorts them there.
+template <int EW>
+__global__ void __launch_bounds__(kRowThreads) k_row_cta(RowArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long *sval = reinterpret_cast<long long *>(smem);
+  int *skey = reinterpret_cast<int *>(smem + kRowMedium * 8);
+  __shared__ unsigned sP;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const unsigned cnt = *a.count;
+  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int cv = a.list[i];
+    const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
+    if (threadIdx.x == 0) sP = 0;
+    __syncthreads();
+    for (int64_t m = mb + wid; m < me; m += nwarps) {
+      const int v = a.members[m];
+      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
+      for (int64_t x = b; x < e; x += 32) {
+        const int64_t j = x + lane;
+        const bool valid = j < e;
+        const int cu = valid ? a.f2c[__ldg(a.g.adj + j)] : -1;
+        const bool keep = valid && cu != cv;
+        const unsigned mask = __ballot_sync(kFull, keep);
+        if (!mask) continue;
+        const int leader = __ffs(mask) - 1;
+        unsigned pos = 0;
+        if (lane == leader) pos = atomicAdd(&sP, (unsigned)__popc(mask));
+        pos = __shfl_sync(kFull, pos, leader) + __popc(mask & lanemask_lt());
+        if (keep) {
+          skey[pos] = cu;
+          sval[pos] = load_ew<EW>(a.g.ew, j);
+        }
+      }
+    }
+    __syncthreads();
+    const int P = (int)sP;
+    int Pp = 1;
+    while (Pp < P) Pp <<= 1;
+    for (int t = P + threadIdx.x; t < Pp; t += blockDim.x) {
+      skey[t] = INT_MAX;
+      sval[t] = 0;
+    }
+    __syncthreads();
+    for (int k = 2; k <= Pp; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < Pp / 2; t += blockDim.x) {
+          const int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
+          const bool up = (lo & k) == 0;
+          const int x = skey[lo], y = skey[hi];
+          if ((x > y) == up && x != y) {
+            skey[lo] = y;
+            skey[hi] = x;
+            const long long vx = sval[lo];
+            sval[lo] = sval[hi];
+            sval[hi] = vx;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const int u = block_reduce_runs(skey, sval, P, a.okey, a.oval, a.tstart[cv]);
+    if (threadIdx.x == 0) a.rowcnt[cv] = u;
+    __syncthreads();
+  }
+}
+
+// Rows with more than 4096 pairs: one CTA per row, pairs staged in global memory and sorted by a
+// block-wide LSD radix sort.
+template <int EW>
+__global__ void __launch_bounds__(kRowThreads) k_row_large(RowArgs a) {
+  __shared__ unsigned sP;
+  __shared__ unsigned hist[256], base[256];
+  __shared__ unsigned wcnt[8][256];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const unsigned cnt = *a.count;
+  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int cv = a.list[i];
+    const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
+    const int64_t lb = a.lofs[i];
+    int32_t *ka = a.ka + lb, *kb = a.kb + lb;
+    long long *va = reinterpret_cast<long long *>(a.va + lb), *vb = reinterpret_cast<long long *>(a.vb + lb);
+    if (threadIdx.x == 0) sP = 0;
+    __syncthreads();
+    for (int64_t m = mb + wid; m < me; m += nwarps) {
+      const int v = a.members[m];
+      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
+      for (int64_t x = b; x < e; x += 32) {
+        const int64_t j = x + lane;
+        const bool valid = j < e;
+        const int cu = valid ? a.f2c[__ldg(a.g.adj + j)] : -1;
+        const bool keep = valid && cu != cv;
+        const unsigned mask = __ballot_sync(kFull, keep);
+        if (!mask) continue;
+        const int leader = __ffs(mask) - 1;
+        unsigned pos = 0;
+        if (lane == leader) pos = atomicAdd(&sP, (unsigned)__popc(mask));
+        pos = __shfl_sync(kFull, pos, leader) + __popc(mask & lanemask_lt());
+        if (keep) {
+          ka[pos] = cu;
+          va[pos] = load_ew<EW>(a.g.ew, j);
+        }
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    const int P = (int)sP;
+    int32_t *ks = ka, *kd = kb;
+    long long *vs = va, *vd = vb;
+    for (int shift = 0; shift < a.key_bits; shift += 8) {
+      block_scatter_pass(ks, vs, kd, vd, P, shift, hist, base, wcnt);
+      __threadfence_block();
+      __syncthreads();
+      int32_t *tk = ks;
+      ks = kd;
+      kd = tk;
+      long long *tv = vs;
+      vs = vd;
+      vd = tv;
+    }
+    const int u = block_reduce_runs(ks, vs, P, a.okey, a.oval, a.tstart[cv]);
+    if (threadIdx.x == 0) a.rowcnt[cv] = u;
+    __syncthreads();
+  }
+}
+
+__global__ void k_large_sizes(const int32_t *list, const unsigned *count, const int64_t *dsum, int64_t *sz) {
+  const unsigned cnt = *count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    sz[i] = dsum[list[i]];
+}
+
+__global__ void k_compact_rows(int64_t nc, const int64_t *tstart, const int64_t *rowcnt, const int64_t *off,
+                               const int32_t *okey, const int64_t *oval, int32_t *adj, int64_t *ew) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = gw; c < nc; c += nw) {
+    const int64_t src = tstart[c], dst = off[c], len = rowcnt[c];
+    for (int64_t t = lane; t < len; t += 32) {
+      adj[dst + t] = okey[src + t];
+      ew[dst + t] = oval[src + t];
+    }
+  }
+}
+
+template <class K>
+void set_smem(K kernel, int bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int EW>
+int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[3], int32_t *lists[3], cudaStream_t s) {
+  const int nsm = num_sms();
+  auto grid_for = [&](int64_t items, int per_block, int limit) {
+    int64_t g = (items + per_block - 1) / per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, limit));
+  };
+  ProfScope ps("contract_rows", s);
+  if (counts[0]) {
+    RowArgs b = a;
+    b.list = lists[0];
+    b.count = counts_dev + 0;
+    k_row_warp<EW><<<grid_for(counts[0], 8, nsm * 16), 256, 0, s>>>(b);
+  }
+  if (counts[1]) {
+    RowArgs b = a;
+    b.list = lists[1];
+    b.count = counts_dev + 1;
+    const int sm = kRowMedium * 12;
+    set_smem(k_row_cta<EW>, sm);
+    k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 4), kRowThreads, sm, s>>>(b);
+  }
+  if (counts[2]) {
+    RowArgs b = a;
+    b.list = lists[2];
+    b.count = counts_dev + 2;
+    k_row_large<EW><<<grid_for(counts[2], 1, nsm * 4), kRowThreads, 0, s>>>(b);
+  }
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+}  // namespace
+
+int alloc_graph(OwnedGraph *g, int64_t n, int64_t m, cudaStream_t s) {
+  g->n = n;
+  g->m = m;
+  g->off_bytes = sizeof(int64_t) * (size_t)(n + 1);
+  g->adj_bytes = sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1);
+  g->vw_bytes = sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1);
+  g->ew_bytes = sizeof(int64_t) * (size_t)std::max<int64_t>(m, 1);
+  g->off = (int64_t *)dev_alloc(g->off_bytes, s);
+  g->adj = (int32_t *)dev_alloc(g->adj_bytes, s);
+  g->vw = (int64_t *)dev_alloc(g->vw_bytes, s);
+  g->ew = (int64_t *)dev_alloc(g->ew_bytes, s);
+  if (!g->off || !g->adj || !g->vw || !g->ew) {
+    g->release(s);
+    set_error("device allocation for a coarse graph failed");
+    return GP_ERR_OOM;
+  }
+  return GP_OK;
+}
+
+int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGraph *out, int32_t *f2c_user,
+                   cudaStream_t s) {
+  Workspace ws(s);
+  const int nsm = num_sms();
+  const int64_t n = g.n;
+  auto grid_n = [&](int64_t items) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, nsm * 8));
+  };
+  if (n == 0) {
+    GP_TRY(alloc_graph(out, 0, 0, s));
+    GP_CUDA(cudaMemsetAsync(out->off, 0, sizeof(int64_t), s));
+    return GP_OK;
+  }
+  // 1. used flags -> new ids by an exclusive prefix sum
+  uint32_t *used;
+  int32_t *newid;
+  int *bad;
+  int64_t *hdr;  // [0] = n', [1] = m'
+  GP_TRY(ws.zeros(&used, (size_t)nl));
+  GP_TRY(ws.get(&newid, (size_t)nl));
+  GP_TRY(ws.zeros(&bad, 1));
+  GP_TRY(ws.zeros(&hdr, 4));
+  k_mark_used<<<grid_n(n), 256, 0, s>>>(labels, n, nl, used, bad);
+  GP_LAUNCH_CHECK();
+  GP_TRY(scan_excl_u32(used, newid, nl, hdr, ws));
+  int64_t hh[4];
+  int hbad = 0;
+  GP_CUDA(cudaMemcpyAsync(hh, hdr, sizeof(hh), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  if (hbad) {
+    set_error("contract: a label is outside [0, n)");
+    return GP_ERR_INVALID_ARG;
+  }
+  const int64_t nc = hh[0];
+  // 2. fine -> coarse map, member counts, coarse vertex weights, degree sums
+  int32_t *f2c = f2c_user;
+  if (!f2c) GP_TRY(ws.get(&f2c, (size_t)n));
+  int64_t *cnt, *dsum, *mstart, *tstart, *cw;
+  GP_TRY(ws.zeros(&cnt, (size_t)nc + 1));
+  GP_TRY(ws.zeros(&dsum, (size_t)nc + 1));
+  GP_TRY(ws.zeros(&cw, (size_t)nc));
+  GP_TRY(ws.get(&mstart, (size_t)nc + 1));
+  GP_TRY(ws.get(&tstart, (size_t)nc + 1));
+  k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, newid, f2c, cnt, cw, dsum);
+  GP_LAUNCH_CHECK();
+  GP_TRY(scan_excl_i64(cnt, mstart, nc, mstart + nc, ws));
+  GP_TRY(scan_excl_i64(dsum, tstart, nc, tstart + nc, ws));
+  // 3. members bucketed by coarse id
+  unsigned *fill;
+  int32_t *members;
+  GP_TRY(ws.zeros(&fill, (size_t)nc));
+  GP_TRY(ws.get(&members, (size_t)n));
+  k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members);
+  // 4. rows binned by pair count
+  int32_t *lists[3];
+  unsigned *counts_dev;
+  for (int b = 0; b < 3; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
+  GP_TRY(ws.zeros(&counts_dev, 4));
+  k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], counts_dev);
+  GP_LAUNCH_CHECK();
+  unsigned counts[4];
+  GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  RowArgs a;
+  a.g = g;
+  a.f2c = f2c;
+  a.mstart = mstart;
+  a.members = members;
+  a.tstart = tstart;
+  a.lofs = nullptr;
+  a.ka = a.kb = nullptr;
+  a.va = a.vb = nullptr;
+  int kb = 0;
+  while (kb < 31 && ((int64_t)1 << kb) < nc) kb++;
+  a.key_bits = kb;
+  GP_TRY(ws.get(&a.okey, (size_t)std::max<int64_t>(g.m, 1)));
+  GP_TRY(ws.get(&a.oval, (size_t)std::max<int64_t>(g.m, 1)));
+  GP_TRY(ws.get(&a.rowcnt, (size_t)nc + 1));
+  if (counts[2]) {
+    int64_t *sz, *lofs;
+    GP_TRY(ws.get(&sz, (size_t)counts[2]));
+    GP_TRY(ws.get(&lofs, (size_t)counts[2] + 1));
+    k_large_sizes<<<grid_n(counts[2]), 256, 0, s>>>(lists[2], counts_dev + 2, dsum, sz);
+    GP_TRY(scan_excl_i64(sz, lofs, counts[2], lofs + counts[2], ws));
+    int64_t tot = 0;
+    GP_CUDA(cudaMemcpyAsync(&tot, lofs + counts[2], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    GP_TRY(ws.get(&a.ka, (size_t)tot));
+    GP_TRY(ws.get(&a.kb, (size_t)tot));
+    GP_TRY(ws.get(&a.va, (size_t)tot));
+    GP_TRY(ws.get(&a.vb, (size_t)tot));
+    a.lofs = lofs;
+  }
+  const int ew = g.ew_mode();
+  GP_TRY(ew == 0 ? build_rows<0>(a, counts_dev, counts, lists, s)
+       : ew == 1 ? build_rows<1>(a, counts_dev, counts, lists, s)
+                 : build_rows<2>(a, counts_dev, counts, lists, s));
+  // 5. coarse offsets from the unique counts, then compaction of the rows
+  int64_t mc = 0;
+  int64_t *off_tmp;
+  GP_TRY(ws.get(&off_tmp, (size_t)nc + 1));
+  GP_TRY(scan_excl_i64(a.rowcnt, off_tmp, nc, off_tmp + nc, ws));
+  GP_CUDA(cudaMemcpyAsync(&mc, off_tmp + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  GP_TRY(alloc_graph(out, nc, mc, s));
+  GP_CUDA(cudaMemcpyAsync(out->off, off_tmp, sizeof(int64_t) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(out->vw, cw, sizeof(int64_t) * (size_t)nc, cudaMemcpyDeviceToDevice, s));
+  {
+    ProfScope ps("contract_compact", s);
+    k_compact_rows<<<grid_n(nc * 32), 256, 0, s>>>(nc, tstart, a.rowcnt, out->off, a.okey, a.oval, out->adj, out->ew);
+  }
+  GP_LAUNCH_CHECK();
+  if (profiling()) {
+    const int64_t rb = n * 2 * g.offset_bytes() + g.m * (4 + g.ew_bytes()) + g.m * 4;
+    prof_add_counts("contract_rows", nc, g.m, rb);
+    prof_add_counts("contract_compact", nc, mc, mc * 12 + nc * 8);
+  }
+  GP_CUDA(cudaStreamSynchronize(s));
+  return GP_OK;
+}
+
+}  // namespace gp

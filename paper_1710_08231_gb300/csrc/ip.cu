@@ -1,0 +1,655 @@
+// ip.cu -- initial partitioning of the coarsest graph, evaluation, projection and degree-0 vertices.
+//
+// Initial partitioning (Section III-B, Section IV-B): the coarsest graph is partitioned several
+// times independently and the best result is kept; each try is a recursive bisection into
+// ceil(k/2) and floor(k/2) blocks. KaHIP's bisection with local search and flows is external to the
+// paper; this library's bisection is deterministic: BFS from the vertex of minimum
+// H(s_try, depth, v), a second BFS from the farthest vertex found (ties: smaller id), vertices
+// ordered by (distance, id) with unreachable ones last, side 0 the shortest prefix whose weight
+// reaches ceil(k/2)/k of the set. All sets of one recursion depth are split together (their BFS
+// runs are one multi-source BFS restricted to each set), one CTA per try, tries in parallel.
+// A balance repair then moves vertices out of overloaded blocks (Section II-A: a block is
+// overloaded when heavier than Lmax).
+// Projection (Section III-C): a fine vertex takes the block of its coarse representative.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "block_sort.cuh"
+#include "ip.cuh"
+#include "lp.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr int kIpThreads = 1024;
+
+struct IpArgs {
+  DGraph g;
+  int k;
+  int64_t lmax;
+  uint64_t seed;
+  int level;
+  int repair_rounds;
+  int64_t ns;                // per-try stride of the scratch arrays: max(n, k)
+  int32_t *part;             // tries * n
+  int32_t *gk;               // tries * n
+  int32_t *dist;             // tries * n
+  int32_t *qa, *qb;          // tries * n
+  unsigned long long *ka, *kb;  // tries * n
+  int32_t *va, *vb;          // tries * n
+  int32_t *mv_t;             // tries * n (repair: target per vertex)
+  long long *mv_g;           // tries * n (repair: gain per vertex)
+  uint8_t *flag;             // tries * n
+  long long *gws;            // tries * k
+  unsigned long long *gminh; // tries * k
+  int *gstart;               // tries * k
+  unsigned long long *gfar;  // tries * k
+  long long *bw;             // tries * k
+  long long *conn;           // tries * kIpThreads * k
+  int *err;
+};
+
+// Multi-source BFS restricted to same-set vertices (part equal, set still being split).
+__device__ void set_bfs(const IpArgs &a, int32_t *part, int32_t *gk, int32_t *dist, int32_t *qa, int32_t *qb,
+                        int nf) {
+  __shared__ int s_next;
+  while (nf > 0) {
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      const int x = qa[i];
+      const int px = part[x];
+      const int dx = dist[x];
+      const int64_t b = a.g.row_begin(x), e = a.g.row_begin(x + 1);
+      for (int64_t j = b; j < e; j++) {
+        const int u = a.g.adj[j];
+        if (gk[u] <= 1 || part[u] != px) continue;
+        if (atomicCAS(&dist[u], -1, dx + 1) == -1) qb[atomicAdd(&s_next, 1)] = u;
+      }
+    }
+    __syncthreads();
+    nf = s_next;
+    int32_t *t = qa;
+    qa = qb;
+    qb = t;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
+  __shared__ BlockSortSmem sm;
+  __shared__ int s_any, s_maxd;
+  const int t = blockIdx.x;
+  const int n = (int)a.g.n, k = a.k;
+  const size_t ns = (size_t)a.ns;
+  int32_t *part = a.part + (size_t)t * n, *gk = a.gk + (size_t)t * ns, *dist = a.dist + (size_t)t * ns;
+  int32_t *qa = a.qa + (size_t)t * ns, *qb = a.qb + (size_t)t * ns;
+  unsigned long long *ka = a.ka + (size_t)t * ns, *kb = a.kb + (size_t)t * ns;
+  int32_t *va = a.va + (size_t)t * ns, *vb = a.vb + (size_t)t * ns;
+  long long *gws = a.gws + (size_t)t * k;
+  unsigned long long *gminh = a.gminh + (size_t)t * k, *gfar = a.gfar + (size_t)t * k;
+  int *gstart = a.gstart + (size_t)t * k;
+  const uint64_t s_try = hash3(a.seed, (uint64_t)a.level, (uint64_t)(4 + t));
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    part[v] = 0;
+    gk[v] = k;
+  }
+  __syncthreads();
+  for (int depth = 0; depth < 64; depth++) {
+    if (threadIdx.x == 0) {
+      s_any = 0;
+      s_maxd = 0;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x)
+      if (gk[v] > 1) s_any = 1;
+    __syncthreads();
+    if (!s_any) break;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+      gws[b] = 0;
+      gminh[b] = ~0ull;
+      gstart[b] = INT_MAX;
+      gfar[b] = 0;
+    }
+    __syncthreads();
+    const uint64_t hd = mix64(mix64(s_try) ^ (uint64_t)depth);
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      if (gk[v] <= 1) continue;
+      const int b = part[v];
+      atomicAdd(reinterpret_cast<unsigned long long *>(&gws[b]), (unsigned long long)a.g.vweight(v));
+      atomicMin(&gminh[b], (unsigned long long)mix64(hd ^ (uint64_t)v));
+      dist[v] = -1;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      if (gk[v] <= 1) continue;
+      const int b = part[v];
+      if (mix64(hd ^ (uint64_t)v) == gminh[b]) atomicMin(&gstart[b], v);
+    }
+    __syncthreads();
+    // BFS 1 from the start vertex of every set
+    int nf = block_compact(k, [&](int b) { return gstart[b] != INT_MAX; }, qa, sm);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      const int v = gstart[qa[i]];
+      qa[i] = v;
+      dist[v] = 0;
+    }
+    __syncthreads();
+    set_bfs(a, part, gk, dist, qa, qb, nf);
+    // farthest vertex per set, ties by smaller id
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      if (gk[v] <= 1 || dist[v] < 0) continue;
+      atomicMax(&gfar[part[v]], ((unsigned long long)dist[v] << 32) | (unsigned long long)(0x7fffffff - v));
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x)
+      if (gk[v] > 1) dist[v] = -1;
+    __syncthreads();
+    nf = block_compact(k, [&](int b) { return gfar[b] != 0; }, qa, sm);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+      const int v = 0x7fffffff - (int)(gfar[qa[i]] & 0xffffffffull);
+      qa[i] = v;
+      dist[v] = 0;
+    }
+    __syncthreads();
+    set_bfs(a, part, gk, dist, qa, qb, nf);
+    // order the vertices of every set by (set, unreachable, distance), stable in id order
+    const int na = block_compact(n, [&](int v) { return gk[v] > 1; }, va, sm);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) atomicMax(&s_maxd, dist[va[i]]);
+    __syncthreads();
+    const int db = bits_of((unsigned long long)s_maxd + 1);
+    const int kbits = bits_of((unsigned long long)(k > 1 ? k - 1 : 0));
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+      const int v = va[i];
+      const int dv = dist[v];
+      const unsigned long long unreach = dv < 0 ? 1ull : 0ull;
+      ka[i] = ((unsigned long long)part[v] << (db + 1)) | (unreach << db) | (unsigned long long)(dv < 0 ? 0 : dv);
+    }
+    __syncthreads();
+    const bool in_b = block_radix_sort(ka, va, kb, vb, na, kbits + db + 1, sm);
+    unsigned long long *ks = in_b ? kb : ka;
+    int32_t *vs = in_b ? vb : va;
+    // side 0: shortest prefix of the set whose weight reaches ceil(kS/2)/kS of the set
+    block_seg_scan(
+        na, [&](int p) { return (int)(ks[p] >> (db + 1)); },
+        [&](int p) { return a.g.vweight(vs[p]); },
+        [&](int p, long long excl, long long) {
+          const int v = vs[p];
+          const int base = (int)(ks[p] >> (db + 1));
+          const int kS = gk[v];
+          const int k0 = (kS + 1) / 2, k1 = kS / 2;
+          const __int128 lhs = (__int128)excl * kS, rhs = (__int128)gws[base] * k0;
+          if (lhs < rhs) {
+            gk[v] = k0;
+          } else {
+            part[v] = base + k0;
+            gk[v] = k1;
+          }
+        },
+        sm);
+    __syncthreads();
+  }
+}
+
+// Balance repair (one CTA per try).
+__global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
+  __shared__ BlockSortSmem sm;
+  __shared__ int s_over, s_light, s_applied;
+  __shared__ long long s_gmin, s_gmax;
+  const int t = blockIdx.x;
+  const int n = (int)a.g.n, k = a.k;
+  const size_t ns = (size_t)a.ns;
+  int32_t *part = a.part + (size_t)t * n;
+  unsigned long long *ka = a.ka + (size_t)t * ns, *kb = a.kb + (size_t)t * ns;
+  int32_t *va = a.va + (size_t)t * ns, *vb = a.vb + (size_t)t * ns;
+  int32_t *mv_t = a.mv_t + (size_t)t * ns;
+  long long *mv_g = a.mv_g + (size_t)t * ns;
+  uint8_t *flag = a.flag + (size_t)t * ns;
+  int32_t *list2 = a.qa + (size_t)t * ns;
+  long long *bw = a.bw + (size_t)t * k;
+  long long *conn = a.conn + ((size_t)t * blockDim.x + threadIdx.x) * (size_t)k;
+  const int kbits = bits_of((unsigned long long)(k > 1 ? k - 1 : 0));
+  for (int b = 0; b < k; b++) conn[b] = 0;
+  for (int rr = 0; rr < a.repair_rounds; rr++) {
+    for (int b = threadIdx.x; b < k; b += blockDim.x) bw[b] = 0;
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x)
+      atomicAdd(reinterpret_cast<unsigned long long *>(&bw[part[v]]), (unsigned long long)a.g.vweight(v));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int over = 0, light = 0;
+      for (int b = 0; b < k; b++) {
+        if (bw[b] > a.lmax) over = 1;
+        if (bw[b] < bw[light]) light = b;
+      }
+      s_over = over;
+      s_light = light;
+      s_applied = 0;
+      s_gmin = LLONG_MAX;
+      s_gmax = LLONG_MIN;
+    }
+    __syncthreads();
+    if (!s_over) break;
+    // per vertex of an overloaded block: target and gain
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+      mv_t[v] = -1;
+      const int P = part[v];
+      if (bw[P] <= a.lmax) continue;
+      const long long cv = a.g.vweight(v);
+      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
+      for (int64_t j = b; j < e; j++) conn[part[a.g.adj[j]]] += a.g.eweight(j);
+      int best = -1;
+      for (int64_t j = b; j < e; j++) {
+        const int B = part[a.g.adj[j]];
+        if (B == P || conn[B] <= 0 || bw[B] + cv > a.lmax) continue;
+        if (best < 0 || conn[B] > conn[best] || (conn[B] == conn[best] && B < best)) best = B;
+      }
+      if (best < 0 && s_light != P && bw[s_light] + cv <= a.lmax) best = s_light;
+      if (best >= 0) {
+        mv_t[v] = best;
+        mv_g[v] = conn[best] - conn[P];
+        atomicMin(&s_gmin, mv_g[v]);
+        atomicMax(&s_gmax, mv_g[v]);
+      }
+      for (int64_t j = b; j < e; j++) conn[part[a.g.adj[j]]] = 0;
+    }
+    __syncthreads();
+    const int nm = block_compact(n, [&](int v) { return mv_t[v] >= 0; }, va, sm);
+    if (nm == 0) break;
+    const unsigned long long grange = (unsigned long long)(s_gmax - s_gmin);
+    const int gb = bits_of(grange);
+    if (kbits + gb > 64) {
+      if (threadIdx.x == 0) atomicExch(a.err, GP_ERR_UNSUPPORTED);
+      return;
+    }
+    // per target: (gain desc, id asc) -- input is in id order, the sort is stable
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+      const int v = va[i];
+      ka[i] = ((unsigned long long)mv_t[v] << gb) | (unsigned long long)(s_gmax - mv_g[v]);
+    }
+    __syncthreads();
+    bool in_b = block_radix_sort(ka, va, kb, vb, nm, kbits + gb, sm);
+    unsigned long long *ks = in_b ? kb : ka;
+    int32_t *vs = in_b ? vb : va;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) flag[v] = 0;
+    __syncthreads();
+    block_seg_scan(
+        nm, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return a.g.vweight(vs[p]); },
+        [&](int p, long long, long long incl) {
+          const int v = vs[p];
+          if (bw[mv_t[v]] + incl <= a.lmax) flag[v] = 1;
+        },
+        sm);
+    __syncthreads();
+    // per source: take movers while the source is still overloaded
+    const int na = block_compact(n, [&](int v) { return flag[v] != 0; }, list2, sm);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+      const int v = list2[i];
+      ka[i] = ((unsigned long long)part[v] << gb) | (unsigned long long)(s_gmax - mv_g[v]);
+      va[i] = v;
+    }
+    __syncthreads();
+    in_b = block_radix_sort(ka, va, kb, vb, na, kbits + gb, sm);
+    ks = in_b ? kb : ka;
+    vs = in_b ? vb : va;
+    block_seg_scan(
+        na, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return a.g.vweight(vs[p]); },
+        [&](int p, long long excl, long long) {
+          const int v = vs[p];
+          const int P = (int)(ks[p] >> gb);
+          flag[v] = (bw[P] - excl > a.lmax) ? 2 : 0;
+        },
+        sm);
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x)
+      if (flag[v] == 2) {
+        part[v] = mv_t[v];
+        s_applied = 1;
+      }
+    __syncthreads();
+    if (!s_applied) break;
+  }
+}
+
+__global__ void k_cut(DGraph g, const int32_t *part, unsigned long long *acc) {
+  __shared__ long long sh[32];
+  long long s = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int pv = part[v];
+    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
+    for (int64_t j = b; j < e; j++)
+      if (part[g.adj[j]] != pv) s += g.eweight(j);
+  }
+  s = warp_sum64(s);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    long long x = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+    x = warp_sum64(x);
+    if (lane == 0 && x) atomicAdd(acc, (unsigned long long)x);
+  }
+}
+
+__global__ void k_project(const int32_t *coarse, const int32_t *f2c, int64_t n, int32_t *fine) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    fine[v] = coarse[f2c[v]];
+}
+
+__global__ void k_vw_stats(DGraph g, unsigned long long *mx, unsigned long long *sum) {
+  unsigned long long m = 0, s = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long c = (unsigned long long)g.vweight(v);
+    m = max(m, c);
+    s += c;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(kFull, m, o));
+    s += __shfl_xor_sync(kFull, s, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(mx, m);
+    atomicAdd(sum, s);
+  }
+}
+
+__global__ void k_deg_flags(DGraph g, uint32_t *keep, int64_t *deg0) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
+    keep[v] = d > 0 ? 1u : 0u;
+    deg0[v] = d;
+  }
+}
+
+__global__ void k_strip_rows(DGraph g, const int32_t *rank, const uint32_t *keep, int64_t *deg_kept) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
+    if (keep[v]) deg_kept[rank[v]] = g.row_begin(v + 1) - g.row_begin(v);
+}
+
+__global__ void k_strip_copy(DGraph g, const int32_t *rank, const uint32_t *keep, const int64_t *off0,
+                             int32_t *adj0, void *vw0, void *ew0) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = gw; v < g.n; v += nw) {
+    if (!keep[v]) continue;
+    const int r = rank[v];
+    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1), dst = off0[r];
+    if (lane == 0 && vw0) {
+      if (g.vw64) static_cast<int64_t *>(vw0)[r] = static_cast<const int64_t *>(g.vw)[v];
+      else static_cast<int32_t *>(vw0)[r] = static_cast<const int32_t *>(g.vw)[v];
+    }
+    for (int64_t j = b + lane; j < e; j += 32) {
+      adj0[dst + (j - b)] = rank[g.adj[j]];
+      if (ew0) {
+        if (g.ew64) static_cast<int64_t *>(ew0)[dst + (j - b)] = static_cast<const int64_t *>(g.ew)[j];
+        else static_cast<int32_t *>(ew0)[dst + (j - b)] = static_cast<const int32_t *>(g.ew)[j];
+      }
+    }
+  }
+}
+
+// Degree-0 vertex placement with unit weights, closed form of the greedy rule: at water level x
+// every block of weight <= x receives one vertex, blocks in id order. F(x) = sum_b max(0, x - bw_b)
+// vertices are placed before level x; vertex j (0-based, ascending id) is placed at the level x with
+// F(x) <= j < F(x+1), into the (j - F(x))-th block (by id) among those with bw_b <= x.
+__global__ void k_place_unit(DGraph g, const int32_t *rank, const int32_t *part0, const int64_t *iso_idx,
+                             const long long *bw, int64_t k, int32_t *part_full) {
+  long long bmin = LLONG_MAX;
+  for (int64_t b = 0; b < k; b++) bmin = min(bmin, bw[b]);
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int r = rank[v];
+    if (r >= 0) {
+      part_full[v] = part0[r];
+      continue;
+    }
+    const long long j = iso_idx[v];
+    long long lo = bmin, hi = bmin + j + 1;  // F(lo) = 0 <= j; F(hi) > j
+    auto F = [&](long long x) {
+      long long s = 0;
+      for (int64_t b = 0; b < k; b++) s += x > bw[b] ? x - bw[b] : 0;
+      return s;
+    };
+    while (hi - lo > 1) {
+      const long long mid = lo + (hi - lo) / 2;
+      if (F(mid) <= j) lo = mid;
+      else hi = mid;
+    }
+    long long rem = j - F(lo);
+    int pick = 0;
+    for (int64_t b = 0; b < k; b++)
+      if (bw[b] <= lo) {
+        if (rem == 0) {
+          pick = (int)b;
+          break;
+        }
+        rem--;
+      }
+    part_full[v] = pick;
+  }
+}
+
+// Degree-0 vertices with general weights: one thread applies the greedy rule in id order.
+__global__ void k_place_seq(DGraph g, const int32_t *rank, const int32_t *part0, long long *bw, int64_t k,
+                            int32_t *part_full) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int64_t v = 0; v < g.n; v++) {
+    const int r = rank[v];
+    if (r >= 0) {
+      part_full[v] = part0[r];
+      continue;
+    }
+    int b = 0;
+    for (int64_t x = 1; x < k; x++)
+      if (bw[x] < bw[b]) b = (int)x;
+    part_full[v] = b;
+    bw[b] += g.vweight(v);
+  }
+}
+
+// rank_out[v] = rank[v] for vertices with neighbours, -1 otherwise; iso_idx[v] = v - rank[v]
+// (the number of degree-0 vertices before v, since rank counts the kept vertices before v).
+__global__ void k_mark_rank(DGraph g, const int32_t *rank, int32_t *rank_out, int64_t *iso_idx) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
+    rank_out[v] = d > 0 ? rank[v] : -1;
+    iso_idx[v] = v - rank[v];
+  }
+}
+
+int grid_for_n(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8));
+}
+
+}  // namespace
+
+int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries, int repair_rounds,
+                      int32_t *parts, cudaStream_t s) {
+  if (g.n >= (1 << 30)) {
+    set_error("initial partitioning supports coarsest graphs below 2^30 vertices");
+    return GP_ERR_UNSUPPORTED;
+  }
+  Workspace ws(s);
+  IpArgs a;
+  a.g = g;
+  a.k = k;
+  a.lmax = lmax;
+  a.seed = seed;
+  a.level = level;
+  a.repair_rounds = repair_rounds;
+  a.ns = std::max<int64_t>(std::max<int64_t>(g.n, k), 1);
+  const size_t tn = (size_t)tries * (size_t)a.ns;
+  const size_t tk = (size_t)tries * (size_t)k;
+  a.part = parts;
+  GP_TRY(ws.get(&a.gk, tn));
+  GP_TRY(ws.get(&a.dist, tn));
+  GP_TRY(ws.get(&a.qa, tn));
+  GP_TRY(ws.get(&a.qb, tn));
+  GP_TRY(ws.get(&a.ka, tn));
+  GP_TRY(ws.get(&a.kb, tn));
+  GP_TRY(ws.get(&a.va, tn));
+  GP_TRY(ws.get(&a.vb, tn));
+  GP_TRY(ws.get(&a.mv_t, tn));
+  GP_TRY(ws.get(&a.mv_g, tn));
+  GP_TRY(ws.get(&a.flag, tn));
+  GP_TRY(ws.get(&a.gws, tk));
+  GP_TRY(ws.get(&a.gminh, tk));
+  GP_TRY(ws.get(&a.gstart, tk));
+  GP_TRY(ws.get(&a.gfar, tk));
+  GP_TRY(ws.get(&a.bw, tk));
+  GP_TRY(ws.get(&a.conn, tk * kIpThreads));
+  GP_TRY(ws.zeros(&a.err, 1));
+  k_bisect<<<tries, kIpThreads, 0, s>>>(a);
+  GP_LAUNCH_CHECK();
+  k_repair<<<tries, kIpThreads, 0, s>>>(a);
+  GP_LAUNCH_CHECK();
+  int err = 0;
+  GP_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("initial partitioning: gain range too wide for the repair sort keys");
+    return err;
+  }
+  return GP_OK;
+}
+
+int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev, cudaStream_t s) {
+  Workspace ws(s);
+  unsigned long long *acc;
+  GP_TRY(ws.zeros(&acc, 1));
+  if (g.n > 0) {
+    k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc);
+    GP_LAUNCH_CHECK();
+  }
+  if (bw_dev) GP_TRY(block_weights(g, part, k, bw_dev, nullptr, s));
+  unsigned long long h = 0;
+  GP_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  *cut_host = (int64_t)(h / 2);
+  return GP_OK;
+}
+
+int project(const int32_t *coarse, const int32_t *f2c, int64_t n, int32_t *fine, cudaStream_t s) {
+  if (n == 0) return GP_OK;
+  k_project<<<grid_for_n(n), 256, 0, s>>>(coarse, f2c, n, fine);
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+int vertex_weight_stats(const DGraph &g, int64_t *maxc, int64_t *total, cudaStream_t s) {
+  Workspace ws(s);
+  unsigned long long *d;
+  GP_TRY(ws.zeros(&d, 2));
+  if (g.n > 0) {
+    k_vw_stats<<<grid_for_n(g.n), 256, 0, s>>>(g, d, d + 1);
+    GP_LAUNCH_CHECK();
+  }
+  unsigned long long h[2];
+  GP_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  if (maxc) *maxc = (int64_t)h[0];
+  if (total) *total = (int64_t)h[1];
+  return GP_OK;
+}
+
+int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s) {
+  out->g0 = g;
+  out->n0 = g.n;
+  out->n_iso = 0;
+  out->rank = nullptr;
+  if (g.n == 0) return GP_OK;
+  uint32_t *keep;
+  int64_t *deg, *total;
+  int32_t *rank;
+  GP_TRY(ws.get(&keep, (size_t)g.n));
+  GP_TRY(ws.get(&deg, (size_t)g.n));
+  GP_TRY(ws.get(&rank, (size_t)g.n));
+  GP_TRY(ws.get(&total, 1));
+  k_deg_flags<<<grid_for_n(g.n), 256, 0, s>>>(g, keep, deg);
+  GP_LAUNCH_CHECK();
+  GP_TRY(scan_excl_u32(keep, rank, g.n, total, ws));
+  int64_t n0 = 0;
+  GP_CUDA(cudaMemcpyAsync(&n0, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  if (n0 == g.n) return GP_OK;
+  out->n0 = n0;
+  out->n_iso = g.n - n0;
+  out->rank = rank;
+  // rank of kept vertices = exclusive count of kept before v; mark degree-0 ones with -1 later
+  int64_t *deg0, *off0;
+  GP_TRY(ws.get(&deg0, (size_t)std::max<int64_t>(n0, 1)));
+  GP_TRY(ws.get(&off0, (size_t)n0 + 1));
+  k_strip_rows<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, keep, deg0);
+  GP_LAUNCH_CHECK();
+  GP_TRY(scan_excl_i64(deg0, off0, n0, off0 + n0, ws));
+  int32_t *adj0;
+  void *vw0 = nullptr, *ew0 = nullptr;
+  GP_TRY(ws.get(&adj0, (size_t)std::max<int64_t>(g.m, 1)));
+  if (g.vw) {
+    if (g.vw64) {
+      int64_t *p;
+      GP_TRY(ws.get(&p, (size_t)n0));
+      vw0 = p;
+    } else {
+      int32_t *p;
+      GP_TRY(ws.get(&p, (size_t)n0));
+      vw0 = p;
+    }
+  }
+  if (g.ew) {
+    if (g.ew64) {
+      int64_t *p;
+      GP_TRY(ws.get(&p, (size_t)g.m));
+      ew0 = p;
+    } else {
+      int32_t *p;
+      GP_TRY(ws.get(&p, (size_t)g.m));
+      ew0 = p;
+    }
+  }
+  k_strip_copy<<<grid_for_n(g.n * 32), 256, 0, s>>>(g, rank, keep, off0, adj0, vw0, ew0);
+  GP_LAUNCH_CHECK();
+  DGraph d;
+  d.n = n0;
+  d.m = g.m;
+  d.off = off0;
+  d.off64 = 1;
+  d.adj = adj0;
+  d.vw = vw0;
+  d.vw64 = g.vw64;
+  d.ew = ew0;
+  d.ew64 = g.ew64;
+  out->g0 = d;
+  return GP_OK;
+}
+
+int place_isolated(const DGraph &g, const Stripped &st, const int32_t *part0, int64_t k, int32_t *part_full,
+                   cudaStream_t s) {
+  Workspace ws(s);
+  if (st.n_iso == 0) {
+    if (g.n) GP_CUDA(cudaMemcpyAsync(part_full, part0, sizeof(int32_t) * (size_t)g.n, cudaMemcpyDeviceToDevice, s));
+    return GP_OK;
+  }
+  // block weights of the kept vertices
+  long long *bw;
+  GP_TRY(ws.zeros(&bw, (size_t)k));
+  GP_TRY(block_weights(st.g0, part0, k, reinterpret_cast<int64_t *>(bw), nullptr, s));
+  // rank[v] becomes -1 for degree-0 vertices; iso_idx[v] = number of degree-0 vertices before v
+  int32_t *rank;
+  int64_t *iso_idx;
+  GP_TRY(ws.get(&rank, (size_t)g.n));
+  GP_TRY(ws.get(&iso_idx, (size_t)g.n));
+  k_mark_rank<<<grid_for_n(g.n), 256, 0, s>>>(g, st.rank, rank, iso_idx);
+  GP_LAUNCH_CHECK();
+  if (!g.vw) {
+    k_place_unit<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, part0, iso_idx, bw, k, part_full);
+  } else {
+    k_place_seq<<<1, 32, 0, s>>>(g, rank, part0, bw, k, part_full);
+  }
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+}  // namespace gp

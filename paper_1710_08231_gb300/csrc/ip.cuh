@@ -1,0 +1,40 @@
+// ip.cuh -- initial partitioning, evaluation, projection and degree-0 vertex handling.
+#pragma once
+
+#include "contract.cuh"
+#include "gp_internal.cuh"
+
+namespace gp {
+
+// Recursive bisection of `tries` independent tries (try t uses s_try = H(seed, level, 4 + t)),
+// followed by balance repair. parts: tries * n int32 (device) receives the k-way partitions.
+int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries,
+                      int repair_rounds, int32_t *parts, cudaStream_t s);
+
+// cut (each undirected edge once) of part on g; also block weights into bw[k] when bw != NULL.
+int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev,
+             cudaStream_t s);
+
+// fine[v] = coarse[f2c[v]]
+int project(const int32_t *coarse, const int32_t *f2c, int64_t n, int32_t *fine, cudaStream_t s);
+
+// Degree-0 vertices: rank[v] = new id of a vertex with neighbours, -1 otherwise. g0 is the graph
+// induced by the vertices with neighbours, with the input's weight types (arrays from ws); when no
+// vertex has degree 0, g0 is the input itself.
+struct Stripped {
+  int64_t n_iso = 0;
+  int64_t n0 = 0;
+  int32_t *rank = nullptr;  // n entries (device), NULL when n_iso == 0
+  DGraph g0;
+};
+int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s);
+
+// part_full[v] = part0[rank[v]] for kept vertices; degree-0 vertices in ascending id order go
+// to the block of minimum weight (ties: smaller id) given bw (block weights of the kept vertices).
+int place_isolated(const DGraph &g, const Stripped &st, const int32_t *part0, int64_t k, int32_t *part_full,
+                   cudaStream_t s);
+
+// max over v of c(v), and sum over v of c(v) (host results)
+int vertex_weight_stats(const DGraph &g, int64_t *maxc, int64_t *total, cudaStream_t s);
+
+}  // namespace gp

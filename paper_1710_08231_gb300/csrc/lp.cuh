@@ -1,0 +1,27 @@
+// lp.cuh -- size-constrained label propagation engine (clustering and refinement).
+#pragma once
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+struct LpConfig {
+  int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 256)
+  int deg_cta = 2048;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 2048)
+                        // d > deg_cta: several CTAs per vertex, global-memory hash
+};
+
+LpConfig lp_config_from(const gp_params *p);
+
+// One LP run from (labels, lw). labels[n] in [0,nl) and lw[nl] (int64 label weights, equal to the
+// vertex-weight sums) are device arrays updated in place. q: NULL or per-entry scores.
+// seed is the run's hash seed. stats (host) may be NULL.
+int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
+           int rounds, uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg);
+
+// Block weights of a partition: bw[k] = sum of c(v) over part[v] = b (device). Sets *bad_dev
+// (device int, may be NULL) when a block id is outside [0,k).
+int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, int *bad_dev,
+                  cudaStream_t s);
+
+}  // namespace gp

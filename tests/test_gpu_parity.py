@@ -1,0 +1,198 @@
+"""GPU path vs the CPU oracle, element by element (labels, coarse CSR, partitions, cuts, stats).
+
+All integer results must be bit-identical. Inputs are seeded synthetic graphs of the paper's
+workload families (grid/mesh, random geometric, R-MAT power law, weighted R-MAT)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_1710_08231_gb300 as m
+    m.build()
+    m.lp_set_schedule(0, 0)
+    return m
+
+
+def _graphs():
+    g_vw = gg.rgg(3000, 9.0, 5)
+    g_vw.vw = np.random.default_rng(2).integers(1, 5, g_vw.n).astype(np.int32)
+    return {
+        "grid256": gg.grid(256, 256),
+        "grid_ragged": gg.grid(37, 53),
+        "rgg15": gg.rgg(1 << 15, 12.0, 1),
+        "rmat13": gg.rmat(13, 16, seed=3),
+        "rmat12w": gg.rmat(12, 16, seed=4, weighted=True),
+        "rgg_vw": g_vw,
+    }
+
+
+GRAPHS = _graphs()
+
+
+def _stats_eq(a: dict, b):
+    for k in ("rounds", "moves", "visits", "edges", "movers"):
+        assert a[k] == getattr(b, k), (k, a[k], getattr(b, k))
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("sched", [(0, 0), (32, 32), (256, 2048)])
+def test_lp_cluster_matches_oracle(gp, name, sched):
+    g = GRAPHS[name]
+    gp.lp_set_schedule(*sched)
+    try:
+        dg = gp.DeviceGraph.from_host(g)
+        c = O.vertex_weights(g)
+        U = int(max(c.max(), 40))
+        seed = 0xC0FFEE
+        lab, st = gp.lp_cluster(dg, U, 10, seed)
+        lab_o, lw_o, st_o = O.lp_cluster(g, U, 10, seed)
+        assert np.array_equal(lab.cpu().numpy(), lab_o)
+        _stats_eq(st, st_o)
+    finally:
+        gp.lp_set_schedule(0, 0)
+
+
+@pytest.mark.parametrize("name", ["rgg15", "rmat13", "rmat12w"])
+def test_lp_cluster_learned_scores_match_oracle(gp, name):
+    import torch
+    g = GRAPHS[name]
+    rng = np.random.default_rng(7)
+    # symmetric per-edge scores in [0, 2^15]
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    key = np.minimum(src, g.adj).astype(np.int64) * g.n + np.maximum(src, g.adj)
+    q = (np.vectorize(lambda x: O.mix64(int(x)) & 0x7FFF, otypes=[np.int64])(key)).astype(np.int32)
+    dg = gp.DeviceGraph.from_host(g)
+    lab, st = gp.lp_cluster(dg, 60, 10, 99, q=torch.from_numpy(q).cuda())
+    lab_o, _, st_o = O.lp_cluster(g, 60, 10, 99, q=q)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    _stats_eq(st, st_o)
+
+
+@pytest.mark.parametrize("name", ["grid256", "rgg15", "rmat13", "rmat12w", "rgg_vw"])
+@pytest.mark.parametrize("k", [2, 16])
+def test_lp_refine_matches_oracle(gp, name, k):
+    import torch
+    g = GRAPHS[name]
+    rng = np.random.default_rng(k)
+    part = rng.integers(0, k, g.n).astype(np.int32)
+    c = O.vertex_weights(g)
+    lm = O.lmax(int(c.sum()), k, 0.03)
+    dg = gp.DeviceGraph.from_host(g)
+    p, bw, st = gp.lp_refine(dg, torch.from_numpy(part).cuda(), k, lm, 25, 1234)
+    p_o, bw_o, st_o = O.lp_refine(g, part, k, lm, 25, 1234)
+    assert np.array_equal(p.cpu().numpy(), p_o)
+    assert np.array_equal(bw.cpu().numpy(), bw_o)
+    _stats_eq(st, st_o)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_contract_matches_oracle(gp, name):
+    import torch
+    g = GRAPHS[name]
+    lab_o, _, _ = O.lp_cluster(g, 30, 10, 5)
+    dg = gp.DeviceGraph.from_host(g)
+    cg, f2c = gp.contract(dg, torch.from_numpy(lab_o).cuda())
+    h = cg.to_host()
+    co, f2c_o = O.contract(g, lab_o)
+    assert h.n == co.n
+    assert np.array_equal(f2c.cpu().numpy(), f2c_o)
+    assert np.array_equal(h.off, co.off)
+    assert np.array_equal(h.adj, co.adj)
+    assert np.array_equal(h.vw, co.vw)
+    assert np.array_equal(h.ew, co.ew)
+    cg.free()
+
+
+def test_contract_arbitrary_labels(gp):
+    import torch
+    g = GRAPHS["rmat13"]
+    rng = np.random.default_rng(11)
+    lab = rng.integers(0, 50, g.n).astype(np.int32)  # few huge clusters: the large-row path
+    dg = gp.DeviceGraph.from_host(g)
+    cg, f2c = gp.contract(dg, torch.from_numpy(lab).cuda())
+    h = cg.to_host()
+    co, f2c_o = O.contract(g, lab)
+    for a, b in [(h.off, co.off), (h.adj, co.adj), (h.vw, co.vw), (h.ew, co.ew), (f2c.cpu().numpy(), f2c_o)]:
+        assert np.array_equal(a, b)
+    cg.free()
+
+
+PARTS = [("grid256", 2), ("grid_ragged", 3), ("rgg15", 16), ("rmat13", 16), ("rmat12w", 8), ("rgg_vw", 4)]
+
+
+@pytest.mark.parametrize("name,k", PARTS)
+def test_partition_matches_oracle(gp, name, k):
+    g = GRAPHS[name]
+    params = gp.default_params()
+    oparams = O.default_params()
+    if g.n < 20000:
+        params.coarse_min = oparams.coarse_min = 300
+    dg = gp.DeviceGraph.from_host(g)
+    part, res = gp.partition(dg, k, 0.03, 1, params)
+    part_o, res_o = O.partition(g, k, 0.03, 1, oparams)
+    assert res.levels == res_o.levels
+    assert res.level_n == list(res_o.level_n[: res_o.levels + 1])
+    assert res.level_m == list(res_o.level_m[: res_o.levels + 1])
+    assert res.try_cut == list(res_o.try_cut[:4])
+    assert res.best_try == res_o.best_try
+    assert np.array_equal(part.cpu().numpy(), part_o)
+    assert (res.cut, res.max_block_weight, res.lmax, res.imbalanced, res.n_isolated) == (
+        res_o.cut, res_o.max_block_weight, res_o.lmax, res_o.imbalanced, res_o.n_isolated)
+
+
+def test_partition_edge_cases(gp):
+    import torch
+    # no edges at all: every vertex is degree-0 and goes to the lightest block
+    n = 10
+    g = gg.Graph(n, np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    dg = gp.DeviceGraph.from_host(g)
+    part, res = gp.partition(dg, 3, 0.0, 1)
+    part_o, res_o = O.partition(g, 3, 0.0, 1)
+    assert np.array_equal(part.cpu().numpy(), part_o) and res.cut == 0
+    # k = 1 and k = n on a small grid
+    g = gg.grid(4, 5)
+    dg = gp.DeviceGraph.from_host(g)
+    for k in (1, g.n):
+        part, res = gp.partition(dg, k, 0.03, 2)
+        part_o, res_o = O.partition(g, k, 0.03, 2)
+        assert np.array_equal(part.cpu().numpy(), part_o) and res.cut == res_o.cut
+    # invalid k is an error, not a crash
+    with pytest.raises(gp.GpError):
+        gp.partition(dg, 0, 0.03, 1)
+    with pytest.raises(gp.GpError):
+        gp.partition(dg, g.n + 1, 0.03, 1)
+
+
+def test_partition_host_buffers(gp):
+    g = GRAPHS["rgg15"]
+    hg = gp.HostGraph(g)
+    part, res = gp.partition_host(hg, 16, 0.03, 1)
+    part_o, res_o = O.partition(g, 16, 0.03, 1)
+    assert np.array_equal(part, part_o) and res.cut == res_o.cut
+
+
+def test_validate_rejects_bad_graphs(gp):
+    g = gg.grid(8, 8)
+    assert gp.validate(gp.DeviceGraph.from_host(g)) == 0
+    bad = gg.Graph(g.n, g.off.copy(), g.adj.copy())
+    bad.adj[3] = bad.adj[2]  # duplicate / unsorted entry
+    assert gp.validate(gp.DeviceGraph.from_host(bad)) == gp.GP_ERR_BAD_GRAPH
+    asym = gg.Graph(g.n, g.off.copy(), g.adj.copy(), None, np.ones(g.m_dir, dtype=np.int32))
+    asym.ew[0] = 2
+    assert gp.validate(gp.DeviceGraph.from_host(asym)) == gp.GP_ERR_BAD_GRAPH
+
+
+def test_determinism_repeated_runs(gp):
+    g = GRAPHS["rmat13"]
+    dg = gp.DeviceGraph.from_host(g)
+    outs = [gp.partition(dg, 16, 0.03, 9)[0].cpu().numpy() for _ in range(3)]
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
