@@ -1,0 +1,314 @@
+"""Benchmark: full multilevel LP partition on the GPU, reported as LP GTEPS.
+
+A step is one complete partition (coarsening LP + contraction per level, initial partitioning,
+projection + LP refinement per level, degree-0 placement, evaluation) of one synthetic graph whose CSR
+is resident in HBM when the timed region starts. value = LP edges traversed per step (CSR entries
+scanned by all LP sub-rounds of the partition, counted by the library) / device time per step.
+
+Default workload: random geometric graph, 2^20 vertices, average degree 12, unit weights, k=16,
+eps=0.03, seed 1 (a stand-in for the paper's rgg instances).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+For N > 1 the script runs under torch.distributed.run; every rank partitions its own replica
+(replicas only: the single-graph path does not shard), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rgg20": dict(kind="rgg", n=1 << 20, deg=12.0, k=16, desc="random geometric graph 2^20 vertices, avg degree 12, unit weights, k=16, eps=0.03, seed 1"),
+    "grid256": dict(kind="grid", a=256, b=256, k=2, desc="2D 4-neighbour grid 256x256, unit weights, k=2, eps=0.03, seed 1"),
+    "rmat24": dict(kind="rmat", scale=24, ef=16, k=16, weighted=False, desc="R-MAT scale 24, edge factor 16, (0.57,0.19,0.19), symmetrised, unit weights, k=16, eps=0.03, seed 1"),
+    "rmat26w": dict(kind="rmat", scale=26, ef=16, k=64, weighted=True, desc="R-MAT scale 26, edge factor 16, edge weights in [1,8], k=64, eps=0.03, seed 1"),
+}
+EPS, SEED = 0.03, 1
+METRIC = "LP GTEPS + ms/partition at equal cut (plain vs learned/batched), % HBM peak"
+
+
+def make_graph(name: str):
+    import graphgen as gg
+    w = WORKLOADS[name]
+    if w["kind"] == "rgg":
+        return gg.rgg(w["n"], w["deg"], SEED)
+    if w["kind"] == "grid":
+        return gg.grid(w["a"], w["b"])
+    return gg.rmat(w["scale"], w["ef"], seed=SEED, weighted=w["weighted"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", 0))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, dist.get_world_size(), local, dist
+    torch.cuda.set_device(0)
+    return 0, 1, 0, None
+
+
+def barrier(dist):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x: float, dist) -> float:
+    import torch
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist) -> float:
+    import torch
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_oracle_sample(g, k: int):
+    import oracle
+    t0 = time.perf_counter()
+    part, res = oracle.partition(g, k, EPS, SEED)
+    dt = time.perf_counter() - t0
+    return res.lp_edges, dt, res
+
+
+def bench_reference(args, g, w):
+    """Reference arm: the CPU oracle as it stands, single-threaded, one full partition per step."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        run_oracle_sample(g, w["k"])
+    tot_e, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        e, dt, res = run_oracle_sample(g, w["k"])
+        tot_e += e
+        tot_t += dt
+    value = tot_e / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": w["desc"], "n": g.n, "m_dir": g.m_dir, "k": w["k"]},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"one full oracle partition of the workload per step (cut {res.cut})"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rgg20", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--once", action="store_true", help="one untimed partition (for profiler launch lists)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        g = make_graph(args.workload)
+        bench_reference(args, g, w)
+        return
+
+    import torch
+    import paper_1710_08231_gb300 as gp
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    gp.build()
+    g = make_graph(args.workload)
+    k = w["k"]
+    dg = gp.DeviceGraph.from_host(g)
+    part = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _, res = gp.partition(dg, k, EPS, SEED + rank, out=part)
+        return res
+
+    if args.once:
+        res = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"once": True, "cut": res.cut, "lp_edges": res.lp_edges, "launches": gp.launch_count()}))
+        return
+
+    for _ in range(args.warmup):
+        res0 = step()
+    lp_edges_step = res0.lp_edges
+
+    # ---- pass A: the timed region (device time per step, L2 flushed between steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = gp.launch_count()
+    barrier(dist)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            res = step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(dist)
+    launches = gp.launch_count() - launches0
+    ms_local = sum(a.elapsed_time(b) for a, b in ev)
+    ms_total = max_over_ranks(ms_local, dist)
+    edges_all = sum_over_ranks(float(lp_edges_step * args.steps), dist)
+    value = edges_all / (ms_total * 1e-3) / 1e9
+
+    # ---- pass B: same steps with per-launch CUDA events around the LP scan kernels
+    gp.profile_read(reset=True)
+    gp.profile_enable(True)
+    for i in range(args.steps):
+        flush.fill_(i)
+        step()
+    torch.cuda.synchronize()
+    gp.profile_enable(False)
+    prof = gp.profile_read(reset=True)
+    lp_entries = [e for e in prof if e["name"].startswith("lp_choose") and e["launches"] > 0]
+    top = max(lp_entries, key=lambda e: e["ms"]) if lp_entries else None
+    peak, peak_kind = peaks()
+    roofline = None
+    if top:
+        achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": top["name"], "launches": top["launches"],
+                    "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
+                    "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
+        lp_all_ms = sum(e["ms"] for e in lp_entries)
+        lp_all_bytes = sum(e["bytes"] for e in lp_entries)
+        roofline["lp_scan_all"] = {"ms_per_step": lp_all_ms / args.steps,
+                                   "achieved_gbs": lp_all_bytes / (lp_all_ms * 1e-3) / 1e9 if lp_all_ms else None}
+
+    # ---- pass C: end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hg = gp.HostGraph(g, pin=True)
+        for _ in range(2):
+            gp.partition_host(hg, k, EPS, SEED + rank)
+        barrier(dist)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            gp.partition_host(hg, k, EPS, SEED + rank)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": edges_all / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hg.h2d_bytes,
+               "d2h_bytes_per_step": hg.d2h_bytes, "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        e, dt, ores = run_oracle_sample(g, k)
+        cpu = {"value": e / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"one full single-threaded oracle partition of the same graph ({dt:.1f} s, cut {ores.cut}, "
+                         f"same cut as the GPU: {ores.cut == res.cut})"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": w["desc"], "n": g.n, "m_dir": g.m_dir, "k": k,
+                           "lp_edges_per_partition": lp_edges_step, "cut": res.cut,
+                           "max_block_weight": res.max_block_weight, "lmax": res.lmax,
+                           "imbalanced": res.imbalanced, "levels": res.levels,
+                           "ms_per_partition": ms_total / args.steps,
+                           "l2": "flushed between steps (256 MB write outside the per-step events)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "wall_ms_per_step": 1e3 * wall / args.steps},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -48,7 +48,7 @@ class OrResult(ctypes.Structure):
     _fields_ = [("cut", I64), ("max_block_weight", I64), ("lmax", I64), ("imbalanced", I64),
                 ("levels", I64), ("best_try", I64), ("n_isolated", I64),
                 ("level_n", I64 * 65), ("level_m", I64 * 65),
-                ("try_cut", I64 * 16), ("try_imbalanced", I64 * 16)]
+                ("try_cut", I64 * 16), ("try_imbalanced", I64 * 16), ("lp_edges", I64)]
 
 
 def build(force: bool = False) -> str:

@@ -60,6 +60,7 @@ typedef struct or_result {
   int64_t level_m[65];        /* m_dir of each level graph */
   int64_t try_cut[16];
   int64_t try_imbalanced[16];
+  int64_t lp_edges;           /* CSR entries scanned by all LP runs */
 } or_result;
 
 /* SplitMix64 output function and the keyed hash H(a,b,c) = mix(mix(mix(a)^b)^c). */

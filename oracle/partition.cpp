@@ -316,8 +316,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
         if (l >= n_q_levels) return -2;
         q = q_levels[l];
       }
+      or_lp_stats ls;
       or_lp(&gl, q, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen,
-            or_hash3(seed, (uint64_t)l, 1), nullptr);
+            or_hash3(seed, (uint64_t)l, 1), &ls);
+      res->lp_edges += ls.edges;
       OwnedGraph c;
       c.off.resize(gl.n + 1);
       c.adj.resize(gl.m_dir);
@@ -346,8 +348,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       or_repair(&gc, k, lmax, p.repair_rounds, pt.data());
       std::vector<int64_t> bw(k);
       or_cut(&gc, pt.data(), k, bw.data());
+      or_lp_stats ls;
       or_lp(&gc, nullptr, pt.data(), bw.data(), k, lmax, p.rounds_refine,
-            or_hash3(s_try, (uint64_t)levels, 3), nullptr);
+            or_hash3(s_try, (uint64_t)levels, 3), &ls);
+      res->lp_edges += ls.edges;
       const int64_t cut = or_cut(&gc, pt.data(), k, bw.data());
       const int64_t imb = *std::max_element(bw.begin(), bw.end()) > lmax ? 1 : 0;
       res->try_cut[t] = cut;
@@ -366,8 +370,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       for (int64_t v = 0; v < gl.n; v++) fine[v] = cur[f2c[l][v]];
       std::vector<int64_t> bw(k);
       or_cut(&gl, fine.data(), k, bw.data());
+      or_lp_stats ls;
       or_lp(&gl, nullptr, fine.data(), bw.data(), k, lmax, p.rounds_refine,
-            or_hash3(seed, (uint64_t)l, 2), nullptr);
+            or_hash3(seed, (uint64_t)l, 2), &ls);
+      res->lp_edges += ls.edges;
       cur.swap(fine);
     }
     res->levels = levels;

@@ -132,6 +132,8 @@ def lib():
                                          ctypes.POINTER(GpResult), VP]
         L.gp_lp_set_schedule.restype = ctypes.c_int
         L.gp_lp_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.gp_launch_count.restype = I64
+        L.gp_launch_count.argtypes = [ctypes.c_int]
         L.gp_profile_enable.restype = ctypes.c_int
         L.gp_profile_enable.argtypes = [ctypes.c_int]
         L.gp_profile_read.restype = ctypes.c_int
@@ -405,6 +407,11 @@ def partition_host(hg: HostGraph, k: int, eps: float, seed: int, params: Optiona
 def lp_set_schedule(deg_warp: int = 0, deg_cta: int = 0):
     """Degree-bin thresholds of the LP kernels for gp_lp_cluster/gp_lp_refine (0 = defaults)."""
     _check(lib().gp_lp_set_schedule(deg_warp, deg_cta), "gp_lp_set_schedule")
+
+
+def launch_count(reset: bool = False) -> int:
+    """Kernel launches issued by the library (optionally resetting the counter)."""
+    return int(lib().gp_launch_count(1 if reset else 0))
 
 
 def profile_enable(on: bool = True):

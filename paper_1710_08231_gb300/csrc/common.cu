@@ -1,5 +1,6 @@
 // common.cu -- errors, allocator, device-wide scans and kernel profiling of the partitioner library.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -132,9 +133,9 @@ int scan_impl(const In *in, Out *out, int64_t n, int64_t *total_dev, Workspace &
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
   int64_t *bt;
   GP_TRY(ws.get(&bt, (size_t)nb));
-  k_scan_reduce<In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bt);
-  k_scan_tops<<<1, 1024, 0, s>>>(bt, nb, total_dev);
-  k_scan_final<In, Out><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bt);
+  (::gp::count_launch(), k_scan_reduce<In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bt));
+  (::gp::count_launch(), k_scan_tops<<<1, 1024, 0, s>>>(bt, nb, total_dev));
+  (::gp::count_launch(), k_scan_final<In, Out><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bt));
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
@@ -185,7 +186,15 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+std::atomic<long long> g_launches{0};
+
 bool profiling() { return g_prof_on; }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+long long launch_count(int reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
 
 ProfScope::ProfScope(const char *nm, cudaStream_t st) : name(nm), s(st), slot(-1) {
   if (!g_prof_on) return;

@@ -400,7 +400,7 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[3], 
     RowArgs b = a;
     b.list = lists[0];
     b.count = counts_dev + 0;
-    k_row_warp<EW><<<grid_for(counts[0], 8, nsm * 16), 256, 0, s>>>(b);
+    (::gp::count_launch(), k_row_warp<EW><<<grid_for(counts[0], 8, nsm * 16), 256, 0, s>>>(b));
   }
   if (counts[1]) {
     RowArgs b = a;
@@ -408,13 +408,13 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[3], 
     b.count = counts_dev + 1;
     const int sm = kRowMedium * 12;
     set_smem(k_row_cta<EW>, sm);
-    k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 4), kRowThreads, sm, s>>>(b);
+    (::gp::count_launch(), k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 4), kRowThreads, sm, s>>>(b));
   }
   if (counts[2]) {
     RowArgs b = a;
     b.list = lists[2];
     b.count = counts_dev + 2;
-    k_row_large<EW><<<grid_for(counts[2], 1, nsm * 4), kRowThreads, 0, s>>>(b);
+    (::gp::count_launch(), k_row_large<EW><<<grid_for(counts[2], 1, nsm * 4), kRowThreads, 0, s>>>(b));
   }
   GP_LAUNCH_CHECK();
   return GP_OK;
@@ -463,7 +463,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_TRY(ws.get(&newid, (size_t)nl));
   GP_TRY(ws.zeros(&bad, 1));
   GP_TRY(ws.zeros(&hdr, 4));
-  k_mark_used<<<grid_n(n), 256, 0, s>>>(labels, n, nl, used, bad);
+  (::gp::count_launch(), k_mark_used<<<grid_n(n), 256, 0, s>>>(labels, n, nl, used, bad));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_u32(used, newid, nl, hdr, ws));
   int64_t hh[4];
@@ -485,7 +485,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_TRY(ws.zeros(&cw, (size_t)nc));
   GP_TRY(ws.get(&mstart, (size_t)nc + 1));
   GP_TRY(ws.get(&tstart, (size_t)nc + 1));
-  k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, newid, f2c, cnt, cw, dsum);
+  (::gp::count_launch(), k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, newid, f2c, cnt, cw, dsum));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_i64(cnt, mstart, nc, mstart + nc, ws));
   GP_TRY(scan_excl_i64(dsum, tstart, nc, tstart + nc, ws));
@@ -494,13 +494,13 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   int32_t *members;
   GP_TRY(ws.zeros(&fill, (size_t)nc));
   GP_TRY(ws.get(&members, (size_t)n));
-  k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members);
+  (::gp::count_launch(), k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members));
   // 4. rows binned by pair count
   int32_t *lists[3];
   unsigned *counts_dev;
   for (int b = 0; b < 3; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
   GP_TRY(ws.zeros(&counts_dev, 4));
-  k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], counts_dev);
+  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], counts_dev));
   GP_LAUNCH_CHECK();
   unsigned counts[4];
   GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
@@ -524,7 +524,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
     int64_t *sz, *lofs;
     GP_TRY(ws.get(&sz, (size_t)counts[2]));
     GP_TRY(ws.get(&lofs, (size_t)counts[2] + 1));
-    k_large_sizes<<<grid_n(counts[2]), 256, 0, s>>>(lists[2], counts_dev + 2, dsum, sz);
+    (::gp::count_launch(), k_large_sizes<<<grid_n(counts[2]), 256, 0, s>>>(lists[2], counts_dev + 2, dsum, sz));
     GP_TRY(scan_excl_i64(sz, lofs, counts[2], lofs + counts[2], ws));
     int64_t tot = 0;
     GP_CUDA(cudaMemcpyAsync(&tot, lofs + counts[2], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -551,7 +551,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_CUDA(cudaMemcpyAsync(out->vw, cw, sizeof(int64_t) * (size_t)nc, cudaMemcpyDeviceToDevice, s));
   {
     ProfScope ps("contract_compact", s);
-    k_compact_rows<<<grid_n(nc * 32), 256, 0, s>>>(nc, tstart, a.rowcnt, out->off, a.okey, a.oval, out->adj, out->ew);
+    (::gp::count_launch(), k_compact_rows<<<grid_n(nc * 32), 256, 0, s>>>(nc, tstart, a.rowcnt, out->off, a.okey, a.oval, out->adj, out->ew));
   }
   GP_LAUNCH_CHECK();
   if (profiling()) {

@@ -231,6 +231,8 @@ int scan_excl_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev
 int scan_excl_u32(const uint32_t *in, int32_t *out, int64_t n, int64_t *total_dev, Workspace &ws);
 
 // ------------------------------------------------------------------------------------------ profile
+// Counts every kernel launch the library issues (read with gp_launch_count).
+void count_launch();
 bool profiling();
 struct ProfScope {
   // Records start/stop events on `s` around a launch when profiling is on.

@@ -501,9 +501,9 @@ int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int l
   GP_TRY(ws.get(&a.bw, tk));
   GP_TRY(ws.get(&a.conn, tk * kIpThreads));
   GP_TRY(ws.zeros(&a.err, 1));
-  k_bisect<<<tries, kIpThreads, 0, s>>>(a);
+  (::gp::count_launch(), k_bisect<<<tries, kIpThreads, 0, s>>>(a));
   GP_LAUNCH_CHECK();
-  k_repair<<<tries, kIpThreads, 0, s>>>(a);
+  (::gp::count_launch(), k_repair<<<tries, kIpThreads, 0, s>>>(a));
   GP_LAUNCH_CHECK();
   int err = 0;
   GP_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -520,7 +520,7 @@ int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host,
   unsigned long long *acc;
   GP_TRY(ws.zeros(&acc, 1));
   if (g.n > 0) {
-    k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc);
+    (::gp::count_launch(), k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc));
     GP_LAUNCH_CHECK();
   }
   if (bw_dev) GP_TRY(block_weights(g, part, k, bw_dev, nullptr, s));
@@ -533,7 +533,7 @@ int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host,
 
 int project(const int32_t *coarse, const int32_t *f2c, int64_t n, int32_t *fine, cudaStream_t s) {
   if (n == 0) return GP_OK;
-  k_project<<<grid_for_n(n), 256, 0, s>>>(coarse, f2c, n, fine);
+  (::gp::count_launch(), k_project<<<grid_for_n(n), 256, 0, s>>>(coarse, f2c, n, fine));
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
@@ -543,7 +543,7 @@ int vertex_weight_stats(const DGraph &g, int64_t *maxc, int64_t *total, cudaStre
   unsigned long long *d;
   GP_TRY(ws.zeros(&d, 2));
   if (g.n > 0) {
-    k_vw_stats<<<grid_for_n(g.n), 256, 0, s>>>(g, d, d + 1);
+    (::gp::count_launch(), k_vw_stats<<<grid_for_n(g.n), 256, 0, s>>>(g, d, d + 1));
     GP_LAUNCH_CHECK();
   }
   unsigned long long h[2];
@@ -567,7 +567,7 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
   GP_TRY(ws.get(&deg, (size_t)g.n));
   GP_TRY(ws.get(&rank, (size_t)g.n));
   GP_TRY(ws.get(&total, 1));
-  k_deg_flags<<<grid_for_n(g.n), 256, 0, s>>>(g, keep, deg);
+  (::gp::count_launch(), k_deg_flags<<<grid_for_n(g.n), 256, 0, s>>>(g, keep, deg));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_u32(keep, rank, g.n, total, ws));
   int64_t n0 = 0;
@@ -581,7 +581,7 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
   int64_t *deg0, *off0;
   GP_TRY(ws.get(&deg0, (size_t)std::max<int64_t>(n0, 1)));
   GP_TRY(ws.get(&off0, (size_t)n0 + 1));
-  k_strip_rows<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, keep, deg0);
+  (::gp::count_launch(), k_strip_rows<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, keep, deg0));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_i64(deg0, off0, n0, off0 + n0, ws));
   int32_t *adj0;
@@ -609,7 +609,7 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
       ew0 = p;
     }
   }
-  k_strip_copy<<<grid_for_n(g.n * 32), 256, 0, s>>>(g, rank, keep, off0, adj0, vw0, ew0);
+  (::gp::count_launch(), k_strip_copy<<<grid_for_n(g.n * 32), 256, 0, s>>>(g, rank, keep, off0, adj0, vw0, ew0));
   GP_LAUNCH_CHECK();
   DGraph d;
   d.n = n0;
@@ -641,12 +641,12 @@ int place_isolated(const DGraph &g, const Stripped &st, const int32_t *part0, in
   int64_t *iso_idx;
   GP_TRY(ws.get(&rank, (size_t)g.n));
   GP_TRY(ws.get(&iso_idx, (size_t)g.n));
-  k_mark_rank<<<grid_for_n(g.n), 256, 0, s>>>(g, st.rank, rank, iso_idx);
+  (::gp::count_launch(), k_mark_rank<<<grid_for_n(g.n), 256, 0, s>>>(g, st.rank, rank, iso_idx));
   GP_LAUNCH_CHECK();
   if (!g.vw) {
-    k_place_unit<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, part0, iso_idx, bw, k, part_full);
+    (::gp::count_launch(), k_place_unit<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, part0, iso_idx, bw, k, part_full));
   } else {
-    k_place_seq<<<1, 32, 0, s>>>(g, rank, part0, bw, k, part_full);
+    (::gp::count_launch(), k_place_seq<<<1, 32, 0, s>>>(g, rank, part0, bw, k, part_full));
   }
   GP_LAUNCH_CHECK();
   return GP_OK;

@@ -1015,51 +1015,52 @@ struct LpKernels {
       int64_t g = (items + per_block - 1) / per_block;
       return (int)std::max<int64_t>(1, std::min<int64_t>(g, limit));
     };
-    {
+    if (cap[0]) {
       ProfScope ps("lp_choose_g4", s);
-      if (cap[0]) k_choose_group<4, EW, LQ><<<grid_for(cap[0], 64, nsm * 16), 256, 0, s>>>(a, 0);
+      (::gp::count_launch(), k_choose_group<4, EW, LQ><<<grid_for(cap[0], 64, nsm * 16), 256, 0, s>>>(a, 0));
     }
-    {
+    if (cap[1]) {
       ProfScope ps("lp_choose_g8", s);
-      if (cap[1]) k_choose_group<8, EW, LQ><<<grid_for(cap[1], 32, nsm * 16), 256, 0, s>>>(a, 1);
+      (::gp::count_launch(), k_choose_group<8, EW, LQ><<<grid_for(cap[1], 32, nsm * 16), 256, 0, s>>>(a, 1));
     }
-    {
+    if (cap[2]) {
       ProfScope ps("lp_choose_g16", s);
-      if (cap[2]) k_choose_group<16, EW, LQ><<<grid_for(cap[2], 16, nsm * 16), 256, 0, s>>>(a, 2);
+      (::gp::count_launch(), k_choose_group<16, EW, LQ><<<grid_for(cap[2], 16, nsm * 16), 256, 0, s>>>(a, 2));
     }
-    {
+    if (cap[3]) {
       ProfScope ps("lp_choose_g32", s);
-      if (cap[3]) k_choose_group<32, EW, LQ><<<grid_for(cap[3], 8, nsm * 16), 256, 0, s>>>(a, 3);
+      (::gp::count_launch(), k_choose_group<32, EW, LQ><<<grid_for(cap[3], 8, nsm * 16), 256, 0, s>>>(a, 3));
     }
-    {
+    if (cap[4]) {
       ProfScope ps("lp_choose_warp", s);
-      if (cap[4]) {
+      {
         const size_t sm = kWarpsPerBlock * kWarpCap * 16;
-        k_choose_warp<EW, LQ><<<grid_for(cap[4], kWarpsPerBlock, warp_grid_cap), kWarpsPerBlock * 32, sm, s>>>(a);
+        (::gp::count_launch(), k_choose_warp<EW, LQ><<<grid_for(cap[4], kWarpsPerBlock, warp_grid_cap), kWarpsPerBlock * 32, sm, s>>>(a));
       }
     }
-    {
+    if (cap[5]) {
       ProfScope ps("lp_choose_cta", s);
-      if (cap[5]) k_choose_cta<EW, LQ><<<grid_for(cap[5], 1, nsm * 3), kCtaThreads, kCtaCap * 16, s>>>(a);
+      (::gp::count_launch(), k_choose_cta<EW, LQ><<<grid_for(cap[5], 1, nsm * 3), kCtaThreads, kCtaCap * 16, s>>>(a));
     }
     if (cap[6]) {
       ProfScope ps("lp_choose_hub", s);
-      k_hub_prefix<<<1, 1024, 0, s>>>(a);
-      k_hub_accum<EW, LQ><<<nsm * 4, 256, 0, s>>>(a);
-      k_hub_choose<LQ><<<grid_for(cap[6], 1, nsm * 4), 256, 0, s>>>(a);
+      (::gp::count_launch(), k_hub_prefix<<<1, 1024, 0, s>>>(a));
+      (::gp::count_launch(), k_hub_accum<EW, LQ><<<nsm * 4, 256, 0, s>>>(a));
+      (::gp::count_launch(), k_hub_choose<LQ><<<grid_for(cap[6], 1, nsm * 4), 256, 0, s>>>(a));
     }
     GP_LAUNCH_CHECK();
     const int64_t mv_cap = a.g.n;
     const int ag = grid_for(mv_cap, 256, nsm * 8);
-    k_demand<<<ag, 256, 0, s>>>(a);
-    k_admit<LQ><<<ag, 256, 0, s>>>(a);
-    k_contest_small<<<1, 1024, 0, s>>>(a);
+    (::gp::count_launch(), k_demand<<<ag, 256, 0, s>>>(a));
+    (::gp::count_launch(), k_admit<LQ><<<ag, 256, 0, s>>>(a));
+    (::gp::count_launch(), k_contest_small<<<1, 1024, 0, s>>>(a));
     {
       LpArgs aa = a;
       void *params[] = {(void *)&aa, (void *)&bar};
+      count_launch();
       GP_CUDA(cudaLaunchCooperativeKernel((void *)k_contest_large<LQ>, coop_grid, 256, params, 0, s));
     }
-    k_apply<<<grid_for(mv_cap, 8, nsm * 8), 256, 0, s>>>(a);
+    (::gp::count_launch(), k_apply<<<grid_for(mv_cap, 8, nsm * 8), 256, 0, s>>>(a));
     GP_LAUNCH_CHECK();
     return GP_OK;
   }
@@ -1092,11 +1093,11 @@ int run_rounds(LpArgs a, const int64_t cap[kBins], int rounds, uint64_t seed, ui
     const uint64_t rmix = mix64(a.smix ^ (uint64_t)r);
     for (int sub = 0; sub < 2; sub++) {
       a.sub = sub;
-      k_sub_reset<<<1, 32, 0, s>>>(a.ctr);
-      k_classify<<<cls_grid, 256, 0, s>>>(a, rmix);
+      (::gp::count_launch(), k_sub_reset<<<1, 32, 0, s>>>(a.ctr));
+      (::gp::count_launch(), k_classify<<<cls_grid, 256, 0, s>>>(a, rmix));
       GP_TRY((LpKernels<EW, LQ>::launch_sub(a, cap, warp_grid_cap, s, bar, coop_grid)));
     }
-    k_round_end<<<1, 32, 0, s>>>(a.ctr);
+    (::gp::count_launch(), k_round_end<<<1, 32, 0, s>>>(a.ctr));
     GP_LAUNCH_CHECK();
   }
   return GP_OK;
@@ -1118,7 +1119,7 @@ int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, 
   GP_CUDA(cudaMemsetAsync(bw, 0, sizeof(int64_t) * (size_t)std::max<int64_t>(k, 1), s));
   if (g.n == 0) return GP_OK;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, num_sms() * 8));
-  k_block_weights<<<grid, 256, 0, s>>>(g, part, k, bw, bad_dev);
+  (::gp::count_launch(), k_block_weights<<<grid, 256, 0, s>>>(g, part, k, bw, bad_dev));
   GP_LAUNCH_CHECK();
   return GP_OK;
 }
@@ -1136,7 +1137,7 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
   GP_TRY(ws.zeros(&ctr, 1));
   const int nsm = num_sms();
   const int grid_n = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, nsm * 8));
-  k_degree_classes<<<grid_n, 256, 0, s>>>(g, cfg.deg_warp, cfg.deg_cta, ctr);
+  (::gp::count_launch(), k_degree_classes<<<grid_n, 256, 0, s>>>(g, cfg.deg_warp, cfg.deg_cta, ctr));
   GP_LAUNCH_CHECK();
   LpCounters h;
   GP_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1178,7 +1179,7 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
     GP_TRY(ws.get(&hub_of, n));
     GP_TRY(ws.get(&hub_cap, (size_t)cap[6] + 1));
     GP_TRY(ws.zeros(&hcount, 1));
-    k_hub_mark<<<grid_n, 256, 0, s>>>(g, cfg.deg_cta, hub_of, hub_cap, hcount);
+    (::gp::count_launch(), k_hub_mark<<<grid_n, 256, 0, s>>>(g, cfg.deg_cta, hub_of, hub_cap, hcount));
     GP_LAUNCH_CHECK();
     int64_t *hub_base, *total;
     GP_TRY(ws.get(&hub_base, (size_t)cap[6] + 1));

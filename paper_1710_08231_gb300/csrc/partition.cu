@@ -25,6 +25,7 @@ void set_allocator(gp_alloc_fn a, gp_free_fn f, void *ctx);
 const char *last_error();
 int prof_enable(int on);
 int prof_read(gp_profile_entry *out, int max_entries, int reset);
+long long launch_count(int reset);
 
 namespace {
 
@@ -198,8 +199,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       int64_t maxc = 0;
       GP_TRY(vertex_weight_stats(gl, &maxc, nullptr, s));
       const int64_t U = std::max<int64_t>(maxc, lmax / p.cluster_div);
-      k_iota<<<grid_n(gl.n), 256, 0, s>>>(labels, gl.n);
-      k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw);
+      (::gp::count_launch(), k_iota<<<grid_n(gl.n), 256, 0, s>>>(labels, gl.n));
+      (::gp::count_launch(), k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw));
       GP_LAUNCH_CHECK();
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
       gp_lp_stats ls;
@@ -370,7 +371,7 @@ int gp_validate_graph(const gp_graph *gd, gp_stream stream) {
   GP_TRY(ws.zeros(&err, 1));
   const DGraph g = make_dgraph(gd);
   if (g.n > 0) {
-    k_validate<<<grid_n(g.n), 256, 0, s>>>(g, err);
+    (::gp::count_launch(), k_validate<<<grid_n(g.n), 256, 0, s>>>(g, err));
     GP_LAUNCH_CHECK();
   }
   int h = 0;
@@ -416,8 +417,8 @@ int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, 
   int64_t *lw;
   GP_TRY(ws.get(&lw, (size_t)std::max<int64_t>(g.n, 1)));
   if (g.n > 0) {
-    k_iota<<<grid_n(g.n), 256, 0, s>>>(labels_out, g.n);
-    k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw);
+    (::gp::count_launch(), k_iota<<<grid_n(g.n), 256, 0, s>>>(labels_out, g.n));
+    (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
     GP_LAUNCH_CHECK();
   }
   GP_TRY(run_lp(g, edge_q, labels_out, lw, g.n, U, rounds, seed, stats, s, schedule_for(nullptr)));
@@ -545,6 +546,8 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta) {
   g_schedule.deg_cta = deg_cta;
   return GP_OK;
 }
+
+int64_t gp_launch_count(int reset) { return gp::launch_count(reset); }
 
 int gp_profile_enable(int on) { return gp::prof_enable(on); }
 int gp_profile_read(gp_profile_entry *out, int max_entries, int reset) {

@@ -147,6 +147,7 @@ def test_partition_matches_oracle(gp, name, k):
     assert np.array_equal(part.cpu().numpy(), part_o)
     assert (res.cut, res.max_block_weight, res.lmax, res.imbalanced, res.n_isolated) == (
         res_o.cut, res_o.max_block_weight, res_o.lmax, res_o.imbalanced, res_o.n_isolated)
+    assert res.lp_edges == res_o.lp_edges
 
 
 def test_partition_edge_cases(gp):
