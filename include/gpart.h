@@ -179,6 +179,23 @@ int gp_lp_cluster(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
                   const int32_t *edge_q, int32_t *labels_out, gp_lp_stats *stats,
                   gp_stream stream);
 
+/* gp_lp_cluster without any device allocation, for callers that cannot allocate device memory
+ * while they run (no cudaMalloc, no caching allocator, no allocator callback). The paper has no
+ * counterpart; this is a deployment variant of gp_lp_cluster with identical results.
+ *   Arguments, layout and results are those of gp_lp_cluster; the caller still owns the graph,
+ *   labels_out and stats.
+ *   Temporary buffers come from one fixed 16 MiB device array inside the library, which every
+ *   process that loads the library holds on each GPU it uses until exit. Graphs with
+ *   n > 32768 vertices or m_dir > 131072 CSR entries are rejected with GP_ERR_UNSUPPORTED.
+ *   The first call on a device looks the array's device address up (with that device current); make
+ *   that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents (every call clears what must
+ *   start at zero), so calls whose GPU work overlaps (other threads, other streams) race: serialise
+ *   them. */
+int gp_lp_cluster_noalloc(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
+                          const int32_t *edge_q, int32_t *labels_out, gp_lp_stats *stats,
+                          gp_stream stream);
+
 /* Degree-bin schedule of gp_lp_cluster and gp_lp_refine (process-wide): vertices with
  * 32 < d <= deg_warp are handled by one warp, deg_warp < d <= deg_cta by one CTA, larger ones by
  * several CTAs. 0 restores the defaults (128, 2048). deg_warp is clamped to [32, 256] and deg_cta to

@@ -68,6 +68,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, VP, SZ, VP, VP)
 _lib = None
 _lock = threading.Lock()
 _keep = []  # ctypes callbacks must outlive the library's use of them
+alloc_calls = [0]  # number of allocations the library requested through the installed allocator
 
 
 class GpError(RuntimeError):
@@ -105,6 +106,9 @@ def lib():
         L.gp_lmax.argtypes = [I64, I64, DBL]
         L.gp_lp_cluster.restype = ctypes.c_int
         L.gp_lp_cluster.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, VP, ctypes.POINTER(GpLpStats), VP]
+        L.gp_lp_cluster_noalloc.restype = ctypes.c_int
+        L.gp_lp_cluster_noalloc.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, VP,
+                                            ctypes.POINTER(GpLpStats), VP]
         L.gp_lp_refine.restype = ctypes.c_int
         L.gp_lp_refine.argtypes = [ctypes.POINTER(GpGraph), I32, I64, I32, U64, VP, VP, ctypes.POINTER(GpLpStats), VP]
         L.gp_contract.restype = ctypes.c_int
@@ -150,6 +154,7 @@ def _install_torch_allocator(L):
 
     @ALLOC_FN
     def _alloc(nbytes, stream, ctx):
+        alloc_calls[0] += 1
         try:
             return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
         except Exception:  # out of memory: report NULL, the library returns GP_ERR_OOM

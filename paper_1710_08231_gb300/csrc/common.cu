@@ -26,7 +26,20 @@ void set_allocator(gp_alloc_fn a, gp_free_fn f, void *ctx) {
   g_alloc_ctx = a ? ctx : nullptr;
 }
 
+// While a thread has an arena installed, its temporary allocations are carved from that fixed
+// device buffer (bump allocation, released all at once by the caller) instead of an allocator.
+static thread_local ScratchArena *t_arena = nullptr;
+void set_thread_arena(ScratchArena *a) { t_arena = a; }
+bool arena_active() { return t_arena != nullptr; }
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
+  if (t_arena) {
+    const size_t off = (t_arena->used + 255) & ~size_t(255);
+    if (off + bytes > t_arena->size) return nullptr;
+    t_arena->used = off + bytes;
+    if (t_arena->used > t_arena->high) t_arena->high = t_arena->used;
+    return t_arena->base + off;
+  }
   if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
   void *p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
@@ -37,7 +50,7 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
 }
 
 void dev_free(void *p, size_t bytes, cudaStream_t s) {
-  if (!p) return;
+  if (!p || t_arena) return;
   if (g_alloc) {
     if (g_free) g_free(p, bytes, s, g_alloc_ctx);
     return;
@@ -197,7 +210,7 @@ long long launch_count(int reset) {
 }
 
 ProfScope::ProfScope(const char *nm, cudaStream_t st) : name(nm), s(st), slot(-1) {
-  if (!g_prof_on) return;
+  if (!g_prof_on || t_arena) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   Pending p;
   p.entry = entry_index(nm);

@@ -33,6 +33,14 @@ void set_error(const std::string &msg);
 #define GP_LAUNCH_CHECK() GP_CUDA(cudaGetLastError())
 
 // ------------------------------------------------------------------------------------------ memory
+struct ScratchArena {
+  unsigned char *base;
+  size_t size;
+  size_t used;
+  size_t high;
+};
+void set_thread_arena(ScratchArena *a);
+bool arena_active();
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 
