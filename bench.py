@@ -254,8 +254,8 @@ def main():
     torch.cuda.synchronize()
     gp.profile_enable(False)
     prof = gp.profile_read(reset=True)
-    lp_entries = [e for e in prof if e["name"].startswith("lp_choose") and e["launches"] > 0]
-    top = max(lp_entries, key=lambda e: e["ms"]) if lp_entries else None
+    kernels = [e for e in prof if e["launches"] > 0 and e["bytes"] > 0 and not e["name"].startswith("lp_phase")]
+    top = max(kernels, key=lambda e: e["ms"]) if kernels else None
     peak, peak_kind = peaks()
     roofline = None
     if top:
@@ -263,11 +263,10 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": None, "kernel": top["name"], "launches": top["launches"],
                     "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
-                    "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"}
-        lp_all_ms = sum(e["ms"] for e in lp_entries)
-        lp_all_bytes = sum(e["bytes"] for e in lp_entries)
-        roofline["lp_scan_all"] = {"ms_per_step": lp_all_ms / args.steps,
-                                   "achieved_gbs": lp_all_bytes / (lp_all_ms * 1e-3) / 1e9 if lp_all_ms else None}
+                    "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                    "kernels_ms_per_step": {e["name"]: e["ms"] / args.steps for e in prof if e["launches"] > 0 and not e["name"].startswith("lp_phase")},
+                    "lp_phases_ms_per_step": {e["name"][9:]: e["ms"] / args.steps for e in prof if e["name"].startswith("lp_phase")},
+                    "contest_calls_per_step": {e["name"][11:-6]: e["items"] / args.steps for e in prof if e["name"].startswith("lp_contest")}}
 
     # ---- pass C: end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None

@@ -198,8 +198,8 @@ int gp_lp_cluster_noalloc(const gp_graph *g, int64_t U, int32_t rounds, uint64_t
 
 /* Degree-bin schedule of gp_lp_cluster and gp_lp_refine (process-wide): vertices with
  * 32 < d <= deg_warp are handled by one warp, deg_warp < d <= deg_cta by one CTA, larger ones by
- * several CTAs. 0 restores the defaults (128, 2048). deg_warp is clamped to [32, 256] and deg_cta to
- * [deg_warp, 2048]. The schedule never changes results. gp_partition uses params.deg_warp/deg_cta
+ * several CTAs. 0 restores the defaults (128, 1024). deg_warp is clamped to [32, 128] and deg_cta to
+ * [deg_warp, 1024]. The schedule never changes results. gp_partition uses params.deg_warp/deg_cta
  * when non-zero, else this schedule. */
 int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta);
 

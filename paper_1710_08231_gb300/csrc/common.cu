@@ -236,6 +236,14 @@ void prof_add_counts(const char *name, int64_t items, int64_t edges, int64_t byt
   e.bytes += bytes;
 }
 
+void prof_add_time(const char *name, double ms) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfEntry &e = g_entries[entry_index(name)];
+  e.ms += ms;
+  e.launches += 1;
+}
+
 int prof_flush(cudaStream_t s) {
   if (!g_prof_on) return GP_OK;
   GP_CUDA(cudaStreamSynchronize(s));

@@ -20,9 +20,12 @@ namespace gp {
 
 namespace {
 
-constexpr int kRowSmall = 32;
-constexpr int kRowMedium = 4096;
+constexpr int kRowSmall = 32;     // <= 32 pairs: one warp, registers
+constexpr int kRowWarp = 256;     // <= 256 pairs: one warp, shared-memory hash
+constexpr int kRowMedium = 4096;  // <= 4096 pairs: one CTA, shared-memory hash
 constexpr int kRowThreads = 256;
+constexpr int kWarpSlots = 2 * kRowWarp;
+constexpr int kCtaSlots = 2 * kRowMedium;
 
 __global__ void k_mark_used(const int32_t *labels, int64_t n, int64_t nl, uint32_t *used, int *bad) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -55,17 +58,17 @@ __global__ void k_members(int64_t n, const int32_t *f2c, const int64_t *mstart, 
   }
 }
 
-__global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2,
+__global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2, int32_t *l3,
                                unsigned *counts) {
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = base + threadIdx.x;
     int b = -1;
     if (c < nc) {
       const int64_t D = dsum[c];
-      b = D <= kRowSmall ? 0 : (D <= kRowMedium ? 1 : 2);
+      b = D <= kRowSmall ? 0 : (D <= kRowWarp ? 3 : (D <= kRowMedium ? 1 : 2));
     }
-    int32_t *lists[3] = {l0, l1, l2};
-    for (int bb = 0; bb < 3; bb++) {
+    int32_t *lists[4] = {l0, l1, l2, l3};
+    for (int bb = 0; bb < 4; bb++) {
       const unsigned m = __ballot_sync(kFull, b == bb);
       if (!m) continue;
       const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
@@ -88,6 +91,7 @@ struct RowArgs {
   int64_t *rowcnt;
   const int32_t *list;
   const unsigned *count;
+  const int64_t *dsum;
   // large rows
   const int64_t *lofs;
   int32_t *ka, *kb;
@@ -238,47 +242,162 @@ __device__ int block_reduce_runs(const int32_t *ks, const long long *vs, int P, 
   return r;
 }
 
-// Rows with 32 < pairs <= 4096: one CTA stages the pairs in shared memory and sorts them there.
+__device__ __forceinline__ unsigned row_slot(int cu) { return (unsigned)cu * 0x9E3779B1u; }
+
+// Rows with 32 < pairs <= 256: one warp sums the pairs by neighbour id in a shared-memory hash
+// table, compacts the distinct ids and sorts them (bitonic) before writing the row.
+template <int EW>
+__global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  long long *vals = reinterpret_cast<long long *>(smem) + wid * kWarpSlots;
+  int *keys = reinterpret_cast<int *>(smem + (kRowThreads / 32) * kWarpSlots * 8) + wid * kWarpSlots;
+  for (int t = lane; t < kWarpSlots; t += 32) {
+    keys[t] = -1;
+    vals[t] = 0;
+  }
+  __syncwarp();
+  const unsigned cnt = *a.count;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned i = gw; i < cnt; i += nw) {
+    const int cv = a.list[i];
+    const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
+    int cap = 64;
+    while (cap < 2 * a.dsum[cv]) cap <<= 1;
+    const unsigned mask = (unsigned)cap - 1;
+    for (int64_t m = mb; m < me; m++) {
+      const int v = a.members[m];
+      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
+      for (int64_t x = b + lane; x < e; x += 32) {
+        const int cu = a.f2c[__ldg(a.g.adj + x)];
+        if (cu == cv) continue;
+        const long long w = load_ew<EW>(a.g.ew, x);
+        unsigned sl = row_slot(cu) & mask;
+        while (true) {
+          const int k = atomicCAS(&keys[sl], -1, cu);
+          if (k == -1 || k == cu) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&vals[sl]), (unsigned long long)w);
+            break;
+          }
+          sl = (sl + 1) & mask;
+        }
+      }
+    }
+    __syncwarp();
+    // compact the used slots to the front (every lane reads its slot before anyone writes)
+    int u = 0;
+    for (int c0 = 0; c0 < cap; c0 += 32) {
+      const int k = keys[c0 + lane];
+      const long long val = vals[c0 + lane];
+      const unsigned hm = __ballot_sync(kFull, k >= 0);
+      __syncwarp();
+      if (k >= 0) {
+        const int pos = u + __popc(hm & lanemask_lt());
+        keys[pos] = k;
+        vals[pos] = val;
+      }
+      u += __popc(hm);
+      __syncwarp();
+    }
+    int Pp = 1;
+    while (Pp < u) Pp <<= 1;
+    for (int t = u + lane; t < cap; t += 32) {
+      keys[t] = t < Pp ? INT_MAX : -1;
+      vals[t] = 0;
+    }
+    __syncwarp();
+    for (int k = 2; k <= Pp; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < Pp / 2; t += 32) {
+          const int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
+          const bool up = (lo & k) == 0;
+          const int x = keys[lo], y = keys[hi];
+          if ((x > y) == up && x != y) {
+            keys[lo] = y;
+            keys[hi] = x;
+            const long long vx = vals[lo];
+            vals[lo] = vals[hi];
+            vals[hi] = vx;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    const int64_t dst = a.tstart[cv];
+    for (int t = lane; t < u; t += 32) {
+      a.okey[dst + t] = keys[t];
+      a.oval[dst + t] = vals[t];
+    }
+    if (lane == 0) a.rowcnt[cv] = u;
+    __syncwarp();
+    for (int t = lane; t < Pp; t += 32) {
+      keys[t] = -1;
+      vals[t] = 0;
+    }
+    __syncwarp();
+  }
+}
+
+// Rows with 256 < pairs <= 4096: the same with one CTA and a larger table.
 template <int EW>
 __global__ void __launch_bounds__(kRowThreads) k_row_cta(RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  long long *sval = reinterpret_cast<long long *>(smem);
-  int *skey = reinterpret_cast<int *>(smem + kRowMedium * 8);
-  __shared__ unsigned sP;
+  long long *vals = reinterpret_cast<long long *>(smem);
+  int *keys = reinterpret_cast<int *>(smem + kCtaSlots * 8);
+  __shared__ long long tmp[32];
+  __shared__ long long tot_s, carry_s;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < kCtaSlots; t += blockDim.x) {
+    keys[t] = -1;
+    vals[t] = 0;
+  }
+  __syncthreads();
   const unsigned cnt = *a.count;
   for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int cv = a.list[i];
     const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
-    if (threadIdx.x == 0) sP = 0;
-    __syncthreads();
+    int cap = 64;
+    while (cap < 2 * a.dsum[cv]) cap <<= 1;
+    const unsigned mask = (unsigned)cap - 1;
     for (int64_t m = mb + wid; m < me; m += nwarps) {
       const int v = a.members[m];
       const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
-      for (int64_t x = b; x < e; x += 32) {
-        const int64_t j = x + lane;
-        const bool valid = j < e;
-        const int cu = valid ? a.f2c[__ldg(a.g.adj + j)] : -1;
-        const bool keep = valid && cu != cv;
-        const unsigned mask = __ballot_sync(kFull, keep);
-        if (!mask) continue;
-        const int leader = __ffs(mask) - 1;
-        unsigned pos = 0;
-        if (lane == leader) pos = atomicAdd(&sP, (unsigned)__popc(mask));
-        pos = __shfl_sync(kFull, pos, leader) + __popc(mask & lanemask_lt());
-        if (keep) {
-          skey[pos] = cu;
-          sval[pos] = load_ew<EW>(a.g.ew, j);
+      for (int64_t x = b + lane; x < e; x += 32) {
+        const int cu = a.f2c[__ldg(a.g.adj + x)];
+        if (cu == cv) continue;
+        const long long w = load_ew<EW>(a.g.ew, x);
+        unsigned sl = row_slot(cu) & mask;
+        while (true) {
+          const int k = atomicCAS(&keys[sl], -1, cu);
+          if (k == -1 || k == cu) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&vals[sl]), (unsigned long long)w);
+            break;
+          }
+          sl = (sl + 1) & mask;
         }
       }
     }
+    if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    const int P = (int)sP;
+    for (int c0 = 0; c0 < cap; c0 += blockDim.x) {
+      const int t = c0 + threadIdx.x;
+      const int k = t < cap ? keys[t] : -1;
+      const long long val = t < cap ? vals[t] : 0;
+      const long long ex = block_excl_scan64((long long)(k >= 0 ? 1 : 0), tmp, &tot_s);
+      if (k >= 0) {
+        keys[carry_s + ex] = k;
+        vals[carry_s + ex] = val;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) carry_s += tot_s;
+      __syncthreads();
+    }
+    const int u = (int)carry_s;
     int Pp = 1;
-    while (Pp < P) Pp <<= 1;
-    for (int t = P + threadIdx.x; t < Pp; t += blockDim.x) {
-      skey[t] = INT_MAX;
-      sval[t] = 0;
+    while (Pp < u) Pp <<= 1;
+    for (int t = u + threadIdx.x; t < cap; t += blockDim.x) {
+      keys[t] = t < Pp ? INT_MAX : -1;
+      vals[t] = 0;
     }
     __syncthreads();
     for (int k = 2; k <= Pp; k <<= 1) {
@@ -286,20 +405,29 @@ __global__ void __launch_bounds__(kRowThreads) k_row_cta(RowArgs a) {
         for (int t = threadIdx.x; t < Pp / 2; t += blockDim.x) {
           const int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
           const bool up = (lo & k) == 0;
-          const int x = skey[lo], y = skey[hi];
+          const int x = keys[lo], y = keys[hi];
           if ((x > y) == up && x != y) {
-            skey[lo] = y;
-            skey[hi] = x;
-            const long long vx = sval[lo];
-            sval[lo] = sval[hi];
-            sval[hi] = vx;
+            keys[lo] = y;
+            keys[hi] = x;
+            const long long vx = vals[lo];
+            vals[lo] = vals[hi];
+            vals[hi] = vx;
           }
         }
         __syncthreads();
       }
     }
-    const int u = block_reduce_runs(skey, sval, P, a.okey, a.oval, a.tstart[cv]);
+    const int64_t dst = a.tstart[cv];
+    for (int t = threadIdx.x; t < u; t += blockDim.x) {
+      a.okey[dst + t] = keys[t];
+      a.oval[dst + t] = vals[t];
+    }
     if (threadIdx.x == 0) a.rowcnt[cv] = u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < Pp; t += blockDim.x) {
+      keys[t] = -1;
+      vals[t] = 0;
+    }
     __syncthreads();
   }
 }
@@ -389,7 +517,7 @@ void set_smem(K kernel, int bytes) {
 }
 
 template <int EW>
-int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[3], int32_t *lists[3], cudaStream_t s) {
+int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[4], int32_t *lists[4], cudaStream_t s) {
   const int nsm = num_sms();
   auto grid_for = [&](int64_t items, int per_block, int limit) {
     int64_t g = (items + per_block - 1) / per_block;
@@ -402,13 +530,21 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[3], 
     b.count = counts_dev + 0;
     (::gp::count_launch(), k_row_warp<EW><<<grid_for(counts[0], 8, nsm * 16), 256, 0, s>>>(b));
   }
+  if (counts[3]) {
+    RowArgs b = a;
+    b.list = lists[3];
+    b.count = counts_dev + 3;
+    const int sm = (kRowThreads / 32) * kWarpSlots * 12;
+    set_smem(k_row_whash<EW>, sm);
+    (::gp::count_launch(), k_row_whash<EW><<<grid_for(counts[3], 8, nsm * 4), kRowThreads, sm, s>>>(b));
+  }
   if (counts[1]) {
     RowArgs b = a;
     b.list = lists[1];
     b.count = counts_dev + 1;
-    const int sm = kRowMedium * 12;
+    const int sm = kCtaSlots * 12;
     set_smem(k_row_cta<EW>, sm);
-    (::gp::count_launch(), k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 4), kRowThreads, sm, s>>>(b));
+    (::gp::count_launch(), k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 2), kRowThreads, sm, s>>>(b));
   }
   if (counts[2]) {
     RowArgs b = a;
@@ -496,11 +632,11 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_TRY(ws.get(&members, (size_t)n));
   (::gp::count_launch(), k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members));
   // 4. rows binned by pair count
-  int32_t *lists[3];
+  int32_t *lists[4];
   unsigned *counts_dev;
-  for (int b = 0; b < 3; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
+  for (int b = 0; b < 4; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
   GP_TRY(ws.zeros(&counts_dev, 4));
-  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], counts_dev));
+  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], lists[3], counts_dev));
   GP_LAUNCH_CHECK();
   unsigned counts[4];
   GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
@@ -511,6 +647,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   a.mstart = mstart;
   a.members = members;
   a.tstart = tstart;
+  a.dsum = dsum;
   a.lofs = nullptr;
   a.ka = a.kb = nullptr;
   a.va = a.vb = nullptr;

@@ -194,12 +194,23 @@ __device__ __forceinline__ T block_excl_scan64(T x, T *tmp, T *total) {
   return r;
 }
 
-// Bounded grid-wide barrier for kernels launched cooperatively (all blocks co-resident).
-// Gives up after `limit` polls, sets *err = GP_ERR_TIMEOUT and returns false.
+// Bounded two-level barrier over `nblocks` blocks of a cooperatively launched kernel (all blocks
+// co-resident). Blocks arrive on one counter per group of kBarrierGroup blocks; the last block of a
+// group arrives on the root counter; the last root arrival advances `gen`, on which everyone waits.
+// Counters are kBarrierStride words apart (separate cache lines). `err` receives GP_ERR_TIMEOUT when
+// a wait gives up (about 2^24 polls), in which case every waiting block returns false.
+constexpr unsigned kBarrierGroup = 16;
+constexpr unsigned kBarrierStride = 32;
+inline unsigned barrier_words(unsigned nblocks) {
+  return ((nblocks + kBarrierGroup - 1) / kBarrierGroup + 1) * kBarrierStride;
+}
+
 struct GridBarrier {
-  unsigned int *count;
+  unsigned int *count;  // barrier_words(nblocks) words, zero-initialised
   unsigned int *gen;
   int *err;
+  unsigned int nblocks;
+  unsigned int rank;    // this block's index among the nblocks
 };
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
@@ -208,22 +219,31 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
   if (threadIdx.x == 0) {
     s_ok = 1;
     volatile unsigned int *vgen = b.gen;
-    unsigned int my = *vgen;
+    const unsigned int my = *vgen;
     __threadfence();
-    unsigned int arrived = atomicAdd(b.count, 1u);
-    if (arrived == gridDim.x * gridDim.y - 1) {
-      *b.count = 0;
+    const unsigned ngroups = (b.nblocks + kBarrierGroup - 1) / kBarrierGroup;
+    const unsigned g = b.rank / kBarrierGroup;
+    const unsigned gsize = min(kBarrierGroup, b.nblocks - g * kBarrierGroup);
+    bool last = false;
+    if (atomicAdd(&b.count[g * kBarrierStride], 1u) == gsize - 1) {
+      b.count[g * kBarrierStride] = 0;
+      if (atomicAdd(&b.count[ngroups * kBarrierStride], 1u) == ngroups - 1) {
+        b.count[ngroups * kBarrierStride] = 0;
+        last = true;
+      }
+    }
+    if (last) {
       __threadfence();
       atomicAdd(b.gen, 1u);
     } else {
       long long polls = 0;
       while (*vgen == my) {
-        if (++polls > (1ll << 26) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
+        if (++polls > (1ll << 24) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
           atomicExch(b.err, GP_ERR_TIMEOUT);
           s_ok = 0;
           break;
         }
-        __nanosleep(32);
+        if (polls > 256) __nanosleep(32);
       }
     }
     __threadfence();
@@ -251,6 +271,7 @@ struct ProfScope {
   int slot;
 };
 void prof_add_counts(const char *name, int64_t items, int64_t edges, int64_t bytes);
+void prof_add_time(const char *name, double ms);  // device time measured inside a kernel
 int prof_flush(cudaStream_t s);  // resolve recorded events (synchronises s)
 
 }  // namespace gp

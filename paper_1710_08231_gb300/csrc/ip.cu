@@ -58,12 +58,14 @@ __device__ void set_bfs(const IpArgs &a, int32_t *part, int32_t *gk, int32_t *di
   while (nf > 0) {
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    // one warp per frontier vertex, lanes over its row
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nf; i += nw) {
       const int x = qa[i];
       const int px = part[x];
       const int dx = dist[x];
       const int64_t b = a.g.row_begin(x), e = a.g.row_begin(x + 1);
-      for (int64_t j = b; j < e; j++) {
+      for (int64_t j = b + lane; j < e; j += 32) {
         const int u = a.g.adj[j];
         if (gk[u] <= 1 || part[u] != px) continue;
         if (atomicCAS(&dist[u], -1, dx + 1) == -1) qb[atomicAdd(&s_next, 1)] = u;

@@ -1,29 +1,30 @@
-// lp.cu -- size-constrained label propagation on the GPU.
+// lp.cu -- size-constrained label propagation on the GPU: one persistent cooperative kernel per call.
 //
 // Method: Section III-A ("Clustering") and Section IV-A ("Parallel Size-Constraint Label
 // Propagation") of "High-Quality Shared-Memory Graph Partitioning"; as refinement with U = Lmax in
-// Section III-C / IV-C. A vertex moves to the eligible cluster of strongest connection; a cluster
-// is eligible when it stays within U after the move; neighbours of moved vertices are visited in
-// the next iteration.
+// Section III-C / IV-C. A vertex moves to the eligible cluster of strongest connection; a cluster is
+// eligible when it stays within U after the move; neighbours of moved vertices are visited in the
+// next iteration.
 //
 // GPU design (what replaces the paper's degree sort, TBB work packets and CAS on cluster sizes):
-//   * each round has two Jacobi sub-rounds split by the hash bit H(seed, r, v) >> 63; all decisions
-//     of a sub-round read the labels and label weights of its start, which makes the result
-//     independent of scheduling;
-//   * active vertices are classified into degree bins (group of 4/8/16/32 lanes, one warp with a
-//     shared-memory hash table, one CTA with a shared-memory hash table, several CTAs with a
-//     global-memory hash table); the bins only schedule work, the chosen label is the same;
+//   * each round has two Jacobi sub-rounds split by the hash bit H(seed, r, v) >> 63; all decisions of
+//     a sub-round read the labels and label weights of its start, so the result does not depend on
+//     the schedule;
+//   * one cooperative launch runs every round of an LP call. The blocks of a "problem" (one LP run;
+//     several independent runs can share a launch) meet at bounded barriers between the phases of a
+//     sub-round: classify -> aggregate+choose -> admission -> apply;
+//   * active vertices are binned by degree: groups of 4/8/16/32 lanes (labels aggregated with
+//     __match_any_sync), one warp with a shared-memory hash table, one CTA with a shared-memory hash
+//     table, or several CTAs with a global-memory hash table for hubs;
 //   * connection sums are exact integers and the choice is a total order (connection, score sum,
 //     H(seed, v, L), -L), so the aggregation order never matters;
-//   * moves to one target are admitted by a deterministic rule instead of CAS: all proposals to
-//     the target are ordered by (gain desc, score sum desc, id asc) and the longest prefix whose
-//     weight fits under U is taken. When the total proposed weight fits, no ordering is needed;
-//     otherwise the contested proposals are sorted (one CTA in shared memory for small sets, a
-//     cooperative LSD radix sort for large ones) and admitted by a segmented prefix sum.
-#include <cooperative_groups.h>
-
+//   * admission is deterministic instead of CAS: proposals to one target are ordered by (gain desc,
+//     score sum desc, id asc) and the longest prefix fitting under U is taken. When all proposals to a
+//     target fit, no order is needed; otherwise the contested proposals are sorted (one CTA in shared
+//     memory up to 4096, else a cooperative LSD radix sort) and admitted by a segmented prefix sum.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "lp.cuh"
 
@@ -31,62 +32,69 @@ namespace gp {
 
 namespace {
 
-constexpr int kBins = 7;  // G4, G8, G16, G32, WARP, CTA, HUB
+constexpr int kBins = 7;     // G4, G8, G16, G32, WARP, CTA, HUB
 constexpr int kBinZero = 7;  // degree-0 visits (statistics only)
-constexpr int kWarpCap = 512;   // slots of a warp table (d <= 256)
-constexpr int kCtaCap = 4096;   // slots of a CTA table (d <= 2048)
-constexpr int kCtaThreads = 256;
-constexpr int kWarpsPerBlock = 8;
-constexpr int kHubChunk = 4096;  // CSR entries per hub work item
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpCap = 256;   // table slots per warp (d <= 128)
+constexpr int kCtaCap = 2048;   // table slots per CTA (d <= 1024)
+constexpr int kHubChunk = 4096; // CSR entries per hub work item
 constexpr int kContestSmall = 4096;
-constexpr int kSmallLabels = 2048;  // label spaces this small are aggregated in shared memory
+constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
+static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
+static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
 
-struct LpCounters {
+struct SubCounters {
   unsigned int bin_count[8];
   unsigned int n_movers;
   unsigned int n_contested;
-  unsigned int stop;
-  int err;
   unsigned int hub_chunks;
-  unsigned int bar_count, bar_gen;
   unsigned int pad;
-  unsigned long long moves_round;
-  unsigned long long moves, rounds, movers;
-  unsigned long long bin_visits[8], bin_edges[8];
   unsigned long long max_gain, max_q;
 };
 
-struct LpArgs {
+struct LpCounters {
+  SubCounters sc[2];                  // by sub-round parity
+  unsigned long long moves_round[2];  // by round parity
+  unsigned long long moves, rounds, movers;
+  unsigned long long bin_visits[8], bin_edges[8];
+  unsigned long long phase_ns[8];  // classify, choose, hubs, admit, contest, apply (block 0's view)
+  unsigned long long contest_small, contest_packed, contest_large;
+  unsigned int bar_count, bar_gen;
+  int err;
+  int pad;
+};
+
+struct LpProblem {
   DGraph g;
-  int64_t nl;
-  int64_t U;
+  int64_t nl, U;
   uint64_t smix;  // mix64(seed)
+  int rounds;
+  int has_hubs;
+  int deg_warp, deg_cta;
+  int block_begin, block_count;
   int32_t *labels;
   int64_t *lw;
-  const uint8_t *act;
-  uint8_t *act_next;
-  int round, sub;
-  int deg_warp, deg_cta;
   const int32_t *q;
+  uint8_t *act[2];
   int32_t *bin[kBins];
-  int32_t *mv_v;
-  int32_t *mv_t;
-  int64_t *mv_gain;
-  int64_t *mv_q;
+  int64_t bin_base[kBins];  // proposal slot of bin position i is bin_base[b] + i
+  int32_t *mv_v, *mv_t;
+  int64_t *mv_gain, *mv_q;
   uint8_t *mv_adm;
+  int32_t *mv_of_v;  // vertex -> its proposal index in the current sub-round
   int64_t *demand;
   uint32_t *ct, *ct2;
-  // hub tables
-  const int32_t *hub_of;   // vertex -> hub index, -1 otherwise
-  const int64_t *hub_base; // hub index -> first slot
+  const int32_t *hub_of;
+  const int64_t *hub_base;
   int32_t *hub_keys;
   unsigned long long *hub_vals;
   unsigned int *hub_qv;
-  long long *hub_c0;       // per active hub (bin position): connection to the own label
-  unsigned int *hub_prefix;  // per active hub: exclusive prefix of work chunks
-  // cooperative sort scratch
-  unsigned int *hist;   // nblocks * 256
-  unsigned long long *hoff;  // nblocks * 256
+  long long *hub_c0;
+  unsigned int *hub_prefix;
+  unsigned int *hist;        // block_count * 256
+  unsigned long long *hoff;  // block_count * 256 + 256
+  unsigned int *bar;         // barrier_words(block_count)
   LpCounters *ctr;
 };
 
@@ -101,7 +109,7 @@ __device__ __forceinline__ int bin_of(int64_t d, int deg_warp, int deg_cta) {
 }
 
 __device__ __forceinline__ unsigned warp_append(unsigned int *counter, bool pred) {
-  unsigned m = __ballot_sync(kFull, pred);
+  const unsigned m = __ballot_sync(kFull, pred);
   if (!m) return 0;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(m) - 1;
@@ -111,6 +119,19 @@ __device__ __forceinline__ unsigned warp_append(unsigned int *counter, bool pred
   return base + __popc(m & lanemask_lt());
 }
 
+// Warp-aggregated arr[key] += val for the lanes with `on` (all lanes of the warp must call).
+__device__ __forceinline__ void warp_add_by_key(int64_t *arr, bool on, int key, long long val) {
+  if (!__any_sync(kFull, on)) return;
+  const int k = on ? key : -1;
+  const unsigned peers = __match_any_sync(kFull, k);
+  if (on) {
+    long long s = 0;
+    for (unsigned m = peers; m; m &= m - 1) s += __shfl_sync(peers, val, __ffs(m) - 1);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicAdd(reinterpret_cast<unsigned long long *>(&arr[key]), (unsigned long long)s);
+  }
+}
+
 // ------------------------------------------------------------------------------------ candidates
 struct Best {
   long long conn;
@@ -118,6 +139,15 @@ struct Best {
   unsigned long long h;
   int L;  // -1: none
 };
+
+__device__ __forceinline__ Best no_best() {
+  Best b;
+  b.conn = 0;
+  b.qs = 0;
+  b.h = 0;
+  b.L = -1;
+  return b;
+}
 
 __device__ __forceinline__ bool better(const Best &a, const Best &b) {
   if (a.L < 0) return false;
@@ -148,197 +178,251 @@ __device__ __forceinline__ Best group_best(Best b) {
   return b;
 }
 
-// Candidate L of vertex v (connection conn, score sum qs) against own-label connection c0.
-__device__ __forceinline__ Best make_cand(const LpArgs &a, int v, int L, int L0, long long conn,
-                                          long long qs, long long c0, long long cv) {
+// Candidate L of vertex v (connection conn, score sum qs) against the own-label connection c0.
+__device__ __forceinline__ Best make_cand(const LpProblem &P, int v, int L, int L0, long long conn, long long qs,
+                                          long long c0, long long cv) {
+  if (L < 0 || L == L0 || conn <= c0) return no_best();  // the own label wins ties
+  if (P.lw[L] + cv > P.U) return no_best();             // not eligible
   Best b;
-  b.L = -1;
-  b.conn = 0;
-  b.qs = 0;
-  b.h = 0;
-  if (L < 0 || L == L0 || conn <= c0) return b;  // own label wins ties
-  if (a.lw[L] + cv > a.U) return b;               // not eligible
   b.L = L;
   b.conn = conn;
   b.qs = qs;
-  b.h = mix64(mix64(a.smix ^ (uint64_t)(uint32_t)v) ^ (uint64_t)(uint32_t)L);
+  b.h = mix64(mix64(P.smix ^ (uint64_t)(uint32_t)v) ^ (uint64_t)(uint32_t)L);
   return b;
 }
 
-__device__ __forceinline__ void write_mover(const LpArgs &a, unsigned idx, int v, const Best &b,
-                                            long long c0) {
-  a.mv_v[idx] = v;
-  a.mv_t[idx] = b.L;
-  a.mv_gain[idx] = b.conn - c0;
-  a.mv_q[idx] = b.qs;
-  a.mv_adm[idx] = 0;
-}
-
-// ------------------------------------------------------------------------------------ kernels
-__global__ void k_degree_classes(DGraph g, int deg_warp, int deg_cta, LpCounters *ctr) {
-  __shared__ unsigned int cnt[8];
-  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    int64_t d = g.row_begin(v + 1) - g.row_begin(v);
-    if (d > 0) atomicAdd(&cnt[bin_of(d, deg_warp, deg_cta)], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(&ctr->bin_count[threadIdx.x], cnt[threadIdx.x]);
-}
-
-__global__ void k_sub_reset(LpCounters *ctr) {
-  if (ctr->stop) return;
-  if (threadIdx.x < 8) ctr->bin_count[threadIdx.x] = 0;
-  if (threadIdx.x == 0) {
-    ctr->n_movers = 0;
-    ctr->n_contested = 0;
-    ctr->hub_chunks = 0;
-    ctr->max_gain = 0;
-    ctr->max_q = 0;
-  }
-}
-
-__global__ void k_round_end(LpCounters *ctr) {
-  if (threadIdx.x != 0 || ctr->stop) return;
-  ctr->rounds += 1;
-  ctr->moves += ctr->moves_round;
-  if (ctr->moves_round == 0) ctr->stop = 1;
-  ctr->moves_round = 0;
-}
-
-__global__ void k_classify(LpArgs a, uint64_t rmix) {
-  if (a.ctr->stop) return;
-  __shared__ unsigned long long s_vis[8], s_edg[8];
-  if (threadIdx.x < 8) {
-    s_vis[threadIdx.x] = 0;
-    s_edg[threadIdx.x] = 0;
-  }
-  __syncthreads();
-  const int64_t n = a.g.n;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = base + threadIdx.x;
-    int b = -1;
-    int64_t d = 0;
-    if (v < n) {
-      bool act = (a.round == 0 || a.act[v]) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == a.sub;
-      if (act) {
-        d = a.g.row_begin(v + 1) - a.g.row_begin(v);
-        b = d == 0 ? kBinZero : bin_of(d, a.deg_warp, a.deg_cta);
-        atomicAdd(&s_vis[b], 1ull);
-        atomicAdd(&s_edg[b], (unsigned long long)d);
-      }
-    }
-#pragma unroll
-    for (int bb = 0; bb < kBins; bb++) {
-      unsigned pos = warp_append(&a.ctr->bin_count[bb], b == bb);
-      if (b == bb) a.bin[bb][pos] = (int32_t)v;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    if (s_vis[threadIdx.x]) atomicAdd(&a.ctr->bin_visits[threadIdx.x], s_vis[threadIdx.x]);
-    if (s_edg[threadIdx.x]) atomicAdd(&a.ctr->bin_edges[threadIdx.x], s_edg[threadIdx.x]);
-  }
-}
-
-// Groups of G lanes, one vertex per group, d <= G: every lane holds one neighbour and computes the
-// connection of its neighbour's label by comparing with all other lanes of the group.
-template <int G, int EW, bool LQ>
-__global__ void __launch_bounds__(256) k_choose_group(LpArgs a, int bin) {
-  if (a.ctr->stop) return;
-  const unsigned cnt = a.ctr->bin_count[bin];
-  const int32_t *list = a.bin[bin];
-  constexpr unsigned kGpw = 32 / G;
-  const int lane = threadIdx.x & (G - 1);
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-  const unsigned sub = (threadIdx.x & 31) / G;
-  for (unsigned base = gw * kGpw; base < cnt; base += nw * kGpw) {
-    const unsigned i = base + sub;
-    const bool valid = i < cnt;
-    const int v = valid ? list[i] : 0;
-    int64_t beg = 0, d = 0;
-    if (valid) {
-      beg = a.g.row_begin(v);
-      d = a.g.row_begin(v + 1) - beg;
-    }
-    const bool has = lane < d;
-    int Lu = -1;
-    long long w = 0;
-    int qq = 0;
-    if (has) {
-      const int u = __ldg(a.g.adj + beg + lane);
-      Lu = a.labels[u];
-      w = load_ew<EW>(a.g.ew, beg + lane);
-      if (LQ) qq = __ldg(a.q + beg + lane);
-    }
-    const int L0 = valid ? a.labels[v] : -2;
-    long long c0 = (has && Lu == L0) ? w : 0;
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) c0 += __shfl_xor_sync(kFull, c0, o, G);
-    long long conn = 0, qs = 0;
-    bool first = true;
-#pragma unroll
-    for (int j = 0; j < G; j++) {
-      const int Lj = __shfl_sync(kFull, Lu, j, G);
-      long long wj;
-      if constexpr (EW == 0) wj = 1;
-      else wj = __shfl_sync(kFull, w, j, G);
-      int qj = 0;
-      if constexpr (LQ) qj = __shfl_sync(kFull, qq, j, G);
-      if (Lj == Lu) {
-        conn += wj;
-        qs += qj;
-        if (j < lane) first = false;
-      }
-    }
-    Best b;
-    b.L = -1;
-    b.conn = b.qs = 0;
-    b.h = 0;
-    if (has && first) b = make_cand(a, v, Lu, L0, conn, qs, c0, valid ? a.g.vweight(v) : 0);
-    b = group_best<LQ, G>(b);
-    const bool mover = valid && lane == 0 && b.L >= 0;
-    const unsigned idx = warp_append(&a.ctr->n_movers, mover);
-    if (mover) write_mover(a, idx, v, b, c0);
+// Records the proposal of the active vertex in slot idx (target -1: no proposal).
+__device__ __forceinline__ void write_slot(const LpProblem &P, int64_t idx, int v, const Best &b, long long c0) {
+  P.mv_t[idx] = b.L;
+  if (b.L >= 0) {
+    P.mv_v[idx] = v;
+    P.mv_gain[idx] = b.conn - c0;
+    P.mv_q[idx] = b.qs;
+    P.mv_adm[idx] = 0;
+    P.mv_of_v[v] = (int32_t)idx;
   }
 }
 
 __device__ __forceinline__ unsigned slot_hash(int L) { return (unsigned)L * 0x9E3779B1u; }
 
-// One warp per vertex, 32 < d <= deg_warp <= 256, open-addressing table in shared memory.
-template <int EW, bool LQ>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_choose_warp(LpArgs a) {
-  if (a.ctr->stop) return;
-  extern __shared__ __align__(16) unsigned char smem[];
+struct Smem {
+  Best best[kWarps];
+  long long sum[kWarps];
+  long long tmp[32];
+  long long tot;
+  unsigned long long vis[8], edg[8];
+  unsigned hist[256];
+  unsigned long long base[256];
+  unsigned wcnt[kWarps][256];
+  unsigned long long moves;
+  long long carry;
+  int carry_t;
+};
+
+template <bool LQ>
+__device__ __forceinline__ Best block_best_of(Best b, Smem &sm) {
+  b = group_best<LQ, 32>(b);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long *vals = reinterpret_cast<unsigned long long *>(smem) + wid * kWarpCap;
-  int *keys = reinterpret_cast<int *>(smem + kWarpsPerBlock * kWarpCap * 8) + wid * kWarpCap;
-  unsigned int *qv = reinterpret_cast<unsigned int *>(smem + kWarpsPerBlock * kWarpCap * 12) + wid * kWarpCap;
+  if (lane == 0) sm.best[wid] = b;
+  __syncthreads();
+  Best r = sm.best[0];
+  for (int w = 1; w < kWarps; w++)
+    if (better(sm.best[w], r)) r = sm.best[w];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
+  x = warp_sum64(x);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sm.sum[wid] = x;
+  __syncthreads();
+  long long r = 0;
+  for (int w = 0; w < kWarps; w++) r += sm.sum[w];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------------------ phases
+// Classify the active vertices of sub-round (r, s) into degree bins. Each block takes a contiguous
+// chunk of vertices, counts them per bin, reserves space with one atomic per bin and then fills it.
+__device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const uint8_t *act, int r, int s,
+                                          uint64_t rmix, int64_t *deg) {
+  if (!((r == 0 || act[v]) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == s)) return -1;
+  const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
+  *deg = d;
+  return d == 0 ? kBinZero : bin_of(d, P.deg_warp, P.deg_cta);
+}
+
+__device__ void phase_classify(const LpProblem &P, SubCounters &C, int r, int s, uint64_t rmix, int lb, int nb,
+                               Smem &sm) {
+  __shared__ unsigned s_cnt[8], s_base[8];
+  if (threadIdx.x < 8) {
+    sm.vis[threadIdx.x] = 0;
+    sm.edg[threadIdx.x] = 0;
+    s_cnt[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const uint8_t *act = P.act[r & 1];
+  uint8_t *act_next = P.act[(r + 1) & 1];
+  const int64_t n = P.g.n;
+  const int64_t chunk = (n + nb - 1) / nb;
+  const int64_t lo = min(n, (int64_t)lb * chunk), hi = min(n, lo + chunk);
+  const int lane = threadIdx.x & 31;
+  // pass 1: counts
+  for (int64_t v0 = lo; v0 < hi; v0 += kThreads) {
+    const int64_t v = v0 + threadIdx.x;
+    int b = -1;
+    int64_t d = 0;
+    if (v < hi) {
+      if (s == 0) act_next[v] = 0;  // the marks of round r go there
+      b = active_bin(P, v, act, r, s, rmix, &d);
+    }
+    const unsigned peers = __match_any_sync(kFull, b);
+    if (b >= 0 && lane == __ffs(peers) - 1) {
+      atomicAdd(&sm.vis[b], (unsigned long long)__popc(peers));
+      if (b < kBins) atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+    }
+    if (b >= 0 && d) atomicAdd(&sm.edg[b], (unsigned long long)d);
+  }
+  __syncthreads();
+  if (threadIdx.x < kBins) {
+    s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&C.bin_count[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+    s_cnt[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  // pass 2: fill the reserved ranges
+  for (int64_t v0 = lo; v0 < hi; v0 += kThreads) {
+    const int64_t v = v0 + threadIdx.x;
+    int b = -1;
+    int64_t d = 0;
+    if (v < hi) b = active_bin(P, v, act, r, s, rmix, &d);
+    const bool put = b >= 0 && b < kBins;
+    const unsigned peers = __match_any_sync(kFull, put ? b : -1);
+    const int leader = __ffs(peers) - 1;
+    unsigned pos = 0;
+    if (put && lane == leader) pos = atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    if (sm.vis[threadIdx.x]) atomicAdd(&P.ctr->bin_visits[threadIdx.x], sm.vis[threadIdx.x]);
+    if (sm.edg[threadIdx.x]) atomicAdd(&P.ctr->bin_edges[threadIdx.x], sm.edg[threadIdx.x]);
+  }
+}
+
+// Groups of G lanes, one vertex per group, d <= G. Equal neighbour labels within a group are found
+// with __match_any_sync and their weights summed over the matching lanes. Each group handles U
+// vertices per step and issues all of their loads before using any (memory-level parallelism).
+template <int G, int EW, bool LQ>
+__device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int lb, int nb) {
+  const unsigned cnt = C.bin_count[bin];
+  if (cnt == 0) return;
+  constexpr int U = G == 32 ? 2 : 4;
+  const int32_t *list = P.bin[bin];
+  constexpr unsigned kGpw = 32 / G;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned sub = (unsigned)lane / G;
+  const unsigned gw = (unsigned)lb * kWarps + (threadIdx.x >> 5), nw = (unsigned)nb * kWarps;
+  const unsigned stride = nw * kGpw;
+  for (unsigned base = gw * kGpw; base < cnt; base += stride * U) {
+    int v[U], Lu[U], L0[U], qq[U];
+    long long w[U];
+    int64_t beg[U], d[U];
+    bool valid[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const unsigned i = base + u * stride + sub;
+      valid[u] = i < cnt;
+      v[u] = valid[u] ? list[i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      beg[u] = 0;
+      d[u] = 0;
+      L0[u] = -2;
+      if (valid[u]) {
+        beg[u] = P.g.row_begin(v[u]);
+        d[u] = P.g.row_begin(v[u] + 1) - beg[u];
+        L0[u] = P.labels[v[u]];
+      }
+    }
+    int nbr[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      nbr[u] = gl < d[u] ? __ldg(P.g.adj + beg[u] + gl) : -1;
+      w[u] = 0;
+      qq[u] = 0;
+      if (gl < d[u]) {
+        w[u] = load_ew<EW>(P.g.ew, beg[u] + gl);
+        if (LQ) qq[u] = __ldg(P.q + beg[u] + gl);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) Lu[u] = nbr[u] >= 0 ? P.labels[nbr[u]] : -1;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const bool has = gl < d[u];
+      long long c0 = (has && Lu[u] == L0[u]) ? w[u] : 0;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) c0 += __shfl_xor_sync(kFull, c0, o, G);
+      const unsigned long long key = ((unsigned long long)sub << 32) | (unsigned)Lu[u];
+      const unsigned peers = __match_any_sync(kFull, key);
+      long long conn;
+      if constexpr (EW == 0) {
+        conn = __popc(peers);
+      } else {
+        if (!__any_sync(kFull, w[u] >= (1ll << 26))) {
+          conn = (long long)__reduce_add_sync(peers, (unsigned)w[u]);
+        } else {
+          conn = 0;
+          for (unsigned m = peers; m; m &= m - 1) conn += __shfl_sync(peers, w[u], __ffs(m) - 1);
+        }
+      }
+      long long qs = 0;
+      if constexpr (LQ) qs = (long long)__reduce_add_sync(peers, (unsigned)qq[u]);
+      const bool first = lane == __ffs(peers) - 1;
+      const long long cv = valid[u] ? P.g.vweight(v[u]) : 0;
+      Best b = no_best();
+      if (has && first) b = make_cand(P, v[u], Lu[u], L0[u], conn, qs, c0, cv);
+      b = group_best<LQ, G>(b);
+      const bool mover = valid[u] && gl == 0 && b.L >= 0;
+      if (valid[u] && gl == 0) write_slot(P, P.bin_base[bin] + base + u * stride + sub, v[u], b, c0);
+      warp_add_by_key(P.demand, mover, b.L, cv);
+    }
+  }
+}
+
+// One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
+template <int EW, bool LQ>
+__device__ void choose_warp(const LpProblem &P, SubCounters &C, int lb, int nb, unsigned char *dsm) {
+  const unsigned cnt = C.bin_count[4];
+  if (cnt == 0) return;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kWarpCap;
+  int *keys = reinterpret_cast<int *>(dsm + kWarps * kWarpCap * 8) + wid * kWarpCap;
+  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kWarps * kWarpCap * 12) + wid * kWarpCap;
   for (int s = lane; s < kWarpCap; s += 32) {
     keys[s] = -1;
     vals[s] = 0;
     if (LQ) qv[s] = 0;
   }
   __syncwarp();
-  const unsigned cnt = a.ctr->bin_count[4];
-  const int32_t *list = a.bin[4];
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const int32_t *list = P.bin[4];
+  const unsigned gw = (unsigned)lb * kWarps + wid, nw = (unsigned)nb * kWarps;
   for (unsigned i = gw; i < cnt; i += nw) {
     const int v = list[i];
-    const int64_t beg = a.g.row_begin(v), end = a.g.row_begin(v + 1);
+    const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
     const int d = (int)(end - beg);
     int cap = 64;
     while (cap < 2 * d) cap <<= 1;
     const unsigned mask = (unsigned)cap - 1;
-    const int L0 = a.labels[v];
+    const int L0 = P.labels[v];
     long long c0 = 0;
     for (int64_t e = beg + lane; e < end; e += 32) {
-      const int L = a.labels[__ldg(a.g.adj + e)];
-      const long long w = load_ew<EW>(a.g.ew, e);
+      const int L = P.labels[__ldg(P.g.adj + e)];
+      const long long w = load_ew<EW>(P.g.ew, e);
       if (L == L0) {
         c0 += w;
         continue;
@@ -348,7 +432,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_choose_warp(LpArgs a) {
         const int k = atomicCAS(&keys[s], -1, L);
         if (k == -1 || k == L) {
           atomicAdd(&vals[s], (unsigned long long)w);
-          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(a.q + e));
+          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(P.q + e));
           break;
         }
         s = (s + 1) & mask;
@@ -356,15 +440,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_choose_warp(LpArgs a) {
     }
     c0 = warp_sum64(c0);
     __syncwarp();
-    const long long cv = a.g.vweight(v);
-    Best b;
-    b.L = -1;
-    b.conn = b.qs = 0;
-    b.h = 0;
+    const long long cv = P.g.vweight(v);
+    Best b = no_best();
     for (int s = lane; s < cap; s += 32) {
       const int L = keys[s];
       if (L >= 0) {
-        Best x = make_cand(a, v, L, L0, (long long)vals[s], LQ ? (long long)qv[s] : 0, c0, cv);
+        const Best x = make_cand(P, v, L, L0, (long long)vals[s], LQ ? (long long)qv[s] : 0, c0, cv);
         if (better(x, b)) b = x;
         keys[s] = -1;
         vals[s] = 0;
@@ -373,79 +454,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_choose_warp(LpArgs a) {
     }
     __syncwarp();
     b = group_best<LQ, 32>(b);
-    const bool mover = lane == 0 && b.L >= 0;
-    const unsigned idx = warp_append(&a.ctr->n_movers, mover);
-    if (mover) write_mover(a, idx, v, b, c0);
+    if (lane == 0) {
+      write_slot(P, P.bin_base[4] + i, v, b, c0);
+      if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
+    }
   }
 }
 
-template <bool LQ>
-__device__ __forceinline__ Best block_best(Best b, Best *sh) {
-  b = group_best<LQ, 32>(b);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sh[wid] = b;
-  __syncthreads();
-  if (wid == 0) {
-    Best x;
-    x.L = -1;
-    x.conn = x.qs = 0;
-    x.h = 0;
-    if (lane < (int)(blockDim.x >> 5)) x = sh[lane];
-    x = group_best<LQ, 32>(x);
-    if (lane == 0) sh[0] = x;
-  }
-  __syncthreads();
-  Best r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ long long block_sum(long long x, long long *sh) {
-  x = warp_sum64(x);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sh[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    long long y = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
-    y = warp_sum64(y);
-    if (lane == 0) sh[0] = y;
-  }
-  __syncthreads();
-  long long r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-// One CTA per vertex, deg_warp < d <= deg_cta <= 2048, table in shared memory.
+// One CTA per vertex (deg_warp < d <= deg_cta), table in shared memory.
 template <int EW, bool LQ>
-__global__ void __launch_bounds__(kCtaThreads) k_choose_cta(LpArgs a) {
-  if (a.ctr->stop) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long *vals = reinterpret_cast<unsigned long long *>(smem);
-  int *keys = reinterpret_cast<int *>(smem + kCtaCap * 8);
-  unsigned int *qv = reinterpret_cast<unsigned int *>(smem + kCtaCap * 12);
-  __shared__ Best sh_best[32];
-  __shared__ long long sh_sum[32];
-  for (int s = threadIdx.x; s < kCtaCap; s += blockDim.x) {
+__device__ void choose_cta(const LpProblem &P, SubCounters &C, int lb, int nb, unsigned char *dsm, Smem &sm) {
+  const unsigned cnt = C.bin_count[5];
+  if (cnt == 0) return;
+  unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm);
+  int *keys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
+  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kCtaCap * 12);
+  __syncthreads();
+  for (int s = threadIdx.x; s < kCtaCap; s += kThreads) {
     keys[s] = -1;
     vals[s] = 0;
     if (LQ) qv[s] = 0;
   }
   __syncthreads();
-  const unsigned cnt = a.ctr->bin_count[5];
-  const int32_t *list = a.bin[5];
-  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+  const int32_t *list = P.bin[5];
+  for (unsigned i = lb; i < cnt; i += nb) {
     const int v = list[i];
-    const int64_t beg = a.g.row_begin(v), end = a.g.row_begin(v + 1);
+    const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
     const int d = (int)(end - beg);
     int cap = 64;
     while (cap < 2 * d) cap <<= 1;
     const unsigned mask = (unsigned)cap - 1;
-    const int L0 = a.labels[v];
+    const int L0 = P.labels[v];
     long long c0 = 0;
-    for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
-      const int L = a.labels[__ldg(a.g.adj + e)];
-      const long long w = load_ew<EW>(a.g.ew, e);
+    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
+      const int L = P.labels[__ldg(P.g.adj + e)];
+      const long long w = load_ew<EW>(P.g.ew, e);
       if (L == L0) {
         c0 += w;
         continue;
@@ -455,240 +498,237 @@ __global__ void __launch_bounds__(kCtaThreads) k_choose_cta(LpArgs a) {
         const int k = atomicCAS(&keys[s], -1, L);
         if (k == -1 || k == L) {
           atomicAdd(&vals[s], (unsigned long long)w);
-          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(a.q + e));
+          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(P.q + e));
           break;
         }
         s = (s + 1) & mask;
       }
     }
-    c0 = block_sum(c0, sh_sum);  // contains __syncthreads: table complete
-    const long long cv = a.g.vweight(v);
-    Best b;
-    b.L = -1;
-    b.conn = b.qs = 0;
-    b.h = 0;
-    for (int s = threadIdx.x; s < cap; s += blockDim.x) {
+    c0 = block_sum_of(c0, sm);  // also completes the table
+    const long long cv = P.g.vweight(v);
+    Best b = no_best();
+    for (int s = threadIdx.x; s < cap; s += kThreads) {
       const int L = keys[s];
       if (L >= 0) {
-        Best x = make_cand(a, v, L, L0, (long long)vals[s], LQ ? (long long)qv[s] : 0, c0, cv);
+        const Best x = make_cand(P, v, L, L0, (long long)vals[s], LQ ? (long long)qv[s] : 0, c0, cv);
         if (better(x, b)) b = x;
         keys[s] = -1;
         vals[s] = 0;
         if (LQ) qv[s] = 0;
       }
     }
-    b = block_best<LQ>(b, sh_best);
-    if (threadIdx.x == 0 && b.L >= 0) {
-      const unsigned idx = atomicAdd(&a.ctr->n_movers, 1u);
-      write_mover(a, idx, v, b, c0);
+    b = block_best_of<LQ>(b, sm);
+    if (threadIdx.x == 0) {
+      write_slot(P, P.bin_base[5] + i, v, b, c0);
+      if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
     }
   }
+  __syncthreads();
 }
 
-// Hubs (d > deg_cta): chunks of kHubChunk entries accumulate into the hub's global table.
-__global__ void k_hub_prefix(LpArgs a) {
-  if (a.ctr->stop) return;
-  __shared__ long long tmp[32];
-  __shared__ long long carry_s, tot_s;
-  const unsigned cnt = a.ctr->bin_count[6];
-  if (threadIdx.x == 0) carry_s = 0;
+// Hubs (d > deg_cta): exclusive prefix of their work chunks (one block).
+__device__ void hub_prefix(const LpProblem &P, SubCounters &C, Smem &sm) {
+  const unsigned cnt = C.bin_count[6];
+  if (threadIdx.x == 0) sm.carry = 0;
   __syncthreads();
-  for (unsigned base = 0; base < cnt; base += blockDim.x) {
+  for (unsigned base = 0; base < cnt; base += kThreads) {
     const unsigned i = base + threadIdx.x;
     long long c = 0;
     if (i < cnt) {
-      const int v = a.bin[6][i];
-      const int64_t d = a.g.row_begin(v + 1) - a.g.row_begin(v);
+      const int v = P.bin[6][i];
+      const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
       c = (d + kHubChunk - 1) / kHubChunk;
-      a.hub_c0[i] = 0;
+      P.hub_c0[i] = 0;
     }
-    const long long ex = block_excl_scan64(c, tmp, &tot_s);
-    if (i < cnt) a.hub_prefix[i] = (unsigned)(carry_s + ex);
+    const long long ex = block_excl_scan64(c, sm.tmp, &sm.tot);
+    if (i < cnt) P.hub_prefix[i] = (unsigned)(sm.carry + ex);
     __syncthreads();
-    if (threadIdx.x == 0) carry_s += tot_s;
+    if (threadIdx.x == 0) sm.carry += sm.tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.ctr->hub_chunks = (unsigned)carry_s;
+  if (threadIdx.x == 0) C.hub_chunks = (unsigned)sm.carry;
 }
 
 template <int EW, bool LQ>
-__global__ void __launch_bounds__(256) k_hub_accum(LpArgs a) {
-  if (a.ctr->stop) return;
-  __shared__ long long sh_sum[32];
-  const unsigned cnt = a.ctr->bin_count[6];
-  const unsigned chunks = a.ctr->hub_chunks;
-  for (unsigned c = blockIdx.x; c < chunks; c += gridDim.x) {
-    // hub i with hub_prefix[i] <= c < hub_prefix[i+1]
+__device__ void hub_accum(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
+  const unsigned cnt = C.bin_count[6], chunks = C.hub_chunks;
+  for (unsigned c = lb; c < chunks; c += nb) {
     unsigned lo = 0, hi = cnt;
     while (hi - lo > 1) {
       const unsigned mid = (lo + hi) >> 1;
-      if (a.hub_prefix[mid] <= c) lo = mid;
+      if (P.hub_prefix[mid] <= c) lo = mid;
       else hi = mid;
     }
     const unsigned i = lo;
-    const int v = a.bin[6][i];
-    const int64_t rb = a.g.row_begin(v), re = a.g.row_begin(v + 1);
-    const int64_t beg = rb + (int64_t)(c - a.hub_prefix[i]) * kHubChunk;
+    const int v = P.bin[6][i];
+    const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
     const int64_t end = min(re, beg + kHubChunk);
-    const int h = a.hub_of[v];
-    const int64_t tb = a.hub_base[h];
-    const int64_t d = re - rb;
+    const int64_t tb = P.hub_base[P.hub_of[v]];
     int64_t cap = 64;
-    while (cap < 2 * d) cap <<= 1;
+    while (cap < 2 * (re - rb)) cap <<= 1;
     const uint64_t mask = (uint64_t)cap - 1;
-    const int L0 = a.labels[v];
+    const int L0 = P.labels[v];
     long long c0 = 0;
-    for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
-      const int L = a.labels[__ldg(a.g.adj + e)];
-      const long long w = load_ew<EW>(a.g.ew, e);
+    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
+      const int L = P.labels[__ldg(P.g.adj + e)];
+      const long long w = load_ew<EW>(P.g.ew, e);
       if (L == L0) {
         c0 += w;
         continue;
       }
       uint64_t s = ((uint64_t)slot_hash(L) * 0x100000001ull) & mask;
       while (true) {
-        const int k = atomicCAS(&a.hub_keys[tb + s], -1, L);
+        const int k = atomicCAS(&P.hub_keys[tb + s], -1, L);
         if (k == -1 || k == L) {
-          atomicAdd(&a.hub_vals[tb + s], (unsigned long long)w);
-          if (LQ) atomicAdd(&a.hub_qv[tb + s], (unsigned)__ldg(a.q + e));
+          atomicAdd(&P.hub_vals[tb + s], (unsigned long long)w);
+          if (LQ) atomicAdd(&P.hub_qv[tb + s], (unsigned)__ldg(P.q + e));
           break;
         }
         s = (s + 1) & mask;
       }
     }
-    c0 = block_sum(c0, sh_sum);
-    if (threadIdx.x == 0 && c0) atomicAdd((unsigned long long *)&a.hub_c0[i], (unsigned long long)c0);
+    c0 = block_sum_of(c0, sm);
+    if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
   }
 }
 
 template <bool LQ>
-__global__ void __launch_bounds__(256) k_hub_choose(LpArgs a) {
-  if (a.ctr->stop) return;
-  __shared__ Best sh_best[32];
-  const unsigned cnt = a.ctr->bin_count[6];
-  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int v = a.bin[6][i];
-    const int64_t d = a.g.row_begin(v + 1) - a.g.row_begin(v);
+__device__ void hub_choose(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
+  const unsigned cnt = C.bin_count[6];
+  for (unsigned i = lb; i < cnt; i += nb) {
+    const int v = P.bin[6][i];
+    const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
     int64_t cap = 64;
     while (cap < 2 * d) cap <<= 1;
-    const int h = a.hub_of[v];
-    const int64_t tb = a.hub_base[h];
-    const int L0 = a.labels[v];
-    const long long c0 = a.hub_c0[i];
-    const long long cv = a.g.vweight(v);
-    Best b;
-    b.L = -1;
-    b.conn = b.qs = 0;
-    b.h = 0;
-    for (int64_t s = threadIdx.x; s < cap; s += blockDim.x) {
-      const int L = a.hub_keys[tb + s];
+    const int64_t tb = P.hub_base[P.hub_of[v]];
+    const int L0 = P.labels[v];
+    const long long c0 = P.hub_c0[i];
+    const long long cv = P.g.vweight(v);
+    Best b = no_best();
+    for (int64_t s = threadIdx.x; s < cap; s += kThreads) {
+      const int L = P.hub_keys[tb + s];
       if (L >= 0) {
-        Best x = make_cand(a, v, L, L0, (long long)a.hub_vals[tb + s], LQ ? (long long)a.hub_qv[tb + s] : 0, c0, cv);
+        const Best x = make_cand(P, v, L, L0, (long long)P.hub_vals[tb + s], LQ ? (long long)P.hub_qv[tb + s] : 0, c0, cv);
         if (better(x, b)) b = x;
-        a.hub_keys[tb + s] = -1;
-        a.hub_vals[tb + s] = 0;
-        if (LQ) a.hub_qv[tb + s] = 0;
+        P.hub_keys[tb + s] = -1;
+        P.hub_vals[tb + s] = 0;
+        if (LQ) P.hub_qv[tb + s] = 0;
       }
     }
-    b = block_best<LQ>(b, sh_best);
-    if (threadIdx.x == 0 && b.L >= 0) {
-      const unsigned idx = atomicAdd(&a.ctr->n_movers, 1u);
-      write_mover(a, idx, v, b, c0);
+    b = block_best_of<LQ>(b, sm);
+    if (threadIdx.x == 0) {
+      write_slot(P, P.bin_base[6] + i, v, b, c0);
+      if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
     }
   }
 }
 
-// ------------------------------------------------------------------------------------ admission
-__global__ void k_demand(LpArgs a) {
-  if (a.ctr->stop) return;
-  __shared__ unsigned long long sdem[kSmallLabels];
-  const bool small = a.nl <= kSmallLabels;
-  if (small) {
-    for (int k = threadIdx.x; k < a.nl; k += blockDim.x) sdem[k] = 0;
-    __syncthreads();
+// Active positions k in [0, sum of bin counts) map to proposal slots bin_base[b] + (k - start_b).
+struct SlotMap {
+  unsigned start[kBins + 1];
+  int64_t base[kBins];
+  __device__ __forceinline__ void init(const LpProblem &P, const SubCounters &C) {
+    start[0] = 0;
+#pragma unroll
+    for (int b = 0; b < kBins; b++) {
+      start[b + 1] = start[b] + C.bin_count[b];
+      base[b] = P.bin_base[b];
+    }
   }
-  const unsigned nm = a.ctr->n_movers;
-  if (threadIdx.x == 0 && blockIdx.x == 0) a.ctr->movers += nm;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
-    const int T = a.mv_t[i];
-    const unsigned long long c = (unsigned long long)a.g.vweight(a.mv_v[i]);
-    if (small) atomicAdd(&sdem[T], c);
-    else atomicAdd(reinterpret_cast<unsigned long long *>(&a.demand[T]), c);
+  __device__ __forceinline__ unsigned total() const { return start[kBins]; }
+  __device__ __forceinline__ int64_t slot(unsigned k) const {
+    int b = 0;
+#pragma unroll
+    for (int x = 1; x < kBins; x++)
+      if (k >= start[x]) b = x;
+    return base[b] + (k - start[b]);
   }
-  if (small) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < a.nl; k += blockDim.x)
-      if (sdem[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&a.demand[k]), sdem[k]);
-  }
-}
+};
 
+// Admission check of every proposal; proposals to targets whose total demand does not fit are
+// recorded as contested.
 template <bool LQ>
-__global__ void k_admit(LpArgs a) {
-  if (a.ctr->stop) return;
-  const unsigned nm = a.ctr->n_movers;
+__device__ void phase_admit(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
+  SlotMap M;
+  M.init(P, C);
+  const unsigned na = M.total();
   unsigned long long mg = 0, mq = 0;
-  for (unsigned base = blockIdx.x * blockDim.x; base < nm; base += gridDim.x * blockDim.x) {
-    const unsigned i = base + threadIdx.x;
+  unsigned movers = 0;
+  for (unsigned base = (unsigned)lb * kThreads; base < na; base += (unsigned)nb * kThreads) {
+    const unsigned k = base + threadIdx.x;
     bool contested = false;
-    if (i < nm) {
-      const int T = a.mv_t[i];
-      if (a.lw[T] + a.demand[T] <= a.U) {
-        a.mv_adm[i] = 1;
-      } else {
-        contested = true;
-        mg = max(mg, (unsigned long long)a.mv_gain[i]);
-        if (LQ) mq = max(mq, (unsigned long long)a.mv_q[i]);
+    int64_t i = 0;
+    if (k < na) {
+      i = M.slot(k);
+      const int T = P.mv_t[i];
+      if (T >= 0) {
+        movers++;
+        if (P.lw[T] + P.demand[T] <= P.U) {
+          P.mv_adm[i] = 1;
+        } else {
+          contested = true;
+          mg = max(mg, (unsigned long long)P.mv_gain[i]);
+          if (LQ) mq = max(mq, (unsigned long long)P.mv_q[i]);
+        }
       }
     }
-    const unsigned pos = warp_append(&a.ctr->n_contested, contested);
-    if (contested) a.ct[pos] = i;
+    const unsigned pos = warp_append(&C.n_contested, contested);
+    if (contested) P.ct[pos] = (unsigned)i;
   }
+  movers = (unsigned)block_sum_of((long long)movers, sm);
+  if (threadIdx.x == 0 && movers) atomicAdd(&P.ctr->movers, (unsigned long long)movers);
   for (int o = 16; o > 0; o >>= 1) {
     mg = max(mg, __shfl_xor_sync(kFull, mg, o));
     mq = max(mq, __shfl_xor_sync(kFull, mq, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    if (mg) atomicMax(&a.ctr->max_gain, mg);
-    if (LQ && mq) atomicMax(&a.ctr->max_q, mq);
+    if (mg) atomicMax(&C.max_gain, mg);
+    if (LQ && mq) atomicMax(&C.max_q, mq);
   }
 }
 
-// Ordering of contested movers: target asc, gain desc, score sum desc, id asc.
-__device__ __forceinline__ bool mover_less(const LpArgs &a, unsigned x, unsigned y) {
-  const int tx = a.mv_t[x], ty = a.mv_t[y];
+// Contested order: target asc, gain desc, score sum desc, id asc.
+__device__ __forceinline__ bool mover_less(const LpProblem &P, unsigned x, unsigned y) {
+  const int tx = P.mv_t[x], ty = P.mv_t[y];
   if (tx != ty) return tx < ty;
-  const long long gx = a.mv_gain[x], gy = a.mv_gain[y];
+  const long long gx = P.mv_gain[x], gy = P.mv_gain[y];
   if (gx != gy) return gx > gy;
-  const long long qx = a.mv_q[x], qy = a.mv_q[y];
+  const long long qx = P.mv_q[x], qy = P.mv_q[y];
   if (qx != qy) return qx > qy;
-  return a.mv_v[x] < a.mv_v[y];
+  return P.mv_v[x] < P.mv_v[y];
 }
 
-// Segmented inclusive prefix sums of c(v) over the sorted contested list, then admission.
-// Processes positions [lo, hi) of `order` with a block-wide carry (one block at a time).
-__device__ void admit_sorted_block(const LpArgs &a, const unsigned *order, unsigned lo, unsigned hi,
-                                   long long carry_in, int carry_target, long long *tmp,
-                                   long long *carry_out, int *carry_target_out) {
-  // carry (carry_in, carry_target): running sum of the open segment that ends at position lo-1.
-  __shared__ long long s_carry;
-  __shared__ int s_ct;
+// Segmented inclusive prefix sums of c(v) over positions [lo, hi) of a sequence sorted by target,
+// starting from the carry of the segment open before lo; a proposal is admitted while the target's
+// snapshot weight plus the prefix fits. at(p) gives (target, proposal index) of position p.
+template <class At>
+__device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi, long long carry_in,
+                             int carry_target, Smem &sm) {
   if (threadIdx.x == 0) {
-    s_carry = carry_in;
-    s_ct = carry_target;
+    sm.carry = carry_in;
+    sm.carry_t = carry_target;
   }
   __syncthreads();
-  for (unsigned base = lo; base < hi; base += blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (unsigned base = lo; base < hi; base += kThreads) {
     const unsigned p = base + threadIdx.x;
     const bool valid = p < hi;
-    unsigned idx = valid ? order[p] : 0;
-    const int T = valid ? a.mv_t[idx] : -1;
-    const int Tprev = (valid && p > lo) ? a.mv_t[order[p - 1]] : (valid ? s_ct : -1);
+    int T = -1, Tprev = -1;
+    unsigned idx = 0;
+    if (valid) {
+      at(p, T, idx);
+      if (p > lo) {
+        unsigned dummy;
+        at(p - 1, Tprev, dummy);
+      } else {
+        Tprev = sm.carry_t;
+      }
+    }
     const bool head = valid && T != Tprev;
-    long long c = valid ? a.g.vweight(a.mv_v[idx]) : 0;
-    // segmented inclusive scan: pairs (flag, value)
+    const long long c = valid ? P.g.vweight(P.mv_v[idx]) : 0;
     int f = head ? 1 : 0;
     long long x = c;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const long long y = __shfl_up_sync(kFull, x, o);
@@ -698,79 +738,101 @@ __device__ void admit_sorted_block(const LpArgs &a, const unsigned *order, unsig
         f |= fy;
       }
     }
-    __shared__ long long wsum[32];
-    __shared__ int wflag[32];
     if (lane == 31) {
-      wsum[wid] = x;
-      wflag[wid] = f;
+      sm.sum[wid] = x;
+      sm.wcnt[wid][0] = (unsigned)f;
     }
     __syncthreads();
-    if (wid == 0) {
-      long long s = lane < nw ? wsum[lane] : 0;
-      int fl = lane < nw ? wflag[lane] : 0;
-      // exclusive scan of (flag, sum) over warps, seeded by the block carry
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(kFull, s, o);
-        const int fy = __shfl_up_sync(kFull, fl, o);
-        if (lane >= o) {
-          if (!fl) s += y;
-          fl |= fy;
-        }
+    if (threadIdx.x == 0) {
+      long long run = sm.carry;
+      for (int w = 0; w < kWarps; w++) {
+        const long long s = sm.sum[w];
+        const int fl = (int)sm.wcnt[w][0];
+        sm.sum[w] = run;  // carry into warp w
+        run = fl ? s : run + s;
       }
-      // s, fl: inclusive over warps 0..lane; convert to exclusive with the block carry
-      long long ps = __shfl_up_sync(kFull, s, 1);
-      int pf = __shfl_up_sync(kFull, fl, 1);
-      if (lane == 0) {
-        ps = 0;
-        pf = 0;
-      }
-      long long ex = pf ? ps : ps + s_carry;
-      if (lane < nw) wsum[lane] = ex;
     }
     __syncthreads();
-    // prefix for this element: if no head at or before it within its warp, add warp exclusive
-    const long long incl = f ? x : x + wsum[wid];
-    if (valid) {
-      if (a.lw[T] + incl <= a.U) a.mv_adm[idx] = 1;
-    }
+    const long long incl = f ? x : x + sm.sum[wid];
+    if (valid && P.lw[T] + incl <= P.U) P.mv_adm[idx] = 1;
     __syncthreads();
-    // new carry: the last valid element of this tile
-    const unsigned last = min(hi, base + blockDim.x) - 1;
+    const unsigned last = min(hi, base + (unsigned)kThreads) - 1;
     if (p == last) {
-      s_carry = incl;
-      s_ct = T;
+      sm.carry = incl;
+      sm.carry_t = T;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (carry_out) *carry_out = s_carry;
-    if (carry_target_out) *carry_target_out = s_ct;
-  }
-  (void)tmp;
 }
 
-// Small contested sets: one CTA sorts the indices in shared memory (bitonic) and admits.
-__global__ void __launch_bounds__(1024) k_contest_small(LpArgs a) {
-  if (a.ctr->stop) return;
-  const unsigned cnt = a.ctr->n_contested;
-  if (cnt == 0 || cnt > kContestSmall) return;
-  __shared__ unsigned key[kContestSmall];
-  unsigned P = 1;
-  while (P < cnt) P <<= 1;
-  for (unsigned i = threadIdx.x; i < P; i += blockDim.x) key[i] = i < cnt ? a.ct[i] : 0xffffffffu;
+__device__ __forceinline__ int bits_for(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
+
+// Small contested sets (one CTA). When (target, gain desc, score desc, id) packs into 64 bits the
+// keys are sorted in shared memory (bitonic); otherwise proposal indices are sorted with a comparator.
+template <bool LQ>
+__device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, unsigned char *dsm, Smem &sm) {
+  unsigned Pp = 1;
+  while (Pp < cnt) Pp <<= 1;
+  const unsigned long long maxg = C.max_gain, maxq = C.max_q;
+  const int bv = bits_for((unsigned long long)(P.g.n > 0 ? P.g.n - 1 : 0));
+  const int bq = LQ ? bits_for(maxq) : 0;
+  const int bg = bits_for(maxg);
+  const int bt = bits_for((unsigned long long)(P.nl > 0 ? P.nl - 1 : 0));
   __syncthreads();
-  for (unsigned k = 2; k <= P; k <<= 1) {
+  if (bv + bq + bg + bt <= 63) {  // top bit clear: real keys never equal the padding
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(dsm);
+    const int sq = bv, sg = bv + bq, st = bv + bq + bg;
+    for (unsigned i = threadIdx.x; i < Pp; i += kThreads) {
+      unsigned long long k = ~0ull;
+      if (i < cnt) {
+        const unsigned idx = P.ct[i];
+        k = (unsigned long long)(unsigned)P.mv_v[idx];
+        if (LQ && bq) k |= (maxq - (unsigned long long)P.mv_q[idx]) << sq;
+        if (bg) k |= (maxg - (unsigned long long)P.mv_gain[idx]) << sg;
+        if (bt) k |= (unsigned long long)(unsigned)P.mv_t[idx] << st;
+      }
+      key[i] = k;
+    }
+    __syncthreads();
+    for (unsigned k = 2; k <= Pp; k <<= 1) {
+      for (unsigned j = k >> 1; j > 0; j >>= 1) {
+        for (unsigned t = threadIdx.x; t < Pp / 2; t += kThreads) {
+          const unsigned i = 2 * j * (t / j) + (t % j), l = i + j;
+          const bool up = (i & k) == 0;
+          const unsigned long long x = key[i], y = key[l];
+          if ((x > y) == up && x != y) {
+            key[i] = y;
+            key[l] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const unsigned long long vmask = bv >= 64 ? ~0ull : ((1ull << bv) - 1);
+    admit_sorted(
+        P,
+        [&](unsigned p, int &T, unsigned &idx) {
+          const unsigned long long k = key[p];
+          T = bt ? (int)(k >> st) : 0;
+          idx = (unsigned)P.mv_of_v[(int)(k & vmask)];
+        },
+        0, cnt, 0, -1, sm);
+    if (threadIdx.x == 0) P.ctr->contest_packed += 1;
+    return;
+  }
+  unsigned *key = reinterpret_cast<unsigned *>(dsm);
+  for (unsigned i = threadIdx.x; i < Pp; i += kThreads) key[i] = i < cnt ? P.ct[i] : 0xffffffffu;
+  __syncthreads();
+  for (unsigned k = 2; k <= Pp; k <<= 1) {
     for (unsigned j = k >> 1; j > 0; j >>= 1) {
-      for (unsigned t = threadIdx.x; t < P / 2; t += blockDim.x) {
-        const unsigned i = 2 * j * (t / j) + (t % j);
-        const unsigned l = i + j;
+      for (unsigned t = threadIdx.x; t < Pp / 2; t += kThreads) {
+        const unsigned i = 2 * j * (t / j) + (t % j), l = i + j;
         const bool up = (i & k) == 0;
         const unsigned x = key[i], y = key[l];
         bool swap;
         if (x == 0xffffffffu) swap = (y != 0xffffffffu) == up;
         else if (y == 0xffffffffu) swap = !up;
-        else swap = mover_less(a, y, x) == up;
+        else swap = mover_less(P, y, x) == up;
         if (swap) {
           key[i] = y;
           key[l] = x;
@@ -779,200 +841,331 @@ __global__ void __launch_bounds__(1024) k_contest_small(LpArgs a) {
       __syncthreads();
     }
   }
-  __shared__ long long tmp[32];
-  admit_sorted_block(a, key, 0, cnt, 0, -1, tmp, nullptr, nullptr);
+  admit_sorted(
+      P,
+      [&](unsigned p, int &T, unsigned &idx) {
+        idx = key[p];
+        T = P.mv_t[idx];
+      },
+      0, cnt, 0, -1, sm);
+  if (threadIdx.x == 0) P.ctr->contest_small += 1;
 }
 
-// Large contested sets: cooperative stable LSD radix sort of the mover indices by
-// (target, gain desc, score sum desc, id) -- least significant key first -- then segmented admission.
-__device__ __forceinline__ unsigned long long field_key(const LpArgs &a, unsigned idx, int field,
+__device__ __forceinline__ unsigned long long field_key(const LpProblem &P, unsigned idx, int field,
                                                         unsigned long long maxg, unsigned long long maxq) {
   switch (field) {
-    case 0: return (unsigned long long)(unsigned)a.mv_v[idx];
-    case 1: return maxq - (unsigned long long)a.mv_q[idx];
-    case 2: return maxg - (unsigned long long)a.mv_gain[idx];
-    default: return (unsigned long long)(unsigned)a.mv_t[idx];
+    case 0: return (unsigned long long)(unsigned)P.mv_v[idx];
+    case 1: return maxq - (unsigned long long)P.mv_q[idx];
+    case 2: return maxg - (unsigned long long)P.mv_gain[idx];
+    default: return (unsigned long long)(unsigned)P.mv_t[idx];
   }
 }
 
-__device__ __forceinline__ int bits_for(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
-
+// Large contested sets: stable LSD radix sort of the proposal indices over the problem's blocks,
+// least significant key first (id, score sum desc, gain desc, target), then segmented admission.
 template <bool LQ>
-__global__ void __launch_bounds__(256) k_contest_large(LpArgs a, GridBarrier bar) {
-  if (a.ctr->stop) return;
-  const unsigned cnt = a.ctr->n_contested;
-  if (cnt <= kContestSmall) return;
-  const unsigned nb = gridDim.x, b = blockIdx.x;
-  const unsigned long long maxg = a.ctr->max_gain, maxq = a.ctr->max_q;
-  const int nbits[4] = {bits_for((unsigned long long)(a.g.n > 0 ? a.g.n - 1 : 0)), LQ ? bits_for(maxq) : 0,
-                        bits_for(maxg), bits_for((unsigned long long)(a.nl > 0 ? a.nl - 1 : 0))};
+__device__ bool contest_large(const LpProblem &P, SubCounters &C, unsigned cnt, int lb, int nb, const GridBarrier &bar,
+                              Smem &sm) {
+  const unsigned long long maxg = C.max_gain, maxq = C.max_q;
+  const int nbits[4] = {bits_for((unsigned long long)(P.g.n > 0 ? P.g.n - 1 : 0)), LQ ? bits_for(maxq) : 0,
+                        bits_for(maxg), bits_for((unsigned long long)(P.nl > 0 ? P.nl - 1 : 0))};
   const unsigned chunk = (cnt + nb - 1) / nb;
-  const unsigned lo = min(cnt, b * chunk), hi = min(cnt, lo + chunk);
-  __shared__ unsigned hist[256];
-  __shared__ unsigned long long base[256];
-  __shared__ unsigned wcnt[8][256];
-  unsigned *src = a.ct, *dst = a.ct2;
+  const unsigned lo = min(cnt, (unsigned)lb * chunk), hi = min(cnt, lo + chunk);
+  unsigned *src = P.ct, *dst = P.ct2;
+  const int wid = threadIdx.x >> 5;
   for (int field = 0; field < 4; field++) {
     for (int shift = 0; shift < nbits[field]; shift += 8) {
-      // 1. block histogram of its slice
-      for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+      for (int t = threadIdx.x; t < 256; t += kThreads) sm.hist[t] = 0;
       __syncthreads();
-      for (unsigned p = lo + threadIdx.x; p < hi; p += blockDim.x)
-        atomicAdd(&hist[(field_key(a, src[p], field, maxg, maxq) >> shift) & 255], 1u);
+      for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads)
+        atomicAdd(&sm.hist[(field_key(P, src[p], field, maxg, maxq) >> shift) & 255], 1u);
       __syncthreads();
-      for (int t = threadIdx.x; t < 256; t += blockDim.x) a.hist[(size_t)b * 256 + t] = hist[t];
-      if (!grid_sync(bar)) return;
-      // 2. per digit: exclusive prefix over blocks; digit totals
-      for (unsigned t = b * blockDim.x + threadIdx.x; t < 256; t += nb * blockDim.x) {
-        unsigned long long run = 0;
-        for (unsigned bb = 0; bb < nb; bb++) {
-          const unsigned h = a.hist[(size_t)bb * 256 + t];
-          a.hoff[(size_t)bb * 256 + t] = run;
-          run += h;
+      // digit-major counts: hist[d * nb + block]
+      for (int t = threadIdx.x; t < 256; t += kThreads) P.hist[(size_t)t * nb + lb] = sm.hist[t];
+      if (!grid_sync(bar)) return false;
+      // one warp per digit scans the per-block counts (coalesced, 32 blocks per step)
+      {
+        const int lane = threadIdx.x & 31;
+        for (unsigned d = (unsigned)lb * kWarps + wid; d < 256; d += (unsigned)nb * kWarps) {
+          unsigned long long run = 0;
+          for (int b0 = 0; b0 < nb; b0 += 32) {
+            const int bb = b0 + lane;
+            const unsigned long long h = bb < nb ? P.hist[(size_t)d * nb + bb] : 0;
+            unsigned long long inc = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+              if (lane >= o) inc += y;
+            }
+            if (bb < nb) P.hoff[(size_t)bb * 256 + d] = run + inc - h;
+            run += __shfl_sync(kFull, inc, 31);
+          }
+          if (lane == 0) P.hoff[(size_t)nb * 256 + d] = run;
         }
-        a.hoff[(size_t)nb * 256 + t] = run;  // digit total
       }
-      if (!grid_sync(bar)) return;
-      // 3. block base per digit = exclusive scan of totals + block prefix
+      if (!grid_sync(bar)) return false;
       if (threadIdx.x == 0) {
         unsigned long long acc = 0;
         for (int t = 0; t < 256; t++) {
-          base[t] = acc + a.hoff[(size_t)b * 256 + t];
-          acc += a.hoff[(size_t)nb * 256 + t];
+          sm.base[t] = acc + P.hoff[(size_t)lb * 256 + t];
+          acc += P.hoff[(size_t)nb * 256 + t];
         }
       }
       __syncthreads();
-      // 4. stable scatter of the slice
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      for (unsigned t0 = lo; t0 < hi; t0 += blockDim.x) {
+      for (unsigned t0 = lo; t0 < hi; t0 += kThreads) {
         const unsigned p = t0 + threadIdx.x;
         const bool valid = p < hi;
         const unsigned x = valid ? src[p] : 0;
-        const int dg = valid ? (int)((field_key(a, x, field, maxg, maxq) >> shift) & 255) : 256;
-        for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) wcnt[k >> 8][k & 255] = 0;
+        const int dg = valid ? (int)((field_key(P, x, field, maxg, maxq) >> shift) & 255) : 256;
+        for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) sm.wcnt[k >> 8][k & 255] = 0;
         __syncthreads();
         const unsigned peers = __match_any_sync(kFull, dg);
         const int rank = __popc(peers & lanemask_lt());
-        if (valid && rank == 0) wcnt[wid][dg] = __popc(peers);
+        if (valid && rank == 0) sm.wcnt[wid][dg] = __popc(peers);
         __syncthreads();
         if (valid) {
           unsigned pre = 0;
-          for (int w = 0; w < wid; w++) pre += wcnt[w][dg];
-          dst[base[dg] + pre + rank] = x;
+          for (int w = 0; w < wid; w++) pre += sm.wcnt[w][dg];
+          dst[sm.base[dg] + pre + rank] = x;
         }
         __syncthreads();
         if (threadIdx.x < 256) {
           unsigned s = 0;
-          for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += wcnt[w][threadIdx.x];
-          base[threadIdx.x] += s;
+          for (int w = 0; w < kWarps; w++) s += sm.wcnt[w][threadIdx.x];
+          sm.base[threadIdx.x] += s;
         }
         __syncthreads();
-        (void)lane;
       }
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar)) return false;
       unsigned *t = src;
       src = dst;
       dst = t;
     }
   }
-  // Segmented admission over the sorted order `src`: blocks take consecutive slices; each block
-  // needs the running sum of the segment open at its slice start. Pass 1: per-block (head seen,
-  // sum of trailing segment part); pass 2: carries resolved sequentially by one thread.
-  __shared__ long long tmp[32];
-  {
-    long long tail = 0;
-    int has_head = 0;
-    int last_t = -1;
-    if (lo < hi) {
-      last_t = a.mv_t[src[hi - 1]];
-      // sum of c over the maximal suffix of the slice whose target equals last_t, and whether the
-      // slice contains a segment head (target change) in it
-      long long part = 0;
-      int headseen = 0;
-      for (unsigned p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-        const unsigned idx = src[p];
-        if (a.mv_t[idx] == last_t) part += a.g.vweight(a.mv_v[idx]);
-        else headseen = 1;
-      }
-      tail = block_sum(part, tmp);
-      has_head = __syncthreads_or(headseen);
-    } else {
-      __syncthreads_or(0);
+  // carries between block slices: per block (sum of the trailing segment, whether the slice has a
+  // segment head, target of its last element), resolved in order by one thread
+  long long tail = 0;
+  int has_head = 0, last_t = -1;
+  if (lo < hi) {
+    last_t = P.mv_t[src[hi - 1]];
+    long long part = 0;
+    int hs = 0;
+    for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) {
+      const unsigned idx = src[p];
+      if (P.mv_t[idx] == last_t) part += P.g.vweight(P.mv_v[idx]);
+      else hs = 1;
     }
-    if (threadIdx.x == 0) {
-      a.hoff[(size_t)b * 4 + 0] = (unsigned long long)tail;
-      a.hoff[(size_t)b * 4 + 1] = (unsigned long long)has_head;
-      a.hoff[(size_t)b * 4 + 2] = (unsigned long long)(long long)last_t;
-      a.hoff[(size_t)b * 4 + 3] = (unsigned long long)(hi > lo ? 1 : 0);
-    }
-    if (!grid_sync(bar)) return;
-    if (b == 0 && threadIdx.x == 0) {
-      // carry into block bb = running sum of the segment open at its start
-      long long run = 0;
-      long long run_t = -1;
-      for (unsigned bb = 0; bb < nb; bb++) {
-        a.hoff[(size_t)nb * 4 + bb * 2 + 0] = (unsigned long long)run;
-        a.hoff[(size_t)nb * 4 + bb * 2 + 1] = (unsigned long long)run_t;
-        if (!a.hoff[(size_t)bb * 4 + 3]) continue;
-        const long long t = (long long)a.hoff[(size_t)bb * 4 + 0];
-        const long long lt = (long long)a.hoff[(size_t)bb * 4 + 2];
-        const int hh = (int)a.hoff[(size_t)bb * 4 + 1];
-        if (!hh && lt == run_t) run += t;
-        else run = t;
-        run_t = lt;
-      }
-    }
-    if (!grid_sync(bar)) return;
+    tail = block_sum_of(part, sm);
+    has_head = __syncthreads_or(hs);
   }
-  const long long carry = (long long)a.hoff[(size_t)nb * 4 + b * 2 + 0];
-  const int carry_t = (int)(long long)a.hoff[(size_t)nb * 4 + b * 2 + 1];
-  if (lo < hi) admit_sorted_block(a, src, lo, hi, carry, carry_t, tmp, nullptr, nullptr);
+  if (threadIdx.x == 0) {
+    P.hoff[(size_t)lb * 4 + 0] = (unsigned long long)tail;
+    P.hoff[(size_t)lb * 4 + 1] = (unsigned long long)has_head;
+    P.hoff[(size_t)lb * 4 + 2] = (unsigned long long)(long long)last_t;
+    P.hoff[(size_t)lb * 4 + 3] = (unsigned long long)(hi > lo ? 1 : 0);
+  }
+  if (!grid_sync(bar)) return false;
+  if (lb == 0 && threadIdx.x == 0) {
+    long long run = 0, run_t = -1;
+    for (int bb = 0; bb < nb; bb++) {
+      P.hoff[(size_t)nb * 4 + bb * 2 + 0] = (unsigned long long)run;
+      P.hoff[(size_t)nb * 4 + bb * 2 + 1] = (unsigned long long)run_t;
+      if (!P.hoff[(size_t)bb * 4 + 3]) continue;
+      const long long t = (long long)P.hoff[(size_t)bb * 4 + 0];
+      const long long lt = (long long)P.hoff[(size_t)bb * 4 + 2];
+      const int hh = (int)P.hoff[(size_t)bb * 4 + 1];
+      if (!hh && lt == run_t) run += t;
+      else run = t;
+      run_t = lt;
+    }
+  }
+  if (!grid_sync(bar)) return false;
+  const long long carry = (long long)P.hoff[(size_t)nb * 4 + lb * 2 + 0];
+  const int carry_t = (int)(long long)P.hoff[(size_t)nb * 4 + lb * 2 + 1];
+  if (lo < hi)
+    admit_sorted(
+        P,
+        [&](unsigned p, int &T, unsigned &idx) {
+          idx = src[p];
+          T = P.mv_t[idx];
+        },
+        lo, hi, carry, carry_t, sm);
+  if (lb == 0 && threadIdx.x == 0) P.ctr->contest_large += 1;
+  return true;
 }
 
-// ------------------------------------------------------------------------------------ apply
-__global__ void k_apply(LpArgs a) {
-  if (a.ctr->stop) return;
-  __shared__ long long sdel[kSmallLabels];
-  __shared__ unsigned long long s_moves;
-  const bool small = a.nl <= kSmallLabels;
-  if (small)
-    for (int k = threadIdx.x; k < a.nl; k += blockDim.x) sdel[k] = 0;
-  if (threadIdx.x == 0) s_moves = 0;
+// Apply admitted moves (32 proposals per warp), update label weights, mark neighbours for the next
+// round and clear the demand of every proposed target.
+__device__ void phase_apply(const LpProblem &P, SubCounters &C, int r, int lb, int nb, Smem &sm) {
+  if (threadIdx.x == 0) sm.moves = 0;
   __syncthreads();
-  const unsigned nm = a.ctr->n_movers;
+  SlotMap M;
+  M.init(P, C);
+  const unsigned na = M.total();
+  uint8_t *act_next = P.act[(r + 1) & 1];
   const int lane = threadIdx.x & 31;
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned i = gw; i < nm; i += nw) {
-    const int T = a.mv_t[i];
-    const bool adm = a.mv_adm[i];
-    if (lane == 0) a.demand[T] = 0;
-    if (!adm) continue;
-    const int v = a.mv_v[i];
-    if (lane == 0) {
-      const long long c = a.g.vweight(v);
-      const int L0 = a.labels[v];
-      a.labels[v] = T;
-      if (small) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sdel[T]), (unsigned long long)c);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&sdel[L0]), (unsigned long long)(-c));
-      } else {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&a.lw[T]), (unsigned long long)c);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&a.lw[L0]), (unsigned long long)(-c));
-      }
-      atomicAdd(&s_moves, 1ull);
+  const unsigned gw = (unsigned)lb * kWarps + (threadIdx.x >> 5), nw = (unsigned)nb * kWarps;
+  for (unsigned base = gw * 32; base < na; base += nw * 32) {
+    const unsigned k = base + lane;
+    const int64_t i = k < na ? M.slot(k) : 0;
+    const int T = k < na ? P.mv_t[i] : -1;
+    const bool valid = T >= 0;
+    const bool adm = valid && P.mv_adm[i];
+    const int v = valid ? P.mv_v[i] : 0;
+    if (valid) P.demand[T] = 0;
+    int L0 = -1;
+    long long c = 0;
+    if (adm) {
+      L0 = P.labels[v];
+      c = P.g.vweight(v);
+      P.labels[v] = T;
     }
-    const int64_t beg = a.g.row_begin(v), end = a.g.row_begin(v + 1);
-    for (int64_t e = beg + lane; e < end; e += 32) a.act_next[__ldg(a.g.adj + e)] = 1;
+    warp_add_by_key(P.lw, adm, T, c);
+    warp_add_by_key(P.lw, adm, L0, -c);
+    const unsigned am = __ballot_sync(kFull, adm);
+    if (lane == 0 && am) atomicAdd(&sm.moves, (unsigned long long)__popc(am));
+    if (!am) continue;
+    // mark the neighbours of the admitted movers: the warp walks the concatenation of their rows
+    int64_t rb = 0, deg = 0;
+    if (adm) {
+      rb = P.g.row_begin(v);
+      deg = P.g.row_begin(v + 1) - rb;
+    }
+    int64_t incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int64_t excl = incl - deg;
+    const int64_t total = __shfl_sync(kFull, incl, 31);
+    for (int64_t t0 = 0; t0 < total; t0 += 32) {
+      const int64_t t = t0 + lane;
+      // owner: the largest lane j with excl_j <= t
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t ex = __shfl_sync(kFull, excl, j + step);
+        if (j + step < 32 && ex <= t) j += step;
+      }
+      const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
+      if (t < total) act_next[__ldg(P.g.adj + rbj + (t - exj))] = 1;
+    }
   }
   __syncthreads();
-  if (small)
-    for (int k = threadIdx.x; k < a.nl; k += blockDim.x)
-      if (sdel[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&a.lw[k]), (unsigned long long)sdel[k]);
-  if (threadIdx.x == 0 && s_moves) atomicAdd(&a.ctr->moves_round, s_moves);
+  if (threadIdx.x == 0 && sm.moves) atomicAdd(&P.ctr->moves_round[r & 1], sm.moves);
 }
 
-// ------------------------------------------------------------------------------------ hub setup
+// ------------------------------------------------------------------------------------ the kernel
+template <int EW, bool LQ>
+__global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, const int *block_prob) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(16) unsigned char p_raw[sizeof(LpProblem)];
+  __shared__ Smem sm;
+  LpProblem &P = *reinterpret_cast<LpProblem *>(p_raw);
+  {
+    const unsigned *src = reinterpret_cast<const unsigned *>(probs + block_prob[blockIdx.x]);
+    unsigned *dst = reinterpret_cast<unsigned *>(p_raw);
+    for (unsigned i = threadIdx.x; i < sizeof(LpProblem) / 4; i += kThreads) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int lb = (int)blockIdx.x - P.block_begin, nb = P.block_count;
+  LpCounters *ctr = P.ctr;
+  const GridBarrier bar{P.bar, &ctr->bar_gen, &ctr->err, (unsigned)nb, (unsigned)lb};
+  // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there)
+  unsigned long long tmark = 0;
+  auto tick = [&](int phase) {
+    if (lb == 0 && threadIdx.x == 0) {
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (phase >= 0) ctr->phase_ns[phase] += now - tmark;
+      tmark = now;
+    }
+  };
+  tick(-1);
+  for (int r = 0; r < P.rounds; r++) {
+    const uint64_t rmix = mix64(P.smix ^ (uint64_t)r);
+    for (int s = 0; s < 2; s++) {
+      const int t = 2 * r + s;
+      SubCounters &C = ctr->sc[t & 1];
+      SubCounters &Cn = ctr->sc[(t + 1) & 1];
+      if (lb == 0) {
+        // the other counter set was last used by sub-round t-1, which every block has finished
+        if (threadIdx.x < 8) Cn.bin_count[threadIdx.x] = 0;
+        if (threadIdx.x == 0) {
+          Cn.n_movers = 0;
+          Cn.n_contested = 0;
+          Cn.hub_chunks = 0;
+          Cn.max_gain = 0;
+          Cn.max_q = 0;
+        }
+      }
+      phase_classify(P, C, r, s, rmix, lb, nb, sm);
+      if (!grid_sync(bar)) return;
+      tick(0);
+      unsigned active = 0;
+      for (int b = 0; b < kBins; b++) active += *(volatile unsigned *)&C.bin_count[b];
+      if (active > 0) {
+        if (lb == 0 && P.has_hubs && C.bin_count[6]) hub_prefix(P, C, sm);
+        choose_groups<4, EW, LQ>(P, C, 0, lb, nb);
+        choose_groups<8, EW, LQ>(P, C, 1, lb, nb);
+        choose_groups<16, EW, LQ>(P, C, 2, lb, nb);
+        choose_groups<32, EW, LQ>(P, C, 3, lb, nb);
+        choose_warp<EW, LQ>(P, C, lb, nb, dsm);
+        choose_cta<EW, LQ>(P, C, lb, nb, dsm, sm);
+        if (!grid_sync(bar)) return;
+        tick(1);
+        if (P.has_hubs && C.bin_count[6]) {
+          hub_accum<EW, LQ>(P, C, lb, nb, sm);
+          if (!grid_sync(bar)) return;
+          hub_choose<LQ>(P, C, lb, nb, sm);
+          if (!grid_sync(bar)) return;
+          tick(2);
+        }
+        if (lb == 0 && threadIdx.x == 0 && s == 0) ctr->moves_round[(r + 1) & 1] = 0;
+        phase_admit<LQ>(P, C, lb, nb, sm);
+        if (!grid_sync(bar)) return;
+        tick(3);
+        const unsigned nc = *(volatile unsigned *)&C.n_contested;
+        if (nc > 0) {
+          if (nc <= kContestSmall) {
+            if (lb == 0) contest_small<LQ>(P, C, nc, dsm, sm);
+          } else {
+            if (!contest_large<LQ>(P, C, nc, lb, nb, bar, sm)) return;
+          }
+          if (!grid_sync(bar)) return;
+          tick(4);
+        }
+        phase_apply(P, C, r, lb, nb, sm);
+        if (!grid_sync(bar)) return;
+        tick(5);
+      } else if (lb == 0 && threadIdx.x == 0 && s == 0) {
+        ctr->moves_round[(r + 1) & 1] = 0;
+      }
+    }
+    // round end: every block reads the round's move count (final after the last barrier)
+    const unsigned long long mr = *(volatile unsigned long long *)&ctr->moves_round[r & 1];
+    if (lb == 0 && threadIdx.x == 0) {
+      ctr->rounds += 1;
+      ctr->moves += mr;
+    }
+    if (mr == 0) break;
+  }
+}
+
+// ------------------------------------------------------------------------------------ host helpers
+__global__ void k_degree_classes(DGraph g, int deg_warp, int deg_cta, unsigned *counts) {
+  __shared__ unsigned int cnt[8];
+  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
+    if (d > 0) atomicAdd(&cnt[bin_of(d, deg_warp, deg_cta)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
+}
+
 __global__ void k_hub_mark(DGraph g, int deg_cta, int32_t *hub_of, int64_t *hub_cap, unsigned *count) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
@@ -988,118 +1181,54 @@ __global__ void k_hub_mark(DGraph g, int deg_cta, int32_t *hub_of, int64_t *hub_
   }
 }
 
+constexpr int kSmallK = 2048;
+
 __global__ void k_block_weights(DGraph g, const int32_t *part, int64_t k, int64_t *bw, int *bad) {
+  __shared__ unsigned long long sbw[kSmallK];
+  const bool small = k <= kSmallK;
+  if (small) {
+    for (int b = threadIdx.x; b < k; b += blockDim.x) sbw[b] = 0;
+    __syncthreads();
+  }
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
     const int b = part[v];
     if (b < 0 || b >= k) {
       if (bad) atomicExch(bad, 1);
       continue;
     }
-    atomicAdd(reinterpret_cast<unsigned long long *>(&bw[b]), (unsigned long long)g.vweight(v));
+    if (small) atomicAdd(&sbw[b], (unsigned long long)g.vweight(v));
+    else atomicAdd(reinterpret_cast<unsigned long long *>(&bw[b]), (unsigned long long)g.vweight(v));
+  }
+  if (small) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < k; b += blockDim.x)
+      if (sbw[b]) atomicAdd(reinterpret_cast<unsigned long long *>(&bw[b]), sbw[b]);
   }
 }
 
-template <class K>
-int max_blocks(K kernel, int threads, size_t smem) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) per_sm = 1;
-  return std::max(1, per_sm) * num_sms();
-}
-
 template <int EW, bool LQ>
-struct LpKernels {
-  static int launch_sub(const LpArgs &a, const int64_t cap[kBins], int warp_grid_cap, cudaStream_t s,
-                        GridBarrier bar, int coop_grid) {
-    const int nsm = num_sms();
-    auto grid_for = [&](int64_t items, int per_block, int limit) {
-      int64_t g = (items + per_block - 1) / per_block;
-      return (int)std::max<int64_t>(1, std::min<int64_t>(g, limit));
-    };
-    if (cap[0]) {
-      ProfScope ps("lp_choose_g4", s);
-      (::gp::count_launch(), k_choose_group<4, EW, LQ><<<grid_for(cap[0], 64, nsm * 16), 256, 0, s>>>(a, 0));
-    }
-    if (cap[1]) {
-      ProfScope ps("lp_choose_g8", s);
-      (::gp::count_launch(), k_choose_group<8, EW, LQ><<<grid_for(cap[1], 32, nsm * 16), 256, 0, s>>>(a, 1));
-    }
-    if (cap[2]) {
-      ProfScope ps("lp_choose_g16", s);
-      (::gp::count_launch(), k_choose_group<16, EW, LQ><<<grid_for(cap[2], 16, nsm * 16), 256, 0, s>>>(a, 2));
-    }
-    if (cap[3]) {
-      ProfScope ps("lp_choose_g32", s);
-      (::gp::count_launch(), k_choose_group<32, EW, LQ><<<grid_for(cap[3], 8, nsm * 16), 256, 0, s>>>(a, 3));
-    }
-    if (cap[4]) {
-      ProfScope ps("lp_choose_warp", s);
-      {
-        const size_t sm = kWarpsPerBlock * kWarpCap * 16;
-        (::gp::count_launch(), k_choose_warp<EW, LQ><<<grid_for(cap[4], kWarpsPerBlock, warp_grid_cap), kWarpsPerBlock * 32, sm, s>>>(a));
-      }
-    }
-    if (cap[5]) {
-      ProfScope ps("lp_choose_cta", s);
-      (::gp::count_launch(), k_choose_cta<EW, LQ><<<grid_for(cap[5], 1, nsm * 3), kCtaThreads, kCtaCap * 16, s>>>(a));
-    }
-    if (cap[6]) {
-      ProfScope ps("lp_choose_hub", s);
-      (::gp::count_launch(), k_hub_prefix<<<1, 1024, 0, s>>>(a));
-      (::gp::count_launch(), k_hub_accum<EW, LQ><<<nsm * 4, 256, 0, s>>>(a));
-      (::gp::count_launch(), k_hub_choose<LQ><<<grid_for(cap[6], 1, nsm * 4), 256, 0, s>>>(a));
-    }
-    GP_LAUNCH_CHECK();
-    const int64_t mv_cap = a.g.n;
-    const int ag = grid_for(mv_cap, 256, nsm * 8);
-    (::gp::count_launch(), k_demand<<<ag, 256, 0, s>>>(a));
-    (::gp::count_launch(), k_admit<LQ><<<ag, 256, 0, s>>>(a));
-    (::gp::count_launch(), k_contest_small<<<1, 1024, 0, s>>>(a));
-    {
-      LpArgs aa = a;
-      void *params[] = {(void *)&aa, (void *)&bar};
-      count_launch();
-      GP_CUDA(cudaLaunchCooperativeKernel((void *)k_contest_large<LQ>, coop_grid, 256, params, 0, s));
-    }
-    (::gp::count_launch(), k_apply<<<grid_for(mv_cap, 8, nsm * 8), 256, 0, s>>>(a));
-    GP_LAUNCH_CHECK();
-    return GP_OK;
+int max_coop_blocks(int *out) {
+  static int cached[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  if (!cached[EW][LQ]) {
+    GP_CUDA(cudaFuncSetAttribute(k_lp<EW, LQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
+    int per_sm = 0;
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp<EW, LQ>, kThreads, kDynSmem));
+    cached[EW][LQ] = std::max(1, per_sm);
   }
-};
-
-bool g_attr_done[3][2] = {{false, false}, {false, false}, {false, false}};
-
-template <int EW, bool LQ>
-int set_attrs() {
-  if (g_attr_done[EW][LQ]) return GP_OK;
-  GP_CUDA(cudaFuncSetAttribute(k_choose_warp<EW, LQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kWarpsPerBlock * kWarpCap * 16));
-  GP_CUDA(cudaFuncSetAttribute(k_choose_cta<EW, LQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtaCap * 16));
-  g_attr_done[EW][LQ] = true;
+  *out = cached[EW][LQ] * num_sms();
   return GP_OK;
 }
 
+int coop_capacity(int ew, bool lq, int *out) {
+  if (lq) return ew == 0 ? max_coop_blocks<0, true>(out) : ew == 1 ? max_coop_blocks<1, true>(out) : max_coop_blocks<2, true>(out);
+  return ew == 0 ? max_coop_blocks<0, false>(out) : ew == 1 ? max_coop_blocks<1, false>(out) : max_coop_blocks<2, false>(out);
+}
+
 template <int EW, bool LQ>
-int run_rounds(LpArgs a, const int64_t cap[kBins], int rounds, uint64_t seed, uint8_t *act_buf[2],
-               cudaStream_t s, GridBarrier bar, int coop_grid) {
-  GP_TRY(set_attrs<EW, LQ>());
-  const int nsm = num_sms();
-  const int warp_grid_cap = max_blocks(k_choose_warp<EW, LQ>, kWarpsPerBlock * 32, kWarpsPerBlock * kWarpCap * 16);
-  const int cls_grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.g.n + 255) / 256, nsm * 8));
-  for (int r = 0; r < rounds; r++) {
-    a.round = r;
-    a.act = act_buf[r & 1];
-    a.act_next = act_buf[(r + 1) & 1];
-    GP_CUDA(cudaMemsetAsync(a.act_next, 0, (size_t)a.g.n, s));
-    const uint64_t rmix = mix64(a.smix ^ (uint64_t)r);
-    for (int sub = 0; sub < 2; sub++) {
-      a.sub = sub;
-      (::gp::count_launch(), k_sub_reset<<<1, 32, 0, s>>>(a.ctr));
-      (::gp::count_launch(), k_classify<<<cls_grid, 256, 0, s>>>(a, rmix));
-      GP_TRY((LpKernels<EW, LQ>::launch_sub(a, cap, warp_grid_cap, s, bar, coop_grid)));
-    }
-    (::gp::count_launch(), k_round_end<<<1, 32, 0, s>>>(a.ctr));
-    GP_LAUNCH_CHECK();
-  }
+int launch_lp(const LpProblem *probs_dev, const int *block_prob_dev, int grid, cudaStream_t s) {
+  void *args[] = {(void *)&probs_dev, (void *)&block_prob_dev};
+  count_launch();
+  GP_CUDA(cudaLaunchCooperativeKernel((void *)k_lp<EW, LQ>, grid, kThreads, args, kDynSmem, s));
   return GP_OK;
 }
 
@@ -1108,19 +1237,207 @@ int run_rounds(LpArgs a, const int64_t cap[kBins], int rounds, uint64_t seed, ui
 LpConfig lp_config_from(const gp_params *p) {
   LpConfig c;
   if (p) {
-    if (p->deg_warp > 0) c.deg_warp = std::max(32, std::min(256, (int)p->deg_warp));
-    if (p->deg_cta > 0) c.deg_cta = std::max(c.deg_warp, std::min(2048, (int)p->deg_cta));
+    if (p->deg_warp > 0) c.deg_warp = (int)p->deg_warp;
+    if (p->deg_cta > 0) c.deg_cta = (int)p->deg_cta;
   }
-  if (c.deg_cta < c.deg_warp) c.deg_cta = c.deg_warp;
+  c.deg_warp = std::max(32, std::min(c.deg_warp, kWarpCap / 2));
+  c.deg_cta = std::max(c.deg_warp, std::min(c.deg_cta, kCtaCap / 2));
   return c;
 }
 
 int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, int *bad_dev, cudaStream_t s) {
   GP_CUDA(cudaMemsetAsync(bw, 0, sizeof(int64_t) * (size_t)std::max<int64_t>(k, 1), s));
   if (g.n == 0) return GP_OK;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, num_sms() * 8));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, num_sms() * 4));
   (::gp::count_launch(), k_block_weights<<<grid, 256, 0, s>>>(g, part, k, bw, bad_dev));
   GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+// Several independent LP runs in one cooperative launch (same edge-weight type and score use).
+int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg) {
+  if (njobs <= 0) return GP_OK;
+  const int ew = jobs[0].g.ew_mode();
+  const bool lq = jobs[0].q != nullptr;
+  for (int j = 0; j < njobs; j++) {
+    if (jobs[j].stats) std::memset(jobs[j].stats, 0, sizeof(gp_lp_stats));
+    if (jobs[j].g.ew_mode() != ew || (jobs[j].q != nullptr) != lq) {
+      set_error("run_lp_multi: jobs of one launch must share weight type and score use");
+      return GP_ERR_INTERNAL;
+    }
+    if (jobs[j].g.n >= (int64_t)1 << 31 || jobs[j].nl >= (int64_t)1 << 31) {
+      set_error("label propagation supports n < 2^31");
+      return GP_ERR_UNSUPPORTED;
+    }
+  }
+  Workspace ws(s);
+  int cap_blocks = 0;
+  GP_TRY(coop_capacity(ew, lq, &cap_blocks));
+  if (njobs > cap_blocks) {
+    set_error("run_lp_multi: more jobs than co-resident blocks");
+    return GP_ERR_UNSUPPORTED;
+  }
+  const int nsm = num_sms();
+  // blocks per job: about one block per 256 vertices, within the co-resident capacity
+  std::vector<int64_t> want(njobs);
+  int64_t total_want = 0;
+  for (int j = 0; j < njobs; j++) {
+    want[j] = std::max<int64_t>(1, std::min<int64_t>(cap_blocks, (jobs[j].g.n + 255) / 256));
+    total_want += want[j];
+  }
+  if (total_want > cap_blocks)
+    for (int j = 0; j < njobs; j++) want[j] = std::max<int64_t>(1, want[j] * (cap_blocks - njobs) / total_want);
+  std::vector<LpProblem> hp(njobs);
+  std::vector<int> block_prob;
+  unsigned *classes;
+  GP_TRY(ws.zeros(&classes, (size_t)8 * njobs));
+  for (int j = 0; j < njobs; j++) {
+    const DGraph &g = jobs[j].g;
+    if (g.n > 0) {
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, nsm * 8));
+      (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(g, cfg.deg_warp, cfg.deg_cta, classes + 8 * j));
+      GP_LAUNCH_CHECK();
+    }
+  }
+  std::vector<unsigned> hcls(8 * (size_t)njobs);
+  GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  std::vector<LpCounters *> ctrs(njobs);
+  for (int j = 0; j < njobs; j++) {
+    const LpJob &jb = jobs[j];
+    LpProblem &P = hp[j];
+    std::memset(&P, 0, sizeof(P));
+    P.g = jb.g;
+    P.nl = jb.nl;
+    P.U = jb.U;
+    P.smix = mix64(jb.seed);
+    P.rounds = jb.g.n > 0 ? jb.rounds : 0;
+    P.deg_warp = cfg.deg_warp;
+    P.deg_cta = cfg.deg_cta;
+    P.labels = jb.labels;
+    P.lw = jb.lw;
+    P.q = jb.q;
+    P.block_begin = (int)block_prob.size();
+    P.block_count = (int)want[j];
+    for (int64_t b = 0; b < want[j]; b++) block_prob.push_back(j);
+    const size_t n = (size_t)std::max<int64_t>(jb.g.n, 1);
+    int64_t slots_total = 0;
+    for (int b = 0; b < kBins; b++) {
+      GP_TRY(ws.get(&P.bin[b], (size_t)std::max<unsigned>(hcls[8 * j + b], 1)));
+      P.bin_base[b] = slots_total;
+      slots_total += hcls[8 * j + b];
+    }
+    GP_TRY(ws.get(&P.mv_v, n));
+    GP_TRY(ws.get(&P.mv_t, n));
+    GP_TRY(ws.get(&P.mv_gain, n));
+    GP_TRY(ws.get(&P.mv_q, n));
+    GP_TRY(ws.get(&P.mv_adm, n));
+    GP_TRY(ws.get(&P.mv_of_v, n));
+    GP_TRY(ws.zeros(&P.demand, (size_t)std::max<int64_t>(jb.nl, 1)));
+    GP_TRY(ws.get(&P.ct, n));
+    GP_TRY(ws.get(&P.ct2, n));
+    GP_TRY(ws.get(&P.act[0], n));
+    GP_TRY(ws.get(&P.act[1], n));
+    GP_TRY(ws.get(&P.hist, (size_t)want[j] * 256 + 16));
+    GP_TRY(ws.get(&P.hoff, (size_t)want[j] * 256 + 256 + 16));
+    GP_TRY(ws.zeros(&P.ctr, 1));
+    GP_TRY(ws.zeros(&P.bar, barrier_words((unsigned)want[j])));
+    ctrs[j] = P.ctr;
+    const unsigned nhub = hcls[8 * j + 6];
+    if (nhub) {
+      int32_t *hub_of;
+      int64_t *hub_cap, *hub_base, *total;
+      unsigned *hcount;
+      GP_TRY(ws.get(&hub_of, n));
+      GP_TRY(ws.get(&hub_cap, (size_t)nhub + 1));
+      GP_TRY(ws.get(&hub_base, (size_t)nhub + 1));
+      GP_TRY(ws.get(&total, 1));
+      GP_TRY(ws.zeros(&hcount, 1));
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((jb.g.n + 255) / 256, nsm * 8));
+      (::gp::count_launch(), k_hub_mark<<<grid, 256, 0, s>>>(jb.g, cfg.deg_cta, hub_of, hub_cap, hcount));
+      GP_LAUNCH_CHECK();
+      GP_TRY(scan_excl_i64(hub_cap, hub_base, nhub, total, ws));
+      int64_t slots = 0;
+      GP_CUDA(cudaMemcpyAsync(&slots, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      GP_TRY(ws.get(&P.hub_keys, (size_t)slots));
+      GP_TRY(ws.zeros(&P.hub_vals, (size_t)slots));
+      GP_TRY(ws.zeros(&P.hub_qv, (size_t)slots));
+      GP_CUDA(cudaMemsetAsync(P.hub_keys, 0xff, sizeof(int32_t) * (size_t)slots, s));
+      GP_TRY(ws.get(&P.hub_c0, (size_t)nhub));
+      GP_TRY(ws.get(&P.hub_prefix, (size_t)nhub + 1));
+      P.hub_of = hub_of;
+      P.hub_base = hub_base;
+      P.has_hubs = 1;
+    }
+  }
+  LpProblem *probs_dev;
+  int *bp_dev;
+  GP_TRY(ws.get(&probs_dev, hp.size()));
+  GP_TRY(ws.get(&bp_dev, block_prob.size()));
+  GP_CUDA(cudaMemcpyAsync(probs_dev, hp.data(), sizeof(LpProblem) * hp.size(), cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(bp_dev, block_prob.data(), sizeof(int) * block_prob.size(), cudaMemcpyHostToDevice, s));
+  const int grid = (int)block_prob.size();
+  {
+    ProfScope ps("lp_persistent", s);
+    int st;
+    if (lq) st = ew == 0 ? launch_lp<0, true>(probs_dev, bp_dev, grid, s)
+               : ew == 1 ? launch_lp<1, true>(probs_dev, bp_dev, grid, s)
+                         : launch_lp<2, true>(probs_dev, bp_dev, grid, s);
+    else st = ew == 0 ? launch_lp<0, false>(probs_dev, bp_dev, grid, s)
+              : ew == 1 ? launch_lp<1, false>(probs_dev, bp_dev, grid, s)
+                        : launch_lp<2, false>(probs_dev, bp_dev, grid, s);
+    GP_TRY(st);
+  }
+  std::vector<LpCounters> hc(njobs);
+  for (int j = 0; j < njobs; j++)
+    GP_CUDA(cudaMemcpyAsync(&hc[j], ctrs[j], sizeof(LpCounters), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  int64_t tot_edges = 0, tot_vis = 0, tot_bytes = 0;
+  for (int j = 0; j < njobs; j++) {
+    const LpCounters &h = hc[j];
+    if (h.err) {
+      set_error("label propagation: a bounded device barrier gave up");
+      return GP_ERR_TIMEOUT;
+    }
+    int64_t vis = 0, edg = 0;
+    for (int b = 0; b < 8; b++) {
+      vis += (int64_t)h.bin_visits[b];
+      edg += (int64_t)h.bin_edges[b];
+    }
+    const DGraph &g = jobs[j].g;
+    // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read;
+    // per scanned entry: adjacency, neighbour label, edge weight (and score)
+    tot_bytes += vis * (2 * g.offset_bytes() + 4 + g.vw_bytes() + 8) + edg * (8 + g.ew_bytes() + (jobs[j].q ? 4 : 0));
+    tot_edges += edg;
+    tot_vis += vis;
+    if (jobs[j].stats) {
+      jobs[j].stats->rounds = (int64_t)h.rounds;
+      jobs[j].stats->moves = (int64_t)h.moves;
+      jobs[j].stats->movers = (int64_t)h.movers;
+      jobs[j].stats->visits = vis;
+      jobs[j].stats->edges = edg;
+    }
+  }
+  prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
+  if (profiling()) {
+    static const char *names[6] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hubs", "lp_phase_admit",
+                                   "lp_phase_contest", "lp_phase_apply"};
+    for (int ph = 0; ph < 6; ph++) {
+      double ms = 0;
+      for (int j = 0; j < njobs; j++) ms += hc[j].phase_ns[ph] * 1e-6;
+      prof_add_time(names[ph], ms);
+    }
+    double cs = 0, cp = 0, cl = 0;
+    for (int j = 0; j < njobs; j++) {
+      cs += hc[j].contest_small;
+      cp += hc[j].contest_packed;
+      cl += hc[j].contest_large;
+    }
+    prof_add_counts("lp_contest_small_calls", (int64_t)cs, 0, 0);
+    prof_add_counts("lp_contest_packed_calls", (int64_t)cp, 0, 0);
+    prof_add_counts("lp_contest_large_calls", (int64_t)cl, 0, 0);
+  }
   return GP_OK;
 }
 
@@ -1128,127 +1445,17 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
            uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (g.n == 0 || rounds <= 0) return GP_OK;
-  if (g.n >= (int64_t)1 << 31 || nl >= (int64_t)1 << 31) {
-    set_error("label propagation supports n < 2^31");
-    return GP_ERR_UNSUPPORTED;
-  }
-  Workspace ws(s);
-  LpCounters *ctr;
-  GP_TRY(ws.zeros(&ctr, 1));
-  const int nsm = num_sms();
-  const int grid_n = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, nsm * 8));
-  (::gp::count_launch(), k_degree_classes<<<grid_n, 256, 0, s>>>(g, cfg.deg_warp, cfg.deg_cta, ctr));
-  GP_LAUNCH_CHECK();
-  LpCounters h;
-  GP_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
-  int64_t cap[kBins];
-  for (int b = 0; b < kBins; b++) cap[b] = h.bin_count[b];
-  GP_CUDA(cudaMemsetAsync(ctr, 0, sizeof(LpCounters), s));
-
-  LpArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.g = g;
-  a.nl = nl;
-  a.U = U;
-  a.smix = mix64(seed);
-  a.labels = labels;
-  a.lw = lw;
-  a.q = q;
-  a.deg_warp = cfg.deg_warp;
-  a.deg_cta = cfg.deg_cta;
-  a.ctr = ctr;
-  for (int b = 0; b < kBins; b++) GP_TRY(ws.get(&a.bin[b], (size_t)std::max<int64_t>(cap[b], 1)));
-  const size_t n = (size_t)g.n;
-  GP_TRY(ws.get(&a.mv_v, n));
-  GP_TRY(ws.get(&a.mv_t, n));
-  GP_TRY(ws.get(&a.mv_gain, n));
-  GP_TRY(ws.get(&a.mv_q, n));
-  GP_TRY(ws.get(&a.mv_adm, n));
-  GP_TRY(ws.zeros(&a.demand, (size_t)nl));
-  GP_TRY(ws.get(&a.ct, n));
-  GP_TRY(ws.get(&a.ct2, n));
-  uint8_t *act_buf[2];
-  GP_TRY(ws.get(&act_buf[0], n));
-  GP_TRY(ws.get(&act_buf[1], n));
-  GP_CUDA(cudaMemsetAsync(act_buf[0], 0, n, s));
-  if (cap[6]) {
-    int32_t *hub_of;
-    int64_t *hub_cap;
-    unsigned *hcount;
-    GP_TRY(ws.get(&hub_of, n));
-    GP_TRY(ws.get(&hub_cap, (size_t)cap[6] + 1));
-    GP_TRY(ws.zeros(&hcount, 1));
-    (::gp::count_launch(), k_hub_mark<<<grid_n, 256, 0, s>>>(g, cfg.deg_cta, hub_of, hub_cap, hcount));
-    GP_LAUNCH_CHECK();
-    int64_t *hub_base, *total;
-    GP_TRY(ws.get(&hub_base, (size_t)cap[6] + 1));
-    GP_TRY(ws.get(&total, 1));
-    GP_TRY(scan_excl_i64(hub_cap, hub_base, cap[6], total, ws));
-    int64_t slots = 0;
-    GP_CUDA(cudaMemcpyAsync(&slots, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaStreamSynchronize(s));
-    GP_TRY(ws.get(&a.hub_keys, (size_t)slots));
-    GP_TRY(ws.zeros(&a.hub_vals, (size_t)slots));
-    GP_TRY(ws.zeros(&a.hub_qv, (size_t)slots));
-    GP_CUDA(cudaMemsetAsync(a.hub_keys, 0xff, sizeof(int32_t) * (size_t)slots, s));
-    GP_TRY(ws.get(&a.hub_c0, (size_t)cap[6]));
-    GP_TRY(ws.get(&a.hub_prefix, (size_t)cap[6] + 1));
-    a.hub_of = hub_of;
-    a.hub_base = hub_base;
-  }
-  // cooperative admission grid
-  int coop_per_sm = 0;
-  void *klarge = q ? (void *)k_contest_large<true> : (void *)k_contest_large<false>;
-  GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_per_sm, klarge, 256, 0));
-  const int coop_grid = std::max(1, std::min(coop_per_sm, 2)) * nsm;
-  GP_TRY(ws.get(&a.hist, (size_t)coop_grid * 256 + 16));
-  GP_TRY(ws.get(&a.hoff, (size_t)coop_grid * 256 + 256 + 16));
-  GridBarrier bar{&ctr->bar_count, &ctr->bar_gen, &ctr->err};
-
-  const int ew = g.ew_mode();
-  int st;
-  if (q) {
-    st = ew == 0 ? run_rounds<0, true>(a, cap, rounds, seed, act_buf, s, bar, coop_grid)
-       : ew == 1 ? run_rounds<1, true>(a, cap, rounds, seed, act_buf, s, bar, coop_grid)
-                 : run_rounds<2, true>(a, cap, rounds, seed, act_buf, s, bar, coop_grid);
-  } else {
-    st = ew == 0 ? run_rounds<0, false>(a, cap, rounds, seed, act_buf, s, bar, coop_grid)
-       : ew == 1 ? run_rounds<1, false>(a, cap, rounds, seed, act_buf, s, bar, coop_grid)
-                 : run_rounds<2, false>(a, cap, rounds, seed, act_buf, s, bar, coop_grid);
-  }
-  GP_TRY(st);
-  GP_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
-  if (h.err) {
-    set_error("label propagation: bounded device wait gave up");
-    return GP_ERR_TIMEOUT;
-  }
-  if (profiling()) {
-    static const char *names[kBins] = {"lp_choose_g4", "lp_choose_g8", "lp_choose_g16", "lp_choose_g32",
-                                       "lp_choose_warp", "lp_choose_cta", "lp_choose_hub"};
-    const int64_t ob = g.offset_bytes(), vb = g.vw_bytes(), eb = g.ew_bytes();
-    for (int b = 0; b < kBins; b++) {
-      const int64_t vis = (int64_t)h.bin_visits[b], edg = (int64_t)h.bin_edges[b];
-      // algorithmic bytes: two offsets, own label, own weight, one label-weight read per vertex;
-      // per entry: adjacency, neighbour label, edge weight (and score)
-      const int64_t bytes = vis * (2 * ob + 4 + vb + 8) + edg * (8 + eb + (q ? 4 : 0));
-      prof_add_counts(names[b], vis, edg, bytes);
-    }
-  }
-  if (stats) {
-    stats->rounds = (int64_t)h.rounds;
-    stats->moves = (int64_t)h.moves;
-    stats->movers = (int64_t)h.movers;
-    int64_t vis = 0, edg = 0;
-    for (int b = 0; b < 8; b++) {
-      vis += (int64_t)h.bin_visits[b];
-      edg += (int64_t)h.bin_edges[b];
-    }
-    stats->visits = vis;
-    stats->edges = edg;
-  }
-  return GP_OK;
+  LpJob j;
+  j.g = g;
+  j.q = q;
+  j.labels = labels;
+  j.lw = lw;
+  j.nl = nl;
+  j.U = U;
+  j.rounds = rounds;
+  j.seed = seed;
+  j.stats = stats;
+  return run_lp_multi(&j, 1, s, cfg);
 }
 
 }  // namespace gp

@@ -6,10 +6,26 @@
 namespace gp {
 
 struct LpConfig {
-  int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 256)
-  int deg_cta = 2048;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 2048)
+  int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 128)
+  int deg_cta = 1024;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 1024)
                         // d > deg_cta: several CTAs per vertex, global-memory hash
 };
+
+// One LP run for run_lp_multi.
+struct LpJob {
+  DGraph g;
+  const int32_t *q = nullptr;
+  int32_t *labels = nullptr;
+  int64_t *lw = nullptr;
+  int64_t nl = 0, U = 0;
+  int rounds = 0;
+  uint64_t seed = 0;
+  gp_lp_stats *stats = nullptr;
+};
+
+// Several independent LP runs in one cooperative launch; they must share the edge-weight type and
+// whether scores are given.
+int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg);
 
 LpConfig lp_config_from(const gp_params *p);
 

@@ -237,14 +237,29 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     int best = -1;
     int64_t best_cut = 0, best_imb = 0;
     std::vector<int64_t> hbw(k);
+    // the tries' LP refinements run as independent problems of one launch
+    int64_t *bws;
+    GP_TRY(ws.get(&bws, (size_t)tries * k));
+    std::vector<LpJob> jobs(tries);
+    std::vector<gp_lp_stats> tstats(tries);
     for (int t = 0; t < tries; t++) {
       int32_t *pt = parts + (size_t)t * gc.n;
       const uint64_t s_try = hash3(seed, (uint64_t)levels, (uint64_t)(4 + t));
-      GP_TRY(block_weights(gc, pt, k, bw, nullptr, s));
-      gp_lp_stats ls;
-      GP_TRY(run_lp(gc, nullptr, pt, bw, k, lmax, (int)p.rounds_refine, hash3(s_try, (uint64_t)levels, 3), &ls, s, cfg));
-      lp_edges += ls.edges;
-      lp_moves += ls.moves;
+      GP_TRY(block_weights(gc, pt, k, bws + (size_t)t * k, nullptr, s));
+      jobs[t].g = gc;
+      jobs[t].labels = pt;
+      jobs[t].lw = bws + (size_t)t * k;
+      jobs[t].nl = k;
+      jobs[t].U = lmax;
+      jobs[t].rounds = (int)p.rounds_refine;
+      jobs[t].seed = hash3(s_try, (uint64_t)levels, 3);
+      jobs[t].stats = &tstats[t];
+    }
+    if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg));
+    for (int t = 0; t < tries; t++) {
+      int32_t *pt = parts + (size_t)t * gc.n;
+      lp_edges += tstats[t].edges;
+      lp_moves += tstats[t].moves;
       int64_t cut = 0;
       GP_TRY(eval_cut(gc, pt, k, &cut, bw, s));
       GP_CUDA(cudaMemcpyAsync(hbw.data(), bw, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, s));
