@@ -15,6 +15,7 @@
 #include <climits>
 
 #include "contract.cuh"
+#include "sort.cuh"
 
 namespace gp {
 
@@ -92,10 +93,6 @@ struct RowArgs {
   const int32_t *list;
   const unsigned *count;
   const int64_t *dsum;
-  // large rows
-  const int64_t *lofs;
-  int32_t *ka, *kb;
-  int64_t *va, *vb;
   int key_bits;
 };
 
@@ -167,80 +164,7 @@ __global__ void __launch_bounds__(256) k_row_warp(RowArgs a) {
   }
 }
 
-// Stable block-wide scatter of one 8-bit digit, tile by tile (blockDim.x == 256).
-__device__ void block_scatter_pass(const int32_t *ks, const long long *vs, int32_t *kd, long long *vd, int P,
-                                   int shift, unsigned *hist, unsigned *base, unsigned (*wcnt)[256]) {
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < P; t += blockDim.x) atomicAdd(&hist[((unsigned)ks[t] >> shift) & 255], 1u);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned acc = 0;
-    for (int t = 0; t < 256; t++) {
-      base[t] = acc;
-      acc += hist[t];
-    }
-  }
-  __syncthreads();
-  const int wid = threadIdx.x >> 5;
-  for (int t0 = 0; t0 < P; t0 += blockDim.x) {
-    const int p = t0 + threadIdx.x;
-    const bool valid = p < P;
-    const int key = valid ? ks[p] : 0;
-    const long long val = valid ? vs[p] : 0;
-    const int dg = valid ? (int)(((unsigned)key >> shift) & 255) : 256;
-    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) wcnt[k >> 8][k & 255] = 0;
-    __syncthreads();
-    const unsigned peers = __match_any_sync(kFull, dg);
-    const int rank = __popc(peers & lanemask_lt());
-    if (valid && rank == 0) wcnt[wid][dg] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      unsigned pre = 0;
-      for (int w = 0; w < wid; w++) pre += wcnt[w][dg];
-      const unsigned pos = base[dg] + pre + rank;
-      kd[pos] = key;
-      vd[pos] = val;
-    }
-    __syncthreads();
-    if (threadIdx.x < 256) {
-      unsigned s = 0;
-      for (int w = 0; w < 8; w++) s += wcnt[w][threadIdx.x];
-      base[threadIdx.x] += s;
-    }
-    __syncthreads();
-  }
-}
 
-// Writes the runs of the sorted pairs (ks, vs)[0, P) as unique (key, sum) into out at `dst`,
-// in key order; returns the number of unique keys (valid in every thread).
-__device__ int block_reduce_runs(const int32_t *ks, const long long *vs, int P, int32_t *okey, int64_t *oval,
-                                 int64_t dst) {
-  __shared__ long long tmp[32];
-  __shared__ long long tot_s;
-  __shared__ long long carry_s;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  for (int t0 = 0; t0 < P; t0 += blockDim.x) {
-    const int p = t0 + threadIdx.x;
-    const bool head = p < P && (p == 0 || ks[p - 1] != ks[p]);
-    const long long ex = block_excl_scan64((long long)(head ? 1 : 0), tmp, &tot_s);
-    if (head) {
-      long long sum = 0;
-      const int key = ks[p];
-      for (int q = p; q < P && ks[q] == key; q++) sum += vs[q];
-      const int64_t pos = dst + carry_s + ex;
-      okey[pos] = key;
-      oval[pos] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s += tot_s;
-    __syncthreads();
-  }
-  const int r = (int)carry_s;
-  __syncthreads();
-  return r;
-}
 
 __device__ __forceinline__ unsigned row_slot(int cu) { return (unsigned)cu * 0x9E3779B1u; }
 
@@ -432,63 +356,67 @@ __global__ void __launch_bounds__(kRowThreads) k_row_cta(RowArgs a) {
   }
 }
 
-// Rows with more than 4096 pairs: one CTA per row, pairs staged in global memory and sorted by a
-// block-wide LSD radix sort.
+// Rows with more than 4096 pairs: the pairs of all such rows are gathered into one array keyed by
+// (row index, neighbour id), sorted together by a device-wide radix sort and reduced by key.
+__global__ void k_large_index(const int32_t *list, const unsigned *count, int32_t *large_idx) {
+  const unsigned cnt = *count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    large_idx[list[i]] = (int32_t)i;
+}
+
 template <int EW>
-__global__ void __launch_bounds__(kRowThreads) k_row_large(RowArgs a) {
-  __shared__ unsigned sP;
-  __shared__ unsigned hist[256], base[256];
-  __shared__ unsigned wcnt[8][256];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const unsigned cnt = *a.count;
-  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
-    const int cv = a.list[i];
-    const int64_t mb = a.mstart[cv], me = a.mstart[cv + 1];
-    const int64_t lb = a.lofs[i];
-    int32_t *ka = a.ka + lb, *kb = a.kb + lb;
-    long long *va = reinterpret_cast<long long *>(a.va + lb), *vb = reinterpret_cast<long long *>(a.vb + lb);
-    if (threadIdx.x == 0) sP = 0;
-    __syncthreads();
-    for (int64_t m = mb + wid; m < me; m += nwarps) {
-      const int v = a.members[m];
-      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
-      for (int64_t x = b; x < e; x += 32) {
-        const int64_t j = x + lane;
-        const bool valid = j < e;
-        const int cu = valid ? a.f2c[__ldg(a.g.adj + j)] : -1;
-        const bool keep = valid && cu != cv;
-        const unsigned mask = __ballot_sync(kFull, keep);
-        if (!mask) continue;
-        const int leader = __ffs(mask) - 1;
-        unsigned pos = 0;
-        if (lane == leader) pos = atomicAdd(&sP, (unsigned)__popc(mask));
-        pos = __shfl_sync(kFull, pos, leader) + __popc(mask & lanemask_lt());
-        if (keep) {
-          ka[pos] = cu;
-          va[pos] = load_ew<EW>(a.g.ew, j);
-        }
-      }
+__global__ void k_large_gather(DGraph g, const int32_t *f2c, const int32_t *large_idx, const int64_t *lofs,
+                               unsigned long long *lfill, int kb, unsigned long long *keys,
+                               unsigned long long *vals) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = gw; v < g.n; v += nw) {
+    const int i = large_idx[f2c[v]];
+    if (i < 0) continue;
+    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
+    unsigned long long pos = 0;
+    if (lane == 0) pos = atomicAdd(&lfill[i], (unsigned long long)(e - b));
+    pos = __shfl_sync(kFull, pos, 0) + (unsigned long long)lofs[i];
+    for (int64_t x = b + lane; x < e; x += 32) {
+      const int cu = f2c[__ldg(g.adj + x)];
+      keys[pos + (x - b)] = ((unsigned long long)i << kb) | (unsigned long long)(unsigned)cu;
+      vals[pos + (x - b)] = (unsigned long long)load_ew<EW>(g.ew, x);
     }
-    __threadfence_block();
-    __syncthreads();
-    const int P = (int)sP;
-    int32_t *ks = ka, *kd = kb;
-    long long *vs = va, *vd = vb;
-    for (int shift = 0; shift < a.key_bits; shift += 8) {
-      block_scatter_pass(ks, vs, kd, vd, P, shift, hist, base, wcnt);
-      __threadfence_block();
-      __syncthreads();
-      int32_t *tk = ks;
-      ks = kd;
-      kd = tk;
-      long long *tv = vs;
-      vs = vd;
-      vd = tv;
-    }
-    const int u = block_reduce_runs(ks, vs, P, a.okey, a.oval, a.tstart[cv]);
-    if (threadIdx.x == 0) a.rowcnt[cv] = u;
-    __syncthreads();
   }
+}
+
+__global__ void k_large_heads(const unsigned long long *keys, int64_t N, int kb, const int32_t *list, int64_t *flag) {
+  const unsigned long long mask = (1ull << kb) - 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[j];
+    const int cv = list[k >> kb];
+    const bool head = (int)(k & mask) != cv && (j == 0 || keys[j - 1] != k);
+    flag[j] = head ? 1 : 0;
+  }
+}
+
+__global__ void k_large_write(const unsigned long long *keys, const unsigned long long *vals, int64_t N, int kb,
+                              const int32_t *list, const int64_t *uidx, const int64_t *lofs, const int64_t *tstart,
+                              int32_t *okey, int64_t *oval) {
+  const unsigned long long mask = (1ull << kb) - 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    if (uidx[j + 1] == uidx[j]) continue;  // not a head
+    const unsigned long long k = keys[j];
+    const int64_t i = (int64_t)(k >> kb);
+    long long sum = 0;
+    for (int64_t q = j; q < N && keys[q] == k; q++) sum += (long long)vals[q];
+    const int64_t out = tstart[list[i]] + (uidx[j] - uidx[lofs[i]]);
+    okey[out] = (int32_t)(k & mask);
+    oval[out] = sum;
+  }
+}
+
+__global__ void k_large_counts(const int32_t *list, const unsigned *count, const int64_t *uidx, const int64_t *lofs,
+                               int64_t *rowcnt) {
+  const unsigned cnt = *count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    rowcnt[list[i]] = uidx[lofs[i + 1]] - uidx[lofs[i]];
 }
 
 __global__ void k_large_sizes(const int32_t *list, const unsigned *count, const int64_t *dsum, int64_t *sz) {
@@ -545,12 +473,6 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[4], 
     const int sm = kCtaSlots * 12;
     set_smem(k_row_cta<EW>, sm);
     (::gp::count_launch(), k_row_cta<EW><<<grid_for(counts[1], 1, nsm * 2), kRowThreads, sm, s>>>(b));
-  }
-  if (counts[2]) {
-    RowArgs b = a;
-    b.list = lists[2];
-    b.count = counts_dev + 2;
-    (::gp::count_launch(), k_row_large<EW><<<grid_for(counts[2], 1, nsm * 4), kRowThreads, 0, s>>>(b));
   }
   GP_LAUNCH_CHECK();
   return GP_OK;
@@ -648,31 +570,58 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   a.members = members;
   a.tstart = tstart;
   a.dsum = dsum;
-  a.lofs = nullptr;
-  a.ka = a.kb = nullptr;
-  a.va = a.vb = nullptr;
   int kb = 0;
   while (kb < 31 && ((int64_t)1 << kb) < nc) kb++;
   a.key_bits = kb;
   GP_TRY(ws.get(&a.okey, (size_t)std::max<int64_t>(g.m, 1)));
   GP_TRY(ws.get(&a.oval, (size_t)std::max<int64_t>(g.m, 1)));
   GP_TRY(ws.get(&a.rowcnt, (size_t)nc + 1));
-  if (counts[2]) {
-    int64_t *sz, *lofs;
-    GP_TRY(ws.get(&sz, (size_t)counts[2]));
-    GP_TRY(ws.get(&lofs, (size_t)counts[2] + 1));
-    (::gp::count_launch(), k_large_sizes<<<grid_n(counts[2]), 256, 0, s>>>(lists[2], counts_dev + 2, dsum, sz));
-    GP_TRY(scan_excl_i64(sz, lofs, counts[2], lofs + counts[2], ws));
-    int64_t tot = 0;
-    GP_CUDA(cudaMemcpyAsync(&tot, lofs + counts[2], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaStreamSynchronize(s));
-    GP_TRY(ws.get(&a.ka, (size_t)tot));
-    GP_TRY(ws.get(&a.kb, (size_t)tot));
-    GP_TRY(ws.get(&a.va, (size_t)tot));
-    GP_TRY(ws.get(&a.vb, (size_t)tot));
-    a.lofs = lofs;
-  }
   const int ew = g.ew_mode();
+  if (counts[2]) {
+    // very large rows: gather, sort by (row, neighbour), reduce
+    ProfScope ps("contract_large_rows", s);
+    const unsigned R = counts[2];
+    int64_t *sz, *lofs;
+    GP_TRY(ws.get(&sz, (size_t)R));
+    GP_TRY(ws.get(&lofs, (size_t)R + 1));
+    (::gp::count_launch(), k_large_sizes<<<grid_n(R), 256, 0, s>>>(lists[2], counts_dev + 2, dsum, sz));
+    GP_TRY(scan_excl_i64(sz, lofs, R, lofs + R, ws));
+    int64_t N = 0;
+    GP_CUDA(cudaMemcpyAsync(&N, lofs + R, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    int32_t *large_idx;
+    unsigned long long *lfill, *k0, *v0, *k1, *v1;
+    GP_TRY(ws.get(&large_idx, (size_t)nc));
+    GP_CUDA(cudaMemsetAsync(large_idx, 0xff, sizeof(int32_t) * (size_t)nc, s));
+    GP_TRY(ws.zeros(&lfill, (size_t)R));
+    GP_TRY(ws.get(&k0, (size_t)N));
+    GP_TRY(ws.get(&v0, (size_t)N));
+    GP_TRY(ws.get(&k1, (size_t)N));
+    GP_TRY(ws.get(&v1, (size_t)N));
+    (::gp::count_launch(), k_large_index<<<grid_n(R), 256, 0, s>>>(lists[2], counts_dev + 2, large_idx));
+    int rb = 0;
+    while (rb < 31 && ((int64_t)1 << rb) < (int64_t)R) rb++;
+    const int kbits = std::max(kb, 1);
+    if (ew == 0)
+      (::gp::count_launch(), k_large_gather<0><<<grid_n(n * 32), 256, 0, s>>>(g, f2c, large_idx, lofs, lfill, kbits, k0, v0));
+    else if (ew == 1)
+      (::gp::count_launch(), k_large_gather<1><<<grid_n(n * 32), 256, 0, s>>>(g, f2c, large_idx, lofs, lfill, kbits, k0, v0));
+    else
+      (::gp::count_launch(), k_large_gather<2><<<grid_n(n * 32), 256, 0, s>>>(g, f2c, large_idx, lofs, lfill, kbits, k0, v0));
+    GP_LAUNCH_CHECK();
+    bool in_tmp = false;
+    GP_TRY(radix_sort_pairs(k0, v0, k1, v1, N, rb + kbits, &in_tmp, ws));
+    unsigned long long *ks = in_tmp ? k1 : k0, *vs = in_tmp ? v1 : v0;
+    int64_t *flag, *uidx;
+    GP_TRY(ws.get(&flag, (size_t)N));
+    GP_TRY(ws.get(&uidx, (size_t)N + 1));
+    (::gp::count_launch(), k_large_heads<<<grid_n(N), 256, 0, s>>>(ks, N, kbits, lists[2], flag));
+    GP_TRY(scan_excl_i64(flag, uidx, N, uidx + N, ws));
+    (::gp::count_launch(), k_large_write<<<grid_n(N), 256, 0, s>>>(ks, vs, N, kbits, lists[2], uidx, lofs, tstart,
+                                                                   a.okey, a.oval));
+    (::gp::count_launch(), k_large_counts<<<grid_n(R), 256, 0, s>>>(lists[2], counts_dev + 2, uidx, lofs, a.rowcnt));
+    GP_LAUNCH_CHECK();
+  }
   GP_TRY(ew == 0 ? build_rows<0>(a, counts_dev, counts, lists, s)
        : ew == 1 ? build_rows<1>(a, counts_dev, counts, lists, s)
                  : build_rows<2>(a, counts_dev, counts, lists, s));
