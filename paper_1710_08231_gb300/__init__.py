@@ -131,6 +131,7 @@ def lib():
         L.gp_mlp_train.argtypes = [VP, VP, I64, VP, I32, ctypes.c_float, VP, VP]
         L.gp_mlp_grad.restype = ctypes.c_int
         L.gp_mlp_grad.argtypes = [VP, VP, I64, VP, VP, VP, VP]
+        L.gp_mlp_train.argtypes = [VP, VP, I64, VP, I32, ctypes.c_float, VP, VP]
         L.gp_partition_batch.restype = ctypes.c_int
         L.gp_partition_batch.argtypes = [ctypes.POINTER(GpBatchItem), I32, ctypes.POINTER(GpParams),
                                          ctypes.POINTER(GpResult), VP]
@@ -428,3 +429,76 @@ def profile_read(reset: bool = False) -> list:
     n = lib().gp_profile_read(buf, 64, 1 if reset else 0)
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "ms": buf[i].ms, "items": buf[i].items,
              "edges": buf[i].edges, "bytes": buf[i].bytes} for i in range(n)]
+
+
+# ---------------------------------------------------------------------------------------------- learned
+MLP_BYTES = 256 * 2 + 32 * 2 + 32 * 4 + 4 + 7 * 4  # sizeof(gp_mlp)
+
+
+def _bf16_bits(a) -> np.ndarray:
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t.view(torch.int16).numpy().view(np.uint16)
+
+
+def bf16_round(a) -> np.ndarray:
+    """Values of `a` rounded to bfloat16 (round to nearest even), as float64."""
+    bits = _bf16_bits(a).astype(np.uint32) << 16
+    return bits.view(np.float32).astype(np.float64)
+
+
+def mlp_pack(w1, b1, w2, b2, device="cuda"):
+    """A device gp_mlp (uint8 tensor): w1 [32,8] and w2 [32] rounded to bfloat16, biases float32."""
+    import torch
+    buf = np.zeros(MLP_BYTES, dtype=np.uint8)
+    buf[0:512] = _bf16_bits(np.asarray(w1, dtype=np.float32).reshape(256)).view(np.uint8)
+    buf[512:576] = _bf16_bits(np.asarray(w2, dtype=np.float32).reshape(32)).view(np.uint8)
+    buf[576:704] = np.asarray(b1, dtype=np.float32).reshape(32).view(np.uint8)
+    buf[704:708] = np.asarray([b2], dtype=np.float32).view(np.uint8)
+    return torch.from_numpy(buf).to(device)
+
+
+def mlp_unpack(t):
+    """(w1 [32,8], b1 [32], w2 [32], b2) as float64 from a device gp_mlp."""
+    buf = t.cpu().numpy()
+    w1 = (buf[0:512].view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64).reshape(32, 8)
+    w2 = (buf[512:576].view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    b1 = buf[576:704].view(np.float32).astype(np.float64)
+    b2 = float(buf[704:708].view(np.float32)[0])
+    return w1, b1, w2, b2
+
+
+def edge_features(dg: DeviceGraph, level: int, stream=None):
+    """Per-entry features [m_dir, 8] (float32, device)."""
+    import torch
+    out = torch.empty((max(dg.m_dir, 1), 8), dtype=torch.float32, device=dg.adj.device)
+    _check(lib().gp_edge_features(ctypes.byref(dg.desc), level, out.data_ptr(), _stream(stream)), "gp_edge_features")
+    return out[: dg.m_dir]
+
+
+def mlp_score(dg: DeviceGraph, level: int, mlp, stream=None):
+    """Scores s (float32) and q = round-half-even(s * 2^15) (int32) of every CSR entry."""
+    import torch
+    s = torch.empty(max(dg.m_dir, 1), dtype=torch.float32, device=dg.adj.device)
+    q = torch.empty(max(dg.m_dir, 1), dtype=torch.int32, device=dg.adj.device)
+    _check(lib().gp_mlp_score(ctypes.byref(dg.desc), level, mlp.data_ptr(), s.data_ptr(), q.data_ptr(),
+                              _stream(stream)), "gp_mlp_score")
+    return s[: dg.m_dir], q[: dg.m_dir]
+
+
+def mlp_train(feat, y, mlp, steps: int, lr: float, stream=None) -> np.ndarray:
+    """Full-batch Adam on (feat [m,8] float32, y [m] float32), updating `mlp` in place; returns the loss
+    before each step."""
+    losses = np.zeros(steps, dtype=np.float32)
+    _check(lib().gp_mlp_train(feat.data_ptr(), y.data_ptr(), int(feat.shape[0]), mlp.data_ptr(), steps, lr,
+                              losses.ctypes.data, _stream(stream)), "gp_mlp_train")
+    return losses
+
+
+def mlp_grad(feat, y, mlp, stream=None):
+    """(mean loss, gradient [321] = dW1 (row-major), db1, dW2, db2) in FP32 from the bf16 weights."""
+    loss = ctypes.c_float(0)
+    grad = np.zeros(321, dtype=np.float32)
+    _check(lib().gp_mlp_grad(feat.data_ptr(), y.data_ptr(), int(feat.shape[0]), mlp.data_ptr(), ctypes.byref(loss),
+                             grad.ctypes.data, _stream(stream)), "gp_mlp_grad")
+    return float(loss.value), grad
