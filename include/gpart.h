@@ -276,9 +276,20 @@ typedef struct gp_batch_item {
   int32_t *part_out;  /* device, g.n entries */
 } gp_batch_item;
 
-/* Partition `count` graphs. res: host array of `count` results. */
+/* Partition `count` graphs in one call. Every graph is partitioned exactly as gp_partition would
+ * partition it alone (same seeds, bounds and result); the work of all graphs is shared: one
+ * cooperative LP launch per level covers every graph (each an independent problem), one contraction
+ * runs on the disjoint union of the level graphs, and one launch does the initial partitioning of
+ * every graph and try. Modes: GP_MODE_PLAIN or GP_MODE_LEARNED. The union of the graphs must have
+ * fewer than 2^31 - 1 vertices. res: host array of `count` results (times are for the whole call). */
 int gp_partition_batch(const gp_batch_item *items, int32_t count, const gp_params *params,
                        gp_result *res, gp_stream stream);
+
+/* Degree-bin schedule autotuner: times three LP rounds of g under a fixed set of (deg_warp, deg_cta)
+ * candidates and returns the fastest (results never depend on the schedule). ms_out: NULL or the
+ * best time. Pass the result in gp_params.deg_warp/deg_cta or to gp_lp_set_schedule. */
+int gp_autotune_schedule(const gp_graph *g, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
+                         gp_stream stream);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Profiling: when enabled, the library records CUDA events on the caller's stream around each

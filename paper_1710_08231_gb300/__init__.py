@@ -137,6 +137,8 @@ def lib():
                                          ctypes.POINTER(GpResult), VP]
         L.gp_lp_set_schedule.restype = ctypes.c_int
         L.gp_lp_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.gp_autotune_schedule.restype = ctypes.c_int
+        L.gp_autotune_schedule.argtypes = [ctypes.POINTER(GpGraph), VP, VP, VP, VP]
         L.gp_launch_count.restype = I64
         L.gp_launch_count.argtypes = [ctypes.c_int]
         L.gp_profile_enable.restype = ctypes.c_int
@@ -502,3 +504,33 @@ def mlp_grad(feat, y, mlp, stream=None):
     _check(lib().gp_mlp_grad(feat.data_ptr(), y.data_ptr(), int(feat.shape[0]), mlp.data_ptr(), ctypes.byref(loss),
                              grad.ctypes.data, _stream(stream)), "gp_mlp_grad")
     return float(loss.value), grad
+
+
+# ---------------------------------------------------------------------------------------------- batch
+def partition_batch(graphs, ks, eps, seeds, params: Optional[GpParams] = None, stream=None):
+    """Partitions several DeviceGraphs in one call; returns (list of part tensors, list of results)."""
+    import torch
+    n = len(graphs)
+    items = (GpBatchItem * max(n, 1))()
+    parts = []
+    for i, dg in enumerate(graphs):
+        part = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.adj.device)
+        parts.append(part)
+        items[i].g = dg.desc
+        items[i].k = int(ks[i])
+        items[i].eps = float(eps[i] if hasattr(eps, "__len__") else eps)
+        items[i].seed = int(seeds[i])
+        items[i].part_out = part.data_ptr()
+    res = (GpResult * max(n, 1))()
+    _check(lib().gp_partition_batch(items, n, ctypes.byref(params) if params else None, res, _stream(stream)),
+           "gp_partition_batch")
+    tries = params.ip_tries if params else 4
+    return [parts[i][: graphs[i].n] for i in range(n)], [_result(res[i], tries) for i in range(n)]
+
+
+def autotune_schedule(dg: DeviceGraph, stream=None):
+    """(deg_warp, deg_cta, ms) picked by timing LP rounds of dg under the candidate schedules."""
+    w, c, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+    _check(lib().gp_autotune_schedule(ctypes.byref(dg.desc), ctypes.byref(w), ctypes.byref(c), ctypes.byref(ms),
+                                      _stream(stream)), "gp_autotune_schedule")
+    return int(w.value), int(c.value), float(ms.value)

@@ -25,35 +25,48 @@ namespace {
 
 constexpr int kIpThreads = 1024;
 
-struct IpArgs {
+// One graph of an initial-partitioning launch: a local view (offsets and vertex weights shifted to its
+// first vertex; adjacency holds global ids, minus vbase gives local ids), its parameters and where its
+// tries' partitions and scratch live.
+struct IpGraph {
   DGraph g;
+  int64_t vbase;
   int k;
+  int level;
   int64_t lmax;
   uint64_t seed;
-  int level;
+  int32_t *parts;     // tries * n
+  int64_t ns;         // per-try stride of n-sized scratch: max(n, k)
+  int64_t scr_off;    // offset of this graph's n-sized scratch (tries * ns)
+  int64_t kscr_off;   // offset of this graph's k-sized scratch (tries * k)
+  int64_t conn_off;   // offset of this graph's repair connection scratch (tries * kIpThreads * k)
+};
+
+struct IpArgs {
+  const IpGraph *graphs;
+  const int *block_graph;
+  const int *block_try;
   int repair_rounds;
-  int64_t ns;                // per-try stride of the scratch arrays: max(n, k)
-  int32_t *part;             // tries * n
-  int32_t *gk;               // tries * n
-  int32_t *dist;             // tries * n
-  int32_t *qa, *qb;          // tries * n
-  unsigned long long *ka, *kb;  // tries * n
-  int32_t *va, *vb;          // tries * n
-  int32_t *mv_t;             // tries * n (repair: target per vertex)
-  long long *mv_g;           // tries * n (repair: gain per vertex)
-  uint8_t *flag;             // tries * n
-  long long *gws;            // tries * k
-  unsigned long long *gminh; // tries * k
-  int *gstart;               // tries * k
-  unsigned long long *gfar;  // tries * k
-  long long *bw;             // tries * k
-  long long *conn;           // tries * kIpThreads * k
+  int32_t *gk;               // n-sized scratch arrays
+  int32_t *dist;
+  int32_t *qa, *qb;
+  unsigned long long *ka, *kb;
+  int32_t *va, *vb;
+  int32_t *mv_t;
+  long long *mv_g;
+  uint8_t *flag;
+  long long *gws;            // k-sized scratch arrays
+  unsigned long long *gminh;
+  int *gstart;
+  unsigned long long *gfar;
+  long long *bw;
+  long long *conn;
   int *err;
 };
 
 // Multi-source BFS restricted to same-set vertices (part equal, set still being split).
-__device__ void set_bfs(const IpArgs &a, int32_t *part, int32_t *gk, int32_t *dist, int32_t *qa, int32_t *qb,
-                        int nf) {
+__device__ void set_bfs(const DGraph &g, int64_t vbase, int32_t *part, int32_t *gk, int32_t *dist, int32_t *qa,
+                        int32_t *qb, int nf) {
   __shared__ int s_next;
   while (nf > 0) {
     if (threadIdx.x == 0) s_next = 0;
@@ -64,9 +77,9 @@ __device__ void set_bfs(const IpArgs &a, int32_t *part, int32_t *gk, int32_t *di
       const int x = qa[i];
       const int px = part[x];
       const int dx = dist[x];
-      const int64_t b = a.g.row_begin(x), e = a.g.row_begin(x + 1);
+      const int64_t b = g.row_begin(x), e = g.row_begin(x + 1);
       for (int64_t j = b + lane; j < e; j += 32) {
-        const int u = a.g.adj[j];
+        const int u = (int)(g.adj[j] - vbase);
         if (gk[u] <= 1 || part[u] != px) continue;
         if (atomicCAS(&dist[u], -1, dx + 1) == -1) qb[atomicAdd(&s_next, 1)] = u;
       }
@@ -83,17 +96,20 @@ __device__ void set_bfs(const IpArgs &a, int32_t *part, int32_t *gk, int32_t *di
 __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
   __shared__ BlockSortSmem sm;
   __shared__ int s_any, s_maxd;
-  const int t = blockIdx.x;
-  const int n = (int)a.g.n, k = a.k;
-  const size_t ns = (size_t)a.ns;
-  int32_t *part = a.part + (size_t)t * n, *gk = a.gk + (size_t)t * ns, *dist = a.dist + (size_t)t * ns;
-  int32_t *qa = a.qa + (size_t)t * ns, *qb = a.qb + (size_t)t * ns;
-  unsigned long long *ka = a.ka + (size_t)t * ns, *kb = a.kb + (size_t)t * ns;
-  int32_t *va = a.va + (size_t)t * ns, *vb = a.vb + (size_t)t * ns;
-  long long *gws = a.gws + (size_t)t * k;
-  unsigned long long *gminh = a.gminh + (size_t)t * k, *gfar = a.gfar + (size_t)t * k;
-  int *gstart = a.gstart + (size_t)t * k;
-  const uint64_t s_try = hash3(a.seed, (uint64_t)a.level, (uint64_t)(4 + t));
+  const IpGraph &G = a.graphs[a.block_graph[blockIdx.x]];
+  const int t = a.block_try[blockIdx.x];
+  const DGraph g = G.g;
+  const int n = (int)g.n, k = G.k;
+  const size_t ns = (size_t)G.ns;
+  const size_t so = (size_t)G.scr_off + (size_t)t * ns, ko = (size_t)G.kscr_off + (size_t)t * k;
+  int32_t *part = G.parts + (size_t)t * n, *gk = a.gk + so, *dist = a.dist + so;
+  int32_t *qa = a.qa + so, *qb = a.qb + so;
+  unsigned long long *ka = a.ka + so, *kb = a.kb + so;
+  int32_t *va = a.va + so, *vb = a.vb + so;
+  long long *gws = a.gws + ko;
+  unsigned long long *gminh = a.gminh + ko, *gfar = a.gfar + ko;
+  int *gstart = a.gstart + ko;
+  const uint64_t s_try = hash3(G.seed, (uint64_t)G.level, (uint64_t)(4 + t));
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
     part[v] = 0;
     gk[v] = k;
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
       if (gk[v] <= 1) continue;
       const int b = part[v];
-      atomicAdd(reinterpret_cast<unsigned long long *>(&gws[b]), (unsigned long long)a.g.vweight(v));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&gws[b]), (unsigned long long)g.vweight(v));
       atomicMin(&gminh[b], (unsigned long long)mix64(hd ^ (uint64_t)v));
       dist[v] = -1;
     }
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
       dist[v] = 0;
     }
     __syncthreads();
-    set_bfs(a, part, gk, dist, qa, qb, nf);
+    set_bfs(g, G.vbase, part, gk, dist, qa, qb, nf);
     // farthest vertex per set, ties by smaller id
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
       if (gk[v] <= 1 || dist[v] < 0) continue;
@@ -156,7 +172,7 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
       dist[v] = 0;
     }
     __syncthreads();
-    set_bfs(a, part, gk, dist, qa, qb, nf);
+    set_bfs(g, G.vbase, part, gk, dist, qa, qb, nf);
     // order the vertices of every set by (set, unreachable, distance), stable in id order
     const int na = block_compact(n, [&](int v) { return gk[v] > 1; }, va, sm);
     for (int i = threadIdx.x; i < na; i += blockDim.x) atomicMax(&s_maxd, dist[va[i]]);
@@ -176,7 +192,7 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
     // side 0: shortest prefix of the set whose weight reaches ceil(kS/2)/kS of the set
     block_seg_scan(
         na, [&](int p) { return (int)(ks[p] >> (db + 1)); },
-        [&](int p) { return a.g.vweight(vs[p]); },
+        [&](int p) { return g.vweight(vs[p]); },
         [&](int p, long long excl, long long) {
           const int v = vs[p];
           const int base = (int)(ks[p] >> (db + 1));
@@ -200,30 +216,34 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
   __shared__ BlockSortSmem sm;
   __shared__ int s_over, s_light, s_applied;
   __shared__ long long s_gmin, s_gmax;
-  const int t = blockIdx.x;
-  const int n = (int)a.g.n, k = a.k;
-  const size_t ns = (size_t)a.ns;
-  int32_t *part = a.part + (size_t)t * n;
-  unsigned long long *ka = a.ka + (size_t)t * ns, *kb = a.kb + (size_t)t * ns;
-  int32_t *va = a.va + (size_t)t * ns, *vb = a.vb + (size_t)t * ns;
-  int32_t *mv_t = a.mv_t + (size_t)t * ns;
-  long long *mv_g = a.mv_g + (size_t)t * ns;
-  uint8_t *flag = a.flag + (size_t)t * ns;
-  int32_t *list2 = a.qa + (size_t)t * ns;
-  long long *bw = a.bw + (size_t)t * k;
-  long long *conn = a.conn + ((size_t)t * blockDim.x + threadIdx.x) * (size_t)k;
+  const IpGraph &G = a.graphs[a.block_graph[blockIdx.x]];
+  const int t = a.block_try[blockIdx.x];
+  const DGraph g = G.g;
+  const int n = (int)g.n, k = G.k;
+  const int64_t lmax = G.lmax, vbase = G.vbase;
+  const size_t ns = (size_t)G.ns;
+  const size_t so = (size_t)G.scr_off + (size_t)t * ns, ko = (size_t)G.kscr_off + (size_t)t * k;
+  int32_t *part = G.parts + (size_t)t * n;
+  unsigned long long *ka = a.ka + so, *kb = a.kb + so;
+  int32_t *va = a.va + so, *vb = a.vb + so;
+  int32_t *mv_t = a.mv_t + so;
+  long long *mv_g = a.mv_g + so;
+  uint8_t *flag = a.flag + so;
+  int32_t *list2 = a.qa + so;
+  long long *bw = a.bw + ko;
+  long long *conn = a.conn + (size_t)G.conn_off + ((size_t)t * blockDim.x + threadIdx.x) * (size_t)k;
   const int kbits = bits_of((unsigned long long)(k > 1 ? k - 1 : 0));
   for (int b = 0; b < k; b++) conn[b] = 0;
   for (int rr = 0; rr < a.repair_rounds; rr++) {
     for (int b = threadIdx.x; b < k; b += blockDim.x) bw[b] = 0;
     __syncthreads();
     for (int v = threadIdx.x; v < n; v += blockDim.x)
-      atomicAdd(reinterpret_cast<unsigned long long *>(&bw[part[v]]), (unsigned long long)a.g.vweight(v));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&bw[part[v]]), (unsigned long long)g.vweight(v));
     __syncthreads();
     if (threadIdx.x == 0) {
       int over = 0, light = 0;
       for (int b = 0; b < k; b++) {
-        if (bw[b] > a.lmax) over = 1;
+        if (bw[b] > lmax) over = 1;
         if (bw[b] < bw[light]) light = b;
       }
       s_over = over;
@@ -238,24 +258,24 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
       mv_t[v] = -1;
       const int P = part[v];
-      if (bw[P] <= a.lmax) continue;
-      const long long cv = a.g.vweight(v);
-      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
-      for (int64_t j = b; j < e; j++) conn[part[a.g.adj[j]]] += a.g.eweight(j);
+      if (bw[P] <= lmax) continue;
+      const long long cv = g.vweight(v);
+      const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
+      for (int64_t j = b; j < e; j++) conn[part[g.adj[j] - vbase]] += g.eweight(j);
       int best = -1;
       for (int64_t j = b; j < e; j++) {
-        const int B = part[a.g.adj[j]];
-        if (B == P || conn[B] <= 0 || bw[B] + cv > a.lmax) continue;
+        const int B = part[g.adj[j] - vbase];
+        if (B == P || conn[B] <= 0 || bw[B] + cv > lmax) continue;
         if (best < 0 || conn[B] > conn[best] || (conn[B] == conn[best] && B < best)) best = B;
       }
-      if (best < 0 && s_light != P && bw[s_light] + cv <= a.lmax) best = s_light;
+      if (best < 0 && s_light != P && bw[s_light] + cv <= lmax) best = s_light;
       if (best >= 0) {
         mv_t[v] = best;
         mv_g[v] = conn[best] - conn[P];
         atomicMin(&s_gmin, mv_g[v]);
         atomicMax(&s_gmax, mv_g[v]);
       }
-      for (int64_t j = b; j < e; j++) conn[part[a.g.adj[j]]] = 0;
+      for (int64_t j = b; j < e; j++) conn[part[g.adj[j] - vbase]] = 0;
     }
     __syncthreads();
     const int nm = block_compact(n, [&](int v) { return mv_t[v] >= 0; }, va, sm);
@@ -278,10 +298,10 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) flag[v] = 0;
     __syncthreads();
     block_seg_scan(
-        nm, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return a.g.vweight(vs[p]); },
+        nm, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return g.vweight(vs[p]); },
         [&](int p, long long, long long incl) {
           const int v = vs[p];
-          if (bw[mv_t[v]] + incl <= a.lmax) flag[v] = 1;
+          if (bw[mv_t[v]] + incl <= lmax) flag[v] = 1;
         },
         sm);
     __syncthreads();
@@ -297,11 +317,11 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
     ks = in_b ? kb : ka;
     vs = in_b ? vb : va;
     block_seg_scan(
-        na, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return a.g.vweight(vs[p]); },
+        na, [&](int p) { return (int)(ks[p] >> gb); }, [&](int p) { return g.vweight(vs[p]); },
         [&](int p, long long excl, long long) {
           const int v = vs[p];
           const int P = (int)(ks[p] >> gb);
-          flag[v] = (bw[P] - excl > a.lmax) ? 2 : 0;
+          flag[v] = (bw[P] - excl > lmax) ? 2 : 0;
         },
         sm);
     __syncthreads();
@@ -467,45 +487,73 @@ int grid_for_n(int64_t n) {
 
 }  // namespace
 
-int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries, int repair_rounds,
-                      int32_t *parts, cudaStream_t s) {
-  if (g.n >= (1 << 30)) {
-    set_error("initial partitioning supports coarsest graphs below 2^30 vertices");
-    return GP_ERR_UNSUPPORTED;
-  }
+int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s) {
+  if (njobs <= 0) return GP_OK;
   Workspace ws(s);
+  std::vector<IpGraph> hg(njobs);
+  std::vector<int> bgraph, btry;
+  int64_t scr = 0, kscr = 0, cscr = 0;
+  for (int j = 0; j < njobs; j++) {
+    const IpJob &jb = jobs[j];
+    if (jb.g.n >= (1 << 30)) {
+      set_error("initial partitioning supports coarsest graphs below 2^30 vertices");
+      return GP_ERR_UNSUPPORTED;
+    }
+    IpGraph &G = hg[j];
+    G.g = jb.g;
+    G.vbase = jb.vbase;
+    G.k = jb.k;
+    G.level = jb.level;
+    G.lmax = jb.lmax;
+    G.seed = jb.seed;
+    G.parts = jb.parts;
+    G.ns = std::max<int64_t>(std::max<int64_t>(jb.g.n, jb.k), 1);
+    G.scr_off = scr;
+    G.kscr_off = kscr;
+    G.conn_off = cscr;
+    scr += (int64_t)tries * G.ns;
+    kscr += (int64_t)tries * jb.k;
+    cscr += (int64_t)tries * kIpThreads * jb.k;
+    for (int t = 0; t < tries; t++) {
+      bgraph.push_back(j);
+      btry.push_back(t);
+    }
+  }
   IpArgs a;
-  a.g = g;
-  a.k = k;
-  a.lmax = lmax;
-  a.seed = seed;
-  a.level = level;
   a.repair_rounds = repair_rounds;
-  a.ns = std::max<int64_t>(std::max<int64_t>(g.n, k), 1);
-  const size_t tn = (size_t)tries * (size_t)a.ns;
-  const size_t tk = (size_t)tries * (size_t)k;
-  a.part = parts;
-  GP_TRY(ws.get(&a.gk, tn));
-  GP_TRY(ws.get(&a.dist, tn));
-  GP_TRY(ws.get(&a.qa, tn));
-  GP_TRY(ws.get(&a.qb, tn));
-  GP_TRY(ws.get(&a.ka, tn));
-  GP_TRY(ws.get(&a.kb, tn));
-  GP_TRY(ws.get(&a.va, tn));
-  GP_TRY(ws.get(&a.vb, tn));
-  GP_TRY(ws.get(&a.mv_t, tn));
-  GP_TRY(ws.get(&a.mv_g, tn));
-  GP_TRY(ws.get(&a.flag, tn));
-  GP_TRY(ws.get(&a.gws, tk));
-  GP_TRY(ws.get(&a.gminh, tk));
-  GP_TRY(ws.get(&a.gstart, tk));
-  GP_TRY(ws.get(&a.gfar, tk));
-  GP_TRY(ws.get(&a.bw, tk));
-  GP_TRY(ws.get(&a.conn, tk * kIpThreads));
+  GP_TRY(ws.get(&a.gk, (size_t)scr));
+  GP_TRY(ws.get(&a.dist, (size_t)scr));
+  GP_TRY(ws.get(&a.qa, (size_t)scr));
+  GP_TRY(ws.get(&a.qb, (size_t)scr));
+  GP_TRY(ws.get(&a.ka, (size_t)scr));
+  GP_TRY(ws.get(&a.kb, (size_t)scr));
+  GP_TRY(ws.get(&a.va, (size_t)scr));
+  GP_TRY(ws.get(&a.vb, (size_t)scr));
+  GP_TRY(ws.get(&a.mv_t, (size_t)scr));
+  GP_TRY(ws.get(&a.mv_g, (size_t)scr));
+  GP_TRY(ws.get(&a.flag, (size_t)scr));
+  GP_TRY(ws.get(&a.gws, (size_t)kscr));
+  GP_TRY(ws.get(&a.gminh, (size_t)kscr));
+  GP_TRY(ws.get(&a.gstart, (size_t)kscr));
+  GP_TRY(ws.get(&a.gfar, (size_t)kscr));
+  GP_TRY(ws.get(&a.bw, (size_t)kscr));
+  GP_TRY(ws.get(&a.conn, (size_t)cscr));
   GP_TRY(ws.zeros(&a.err, 1));
-  (::gp::count_launch(), k_bisect<<<tries, kIpThreads, 0, s>>>(a));
+  IpGraph *graphs_dev;
+  int *bg_dev, *bt_dev;
+  GP_TRY(ws.get(&graphs_dev, hg.size()));
+  GP_TRY(ws.get(&bg_dev, bgraph.size()));
+  GP_TRY(ws.get(&bt_dev, btry.size()));
+  GP_CUDA(cudaMemcpyAsync(graphs_dev, hg.data(), sizeof(IpGraph) * hg.size(), cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(bg_dev, bgraph.data(), sizeof(int) * bgraph.size(), cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(bt_dev, btry.data(), sizeof(int) * btry.size(), cudaMemcpyHostToDevice, s));
+  a.graphs = graphs_dev;
+  a.block_graph = bg_dev;
+  a.block_try = bt_dev;
+  const int grid = (int)bgraph.size();
+  (::gp::count_launch(), k_bisect<<<grid, kIpThreads, 0, s>>>(a));
   GP_LAUNCH_CHECK();
-  (::gp::count_launch(), k_repair<<<tries, kIpThreads, 0, s>>>(a));
+  (::gp::count_launch(), k_repair<<<grid, kIpThreads, 0, s>>>(a));
   GP_LAUNCH_CHECK();
   int err = 0;
   GP_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -515,6 +563,19 @@ int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int l
     return err;
   }
   return GP_OK;
+}
+
+int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries, int repair_rounds,
+                      int32_t *parts, cudaStream_t s) {
+  IpJob j;
+  j.g = g;
+  j.vbase = 0;
+  j.k = k;
+  j.lmax = lmax;
+  j.seed = seed;
+  j.level = level;
+  j.parts = parts;
+  return initial_partition_multi(&j, 1, tries, repair_rounds, s);
 }
 
 int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev, cudaStream_t s) {

@@ -11,6 +11,18 @@ namespace gp {
 int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries,
                       int repair_rounds, int32_t *parts, cudaStream_t s);
 
+// The same for several graphs of a disjoint union in one launch (one CTA per graph and try).
+struct IpJob {
+  DGraph g;            // local view of the graph
+  int64_t vbase = 0;   // adjacency values minus vbase are local ids
+  int k = 1;
+  int64_t lmax = 0;
+  uint64_t seed = 0;
+  int level = 0;
+  int32_t *parts = nullptr;  // tries * g.n
+};
+int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s);
+
 // cut (each undirected edge once) of part on g; also block weights into bw[k] when bw != NULL.
 int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev,
              cudaStream_t s);

@@ -65,8 +65,12 @@ struct LpCounters {
   int pad;
 };
 
+// One LP run. Vertex ids of bins, slots and hashes are local (0..g.n-1); adjacency entries, labels
+// and the label/activity arrays use global ids (local + vbase, labels from lbase on), so several graphs
+// stored as one disjoint union can run as independent problems of one launch.
 struct LpProblem {
-  DGraph g;
+  DGraph g;  // g.n local vertices; offsets/vertex weights indexed by local id, adjacency by global entry
+  int64_t vbase, lbase;
   int64_t nl, U;
   uint64_t smix;  // mix64(seed)
   int rounds;
@@ -187,7 +191,7 @@ __device__ __forceinline__ Best make_cand(const LpProblem &P, int v, int L, int 
   b.L = L;
   b.conn = conn;
   b.qs = qs;
-  b.h = mix64(mix64(P.smix ^ (uint64_t)(uint32_t)v) ^ (uint64_t)(uint32_t)L);
+  b.h = mix64(mix64(P.smix ^ (uint64_t)(uint32_t)v) ^ (uint64_t)(L - P.lbase));
   return b;
 }
 
@@ -248,7 +252,7 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
 // chunk of vertices, counts them per bin, reserves space with one atomic per bin and then fills it.
 __device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const uint8_t *act, int r, int s,
                                           uint64_t rmix, int64_t *deg) {
-  if (!((r == 0 || act[v]) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == s)) return -1;
+  if (!((r == 0 || act[P.vbase + v]) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == s)) return -1;
   const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
   *deg = d;
   return d == 0 ? kBinZero : bin_of(d, P.deg_warp, P.deg_cta);
@@ -275,7 +279,7 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, int r, int s,
     int b = -1;
     int64_t d = 0;
     if (v < hi) {
-      if (s == 0) act_next[v] = 0;  // the marks of round r go there
+      if (s == 0) act_next[P.vbase + v] = 0;  // the marks of round r go there
       b = active_bin(P, v, act, r, s, rmix, &d);
     }
     const unsigned peers = __match_any_sync(kFull, b);
@@ -345,7 +349,7 @@ __device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int l
       if (valid[u]) {
         beg[u] = P.g.row_begin(v[u]);
         d[u] = P.g.row_begin(v[u] + 1) - beg[u];
-        L0[u] = P.labels[v[u]];
+        L0[u] = P.labels[P.vbase + v[u]];
       }
     }
     int nbr[U];
@@ -418,7 +422,7 @@ __device__ void choose_warp(const LpProblem &P, SubCounters &C, int lb, int nb, 
     int cap = 64;
     while (cap < 2 * d) cap <<= 1;
     const unsigned mask = (unsigned)cap - 1;
-    const int L0 = P.labels[v];
+    const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
     for (int64_t e = beg + lane; e < end; e += 32) {
       const int L = P.labels[__ldg(P.g.adj + e)];
@@ -484,7 +488,7 @@ __device__ void choose_cta(const LpProblem &P, SubCounters &C, int lb, int nb, u
     int cap = 64;
     while (cap < 2 * d) cap <<= 1;
     const unsigned mask = (unsigned)cap - 1;
-    const int L0 = P.labels[v];
+    const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
     for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
       const int L = P.labels[__ldg(P.g.adj + e)];
@@ -568,7 +572,7 @@ __device__ void hub_accum(const LpProblem &P, SubCounters &C, int lb, int nb, Sm
     int64_t cap = 64;
     while (cap < 2 * (re - rb)) cap <<= 1;
     const uint64_t mask = (uint64_t)cap - 1;
-    const int L0 = P.labels[v];
+    const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
     for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
       const int L = P.labels[__ldg(P.g.adj + e)];
@@ -602,7 +606,7 @@ __device__ void hub_choose(const LpProblem &P, SubCounters &C, int lb, int nb, S
     int64_t cap = 64;
     while (cap < 2 * d) cap <<= 1;
     const int64_t tb = P.hub_base[P.hub_of[v]];
-    const int L0 = P.labels[v];
+    const int L0 = P.labels[P.vbase + v];
     const long long c0 = P.hub_c0[i];
     const long long cv = P.g.vweight(v);
     Best b = no_best();
@@ -789,7 +793,7 @@ __device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, 
         k = (unsigned long long)(unsigned)P.mv_v[idx];
         if (LQ && bq) k |= (maxq - (unsigned long long)P.mv_q[idx]) << sq;
         if (bg) k |= (maxg - (unsigned long long)P.mv_gain[idx]) << sg;
-        if (bt) k |= (unsigned long long)(unsigned)P.mv_t[idx] << st;
+        if (bt) k |= (unsigned long long)(P.mv_t[idx] - P.lbase) << st;
       }
       key[i] = k;
     }
@@ -813,7 +817,7 @@ __device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, 
         P,
         [&](unsigned p, int &T, unsigned &idx) {
           const unsigned long long k = key[p];
-          T = bt ? (int)(k >> st) : 0;
+          T = (int)((bt ? (long long)(k >> st) : 0) + P.lbase);
           idx = (unsigned)P.mv_of_v[(int)(k & vmask)];
         },
         0, cnt, 0, -1, sm);
@@ -857,7 +861,7 @@ __device__ __forceinline__ unsigned long long field_key(const LpProblem &P, unsi
     case 0: return (unsigned long long)(unsigned)P.mv_v[idx];
     case 1: return maxq - (unsigned long long)P.mv_q[idx];
     case 2: return maxg - (unsigned long long)P.mv_gain[idx];
-    default: return (unsigned long long)(unsigned)P.mv_t[idx];
+    default: return (unsigned long long)(P.mv_t[idx] - P.lbase);
   }
 }
 
@@ -1016,9 +1020,9 @@ __device__ void phase_apply(const LpProblem &P, SubCounters &C, int r, int lb, i
     int L0 = -1;
     long long c = 0;
     if (adm) {
-      L0 = P.labels[v];
+      L0 = P.labels[P.vbase + v];
       c = P.g.vweight(v);
-      P.labels[v] = T;
+      P.labels[P.vbase + v] = T;
     }
     warp_add_by_key(P.lw, adm, T, c);
     warp_add_by_key(P.lw, adm, L0, -c);
@@ -1308,6 +1312,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     LpProblem &P = hp[j];
     std::memset(&P, 0, sizeof(P));
     P.g = jb.g;
+    P.vbase = jb.vbase;
+    P.lbase = jb.lbase;
     P.nl = jb.nl;
     P.U = jb.U;
     P.smix = mix64(jb.seed);
@@ -1334,10 +1340,13 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.mv_adm, n));
     GP_TRY(ws.get(&P.mv_of_v, n));
     GP_TRY(ws.zeros(&P.demand, (size_t)std::max<int64_t>(jb.nl, 1)));
+    P.demand -= jb.lbase;  // indexed by global label
     GP_TRY(ws.get(&P.ct, n));
     GP_TRY(ws.get(&P.ct2, n));
     GP_TRY(ws.get(&P.act[0], n));
     GP_TRY(ws.get(&P.act[1], n));
+    P.act[0] -= jb.vbase;  // indexed by global vertex id
+    P.act[1] -= jb.vbase;
     GP_TRY(ws.get(&P.hist, (size_t)want[j] * 256 + 16));
     GP_TRY(ws.get(&P.hoff, (size_t)want[j] * 256 + 256 + 16));
     GP_TRY(ws.zeros(&P.ctr, 1));

@@ -11,9 +11,13 @@ struct LpConfig {
                         // d > deg_cta: several CTAs per vertex, global-memory hash
 };
 
-// One LP run for run_lp_multi.
+// One LP run for run_lp_multi. With vbase/lbase != 0 the job is one graph of a disjoint union:
+// g is its view (g.n local vertices, offsets and vertex weights shifted to its first vertex, adjacency
+// and edge weights of the union), labels/lw are the union's arrays (labels hold global label ids
+// lbase .. lbase + nl - 1) and hashes use local ids, so the result equals a run on the graph alone.
 struct LpJob {
   DGraph g;
+  int64_t vbase = 0, lbase = 0;
   const int32_t *q = nullptr;
   int32_t *labels = nullptr;
   int64_t *lw = nullptr;

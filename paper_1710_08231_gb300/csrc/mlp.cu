@@ -438,15 +438,4 @@ int gp_mlp_grad(const float *feat, const float *y, int64_t m, const gp_mlp *mlp,
   return GP_OK;
 }
 
-int gp_partition_batch(const gp_batch_item *items, int32_t count, const gp_params *params, gp_result *res,
-                       gp_stream stream) {
-  if (count < 0 || (count > 0 && (!items || !res))) return GP_ERR_INVALID_ARG;
-  for (int32_t i = 0; i < count; i++) {
-    const int st = gp_partition(&items[i].g, items[i].k, items[i].eps, items[i].seed, params, items[i].part_out,
-                                &res[i], stream);
-    if (st != GP_OK) return st;
-  }
-  return GP_OK;
-}
-
 }  // extern "C"

@@ -122,6 +122,8 @@ struct Hierarchy {
 
 }  // namespace
 
+LpConfig schedule_for_batch(const gp_params *p) { return schedule_for(p); }
+
 // ------------------------------------------------------------------------------------------ driver
 int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, const gp_params *pp,
                      int32_t *part_out, gp_result *res, cudaStream_t s) {
@@ -563,6 +565,66 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta) {
 }
 
 int64_t gp_launch_count(int reset) { return gp::launch_count(reset); }
+
+int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
+                         gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if (!deg_warp_out || !deg_cta_out) {
+    set_error("gp_autotune_schedule: outputs are required");
+    return GP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DGraph g = make_dgraph(gd);
+  static const int cand[][2] = {{32, 256}, {64, 256}, {64, 512}, {128, 512}, {128, 1024}, {32, 1024}};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  Workspace ws(s);
+  int32_t *labels;
+  int64_t *lw;
+  GP_TRY(ws.get(&labels, (size_t)std::max<int64_t>(g.n, 1)));
+  GP_TRY(ws.get(&lw, (size_t)std::max<int64_t>(g.n, 1)));
+  int64_t maxc = 0, W = 0;
+  GP_TRY(vertex_weight_stats(g, &maxc, &W, s));
+  const int64_t U = std::max<int64_t>(maxc, std::max<int64_t>(W / 32, 1));
+  cudaEvent_t a, b;
+  GP_CUDA(cudaEventCreate(&a));
+  GP_CUDA(cudaEventCreate(&b));
+  double best_ms = -1;
+  int best = 0;
+  for (int rep = 0; rep < 2; rep++) {  // the first sweep warms up
+    for (int c = 0; c < nc; c++) {
+      gp_params pr;
+      gp_default_params(&pr);
+      pr.deg_warp = cand[c][0];
+      pr.deg_cta = cand[c][1];
+      const LpConfig cfg = lp_config_from(&pr);
+      if (g.n > 0) {
+        (::gp::count_launch(), k_iota<<<grid_n(g.n), 256, 0, s>>>(labels, g.n));
+        (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
+      }
+      GP_CUDA(cudaEventRecord(a, s));
+      const int st = run_lp(g, nullptr, labels, lw, g.n, U, 3, 0x5eedULL, nullptr, s, cfg);
+      GP_CUDA(cudaEventRecord(b, s));
+      if (st != GP_OK) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return st;
+      }
+      GP_CUDA(cudaEventSynchronize(b));
+      float ms = 0;
+      GP_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (rep == 1 && (best_ms < 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *deg_warp_out = cand[best][0];
+  *deg_cta_out = cand[best][1];
+  if (ms_out) *ms_out = best_ms;
+  return GP_OK;
+}
 
 int gp_profile_enable(int on) { return gp::prof_enable(on); }
 int gp_profile_read(gp_profile_entry *out, int max_entries, int reset) {
