@@ -8,7 +8,13 @@ scanned by all LP sub-rounds of the partition, counted by the library) / device 
 Default workload: random geometric graph, 2^20 vertices, average degree 12, unit weights, k=16,
 eps=0.03, seed 1 (a stand-in for the paper's rgg instances).
 
+The line also carries two comparisons at the same seed: the learned edge scorer (trained untimed on
+same-family graphs with other seeds) against plain LP on the same graph, and the batch of 512 uneven
+graphs partitioned in one call against a per-graph loop (results identical by construction, checked).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                       [--mode plain|learned] [--no-compare]
+--workload batch512 makes the batched call itself the timed step (value: LP GTEPS of the batch).
 For N > 1 the script runs under torch.distributed.run; every rank partitions its own replica
 (replicas only: the single-graph path does not shard), so scaling is weak.
 """
@@ -33,9 +39,109 @@ WORKLOADS = {
     "grid256": dict(kind="grid", a=256, b=256, k=2, desc="2D 4-neighbour grid 256x256, unit weights, k=2, eps=0.03, seed 1"),
     "rmat24": dict(kind="rmat", scale=24, ef=16, k=16, weighted=False, desc="R-MAT scale 24, edge factor 16, (0.57,0.19,0.19), symmetrised, unit weights, k=16, eps=0.03, seed 1"),
     "rmat26w": dict(kind="rmat", scale=26, ef=16, k=64, weighted=True, desc="R-MAT scale 26, edge factor 16, edge weights in [1,8], k=64, eps=0.03, seed 1"),
+    "batch512": dict(kind="batch", count=512, desc="batch of 512 uneven graphs (grids and RGGs, 1k-200k vertices, log-uniform), unit weights, k in {2,4,8}, eps=0.03, seed 1"),
 }
 EPS, SEED = 0.03, 1
 METRIC = "LP GTEPS + ms/partition at equal cut (plain vs learned/batched), % HBM peak"
+
+
+def make_batch(count: int = 512):
+    import graphgen as gg
+    specs = gg.batch_specs(count, seed=SEED)
+    return specs, [gg.batch_graph(sp) for sp in specs]
+
+
+def family_graphs(name: str):
+    """Training graphs for the learned scorer: the workload's family at a smaller size, other seeds."""
+    import graphgen as gg
+    w = WORKLOADS[name]
+    if w["kind"] == "rgg":
+        return [gg.rgg(1 << 16, w["deg"], s) for s in (101, 102)]
+    if w["kind"] == "grid":
+        return [gg.grid(128, 128), gg.grid(96, 160)]
+    return [gg.rmat(16, w["ef"], seed=s, weighted=w["weighted"]) for s in (101, 102)]
+
+
+def train_scorer(gp, name: str, k: int):
+    """Trains the 8-32-1 scorer on which edges plain partitions of same-family graphs leave uncut."""
+    import torch
+    feats, ys = [], []
+    for g in family_graphs(name):
+        dg = gp.DeviceGraph.from_host(g)
+        part, _ = gp.partition(dg, k, EPS, SEED)
+        p = part.cpu().numpy()
+        src = np.repeat(np.arange(g.n), np.diff(g.off))
+        feats.append(gp.edge_features(dg, 0))
+        ys.append(torch.from_numpy((p[src] == p[g.adj]).astype(np.float32)).cuda())
+    rng = np.random.default_rng(SEED)
+    mlp = gp.mlp_pack(rng.normal(0, 0.2, (32, 8)), rng.normal(0, 0.1, 32), rng.normal(0, 0.2, 32),
+                      float(rng.normal(0, 0.1)))
+    losses = gp.mlp_train(torch.cat(feats), torch.cat(ys), mlp, 300, 1e-2)
+    return mlp, [float(losses[0]), float(losses[-1])]
+
+
+def time_steps(fn, steps, flush):
+    """Device time (ms) of `steps` calls of fn, events on the current stream, L2 flushed between."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = None
+    for i in range(steps):
+        flush.fill_(i)
+        ev[i][0].record(stream)
+        out = fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev), out
+
+
+def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res):
+    mlp, loss = train_scorer(gp, name, k)
+    params = gp.default_params(mode=gp.MODE_LEARNED)
+    params.mlp = mlp.data_ptr()
+    for _ in range(2):
+        gp.partition(dg, k, EPS, SEED, params)
+    ms, (_, res) = time_steps(lambda: gp.partition(dg, k, EPS, SEED, params), steps, flush)
+    return {"ms_per_partition": ms / steps, "gteps": res.lp_edges * steps / (ms * 1e-3) / 1e9, "cut": res.cut,
+            "imbalanced": res.imbalanced, "plain_cut": plain_res.cut, "plain_ms_per_partition": plain_ms,
+            "cut_ratio_learned_over_plain": res.cut / max(plain_res.cut, 1),
+            "time_ratio_learned_over_plain": (ms / steps) / plain_ms, "levels": res.levels,
+            "training": {"graphs": "2 same-family graphs, seeds 101-102", "steps": 300, "lr": 1e-2,
+                         "bce_first_last": loss},
+            "note": "learned is reported as measured; worse cuts are not hidden"}
+
+
+def batch_items(gp, graphs):
+    return [gp.DeviceGraph.from_host(g) for g in graphs]
+
+
+def compare_batched(gp, steps, flush):
+    specs, graphs = make_batch(512)
+    dgs = batch_items(gp, graphs)
+    ks = [sp.k for sp in specs]
+    seeds = [sp.seed for sp in specs]
+    big = max(range(len(graphs)), key=lambda i: graphs[i].n)
+    dw, dc, _ = gp.autotune_schedule(dgs[big])
+    params = gp.default_params(deg_warp=dw, deg_cta=dc)
+    gp.partition_batch(dgs, ks, EPS, seeds, params)
+    ms_b, (_, rb) = time_steps(lambda: gp.partition_batch(dgs, ks, EPS, seeds, params), steps, flush)
+    loop_res = []
+
+    def loop():
+        loop_res.clear()
+        for dg, k, sd in zip(dgs, ks, seeds):
+            loop_res.append(gp.partition(dg, k, EPS, sd, params)[1])
+        return loop_res
+
+    loop()
+    ms_l, _ = time_steps(loop, 1, flush)
+    edges = sum(r.lp_edges for r in rb)
+    return {"graphs": len(graphs), "n_total": int(sum(g.n for g in graphs)),
+            "m_dir_total": int(sum(g.m_dir for g in graphs)), "schedule": {"deg_warp": dw, "deg_cta": dc},
+            "batched_ms": ms_b / steps, "per_graph_loop_ms": ms_l, "speedup": ms_l / (ms_b / steps),
+            "batched_gteps": edges * steps / (ms_b * 1e-3) / 1e9,
+            "cuts_equal_to_loop": all(a.cut == b.cut for a, b in zip(rb, loop_res)),
+            "total_cut": int(sum(r.cut for r in rb)), "imbalanced": int(sum(r.imbalanced for r in rb))}
 
 
 def make_graph(name: str):
@@ -55,6 +161,33 @@ def peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+TRAFFIC_SUMMARY = {"rgg20": "profiles/k_lp_rgg20_dram_per_launch.md"}
+LP_SOURCES = ["paper_1710_08231_gb300/csrc/lp.cu", "paper_1710_08231_gb300/csrc/lp.cuh",
+              "paper_1710_08231_gb300/csrc/gp_internal.cuh"]
+
+
+def lp_traffic(workload: str):
+    """DRAM bytes per k_lp launch from the committed ncu summary of this workload, or None when there
+    is none or the LP sources changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, TRAFFIC_SUMMARY.get(workload, ""))
+    if workload not in TRAFFIC_SUMMARY or not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "source_sha256"):
+                k, v = line.split(":", 1)
+                fields[k] = v.strip()
+    h = hashlib.sha256()
+    for src in LP_SOURCES:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if fields.get("source_sha256") != h.hexdigest() or "traffic_bytes_per_launch" not in fields:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
 
 
 class ClockSampler:
@@ -158,10 +291,43 @@ def run_oracle_sample(g, k: int):
     return res.lp_edges, dt, res
 
 
+def oracle_batch_sample(specs, graphs, budget_s: float = 10.0):
+    """Oracle partitions of the batch's graphs in order until budget_s of CPU time: (edges, s, count)."""
+    import oracle
+    e, t, c = 0, 0.0, 0
+    for sp, g in zip(specs, graphs):
+        t0 = time.perf_counter()
+        _, res = oracle.partition(g, sp.k, EPS, sp.seed)
+        t += time.perf_counter() - t0
+        e += res.lp_edges
+        c += 1
+        if t >= budget_s:
+            break
+    return e, t, c
+
+
 def bench_reference(args, g, w):
     """Reference arm: the CPU oracle as it stands, single-threaded, one full partition per step."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
+        return
+    if w["kind"] == "batch":
+        specs, graphs = g
+        for _ in range(args.warmup):
+            oracle_batch_sample(specs, graphs, 2.0)
+        tot_e, tot_t, cnt = 0, 0.0, 0
+        for _ in range(args.steps):
+            e, dt, c = oracle_batch_sample(specs, graphs, 10.0)
+            tot_e, tot_t, cnt = tot_e + e, tot_t + dt, c
+        value = tot_e / tot_t / 1e9
+        sample = f"the batch's first {cnt} graphs in order (about 10 s of oracle time per step), single-threaded"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic", "config": {"workload": w["desc"]},
+                "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     for _ in range(args.warmup):
         run_oracle_sample(g, w["k"])
@@ -191,12 +357,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--once", action="store_true", help="one untimed partition (for profiler launch lists)")
+    ap.add_argument("--mode", default="plain", choices=["plain", "learned"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the learned and batched comparisons")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     w = WORKLOADS[args.workload]
+    is_batch = w["kind"] == "batch"
     if args.impl == "reference":
-        g = make_graph(args.workload)
-        bench_reference(args, g, w)
+        bench_reference(args, make_batch(w["count"]) if is_batch else make_graph(args.workload), w)
         return
 
     import torch
@@ -204,16 +372,46 @@ def main():
 
     rank, world, local, dist = dist_setup(args.gpus)
     gp.build()
-    g = make_graph(args.workload)
-    k = w["k"]
-    dg = gp.DeviceGraph.from_host(g)
-    part = torch.empty(g.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
+    if is_batch:
+        specs, graphs = make_batch(w["count"])
+        dgs = batch_items(gp, graphs)
+        ks = [sp.k for sp in specs]
+        seeds = [sp.seed + rank for sp in specs]
+        big = max(range(len(graphs)), key=lambda i: graphs[i].n)
+        dw, dc, _ = gp.autotune_schedule(dgs[big])
+        params = gp.default_params(deg_warp=dw, deg_cta=dc)
+        g = None
+        k = None
 
-    def step():
-        _, res = gp.partition(dg, k, EPS, SEED + rank, out=part)
-        return res
+        class _Sum:  # the batch's results summed into the fields the line reports
+            pass
+
+        def step():
+            _, rs = gp.partition_batch(dgs, ks, EPS, seeds, params)
+            r = _Sum()
+            r.lp_edges = sum(x.lp_edges for x in rs)
+            r.cut = sum(x.cut for x in rs)
+            r.max_block_weight = max(x.max_block_weight for x in rs)
+            r.lmax = None
+            r.imbalanced = sum(x.imbalanced for x in rs)
+            r.levels = max(x.levels for x in rs)
+            return r
+    else:
+        g = make_graph(args.workload)
+        k = w["k"]
+        dg = gp.DeviceGraph.from_host(g)
+        part = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        params = None
+        if args.mode == "learned":
+            mlp, _ = train_scorer(gp, args.workload, k)
+            params = gp.default_params(mode=gp.MODE_LEARNED)
+            params.mlp = mlp.data_ptr()
+
+        def step():
+            _, res = gp.partition(dg, k, EPS, SEED + rank, params, out=part)
+            return res
 
     if args.once:
         res = step()
@@ -261,7 +459,10 @@ def main():
     if top:
         achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": top["name"], "launches": top["launches"],
+                    "traffic": lp_traffic(args.workload) if top["name"] == "lp_persistent" else None,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per k_lp launch, "
+                                      + TRAFFIC_SUMMARY.get(args.workload, "none"),
+                    "kernel": top["name"], "launches": top["launches"],
                     "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
                     "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                     "kernels_ms_per_step": {e["name"]: e["ms"] / args.steps for e in prof if e["launches"] > 0 and not e["name"].startswith("lp_phase")},
@@ -270,7 +471,32 @@ def main():
 
     # ---- pass C: end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and is_batch:
+        # host CSR in pinned memory; every step copies all graphs in, partitions, copies the parts out
+        hosts = [(torch.from_numpy(np.ascontiguousarray(x.off)).pin_memory(),
+                  torch.from_numpy(np.ascontiguousarray(x.adj)).pin_memory()) for x in graphs]
+        outs = [torch.empty(x.n, dtype=torch.int32).pin_memory() for x in graphs]
+        h2d = sum(a.numel() * a.element_size() + b.numel() * b.element_size() for a, b in hosts)
+        d2h = sum(o.numel() * 4 for o in outs)
+
+        def e2e_step():
+            devs = [gp.DeviceGraph(x.n, a.to("cuda", non_blocking=True), b.to("cuda", non_blocking=True), None, None)
+                    for x, (a, b) in zip(graphs, hosts)]
+            parts, rs = gp.partition_batch(devs, ks, EPS, seeds, params)
+            for p_, o in zip(parts, outs):
+                o.copy_(p_, non_blocking=True)
+            torch.cuda.synchronize()
+            return rs
+
+        e2e_step()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            e2e_step()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": edges_all / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / args.steps}
+    elif not args.no_e2e and params is None:
         hg = gp.HostGraph(g, pin=True)
         for _ in range(2):
             gp.partition_host(hg, k, EPS, SEED + rank)
@@ -283,18 +509,32 @@ def main():
         e2e = {"value": edges_all / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hg.h2d_bytes,
                "d2h_bytes_per_step": hg.d2h_bytes, "ms_per_step": 1e3 * e2e_s / args.steps}
 
+    compare = None
+    if rank == 0 and world == 1 and not args.no_compare and not is_batch and args.mode == "plain":
+        compare = {"learned": compare_learned(gp, args.workload, g, dg, k, args.steps, flush,
+                                              ms_total / args.steps, res),
+                   "batched": compare_batched(gp, 3, flush)}
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and is_batch:
+        e, dt, cnt = oracle_batch_sample(specs, graphs, 10.0)
+        cpu = {"value": e / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"the batch's first {cnt} graphs in order, single-threaded ({dt:.1f} s)"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline and args.mode == "plain":
         e, dt, ores = run_oracle_sample(g, k)
         cpu = {"value": e / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": f"one full single-threaded oracle partition of the same graph ({dt:.1f} s, cut {ores.cut}, "
                          f"same cut as the GPU: {ores.cut == res.cut})"}
 
     if rank == 0:
+        shape = ({"graphs": len(graphs), "n_total": int(sum(x.n for x in graphs)),
+                  "m_dir_total": int(sum(x.m_dir for x in graphs)), "k": "2, 4 or 8 per graph",
+                  "schedule": {"deg_warp": dw, "deg_cta": dc, "picked_by": "gp_autotune_schedule on the largest graph"}}
+                 if is_batch else {"n": g.n, "m_dir": g.m_dir, "k": k, "mode": args.mode})
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": w["desc"], "n": g.n, "m_dir": g.m_dir, "k": k,
+                "config": {"workload": w["desc"], **shape,
                            "lp_edges_per_partition": lp_edges_step, "cut": res.cut,
                            "max_block_weight": res.max_block_weight, "lmax": res.lmax,
                            "imbalanced": res.imbalanced, "levels": res.levels,
@@ -303,7 +543,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "wall_ms_per_step": 1e3 * wall / args.steps},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), "compare": compare}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
