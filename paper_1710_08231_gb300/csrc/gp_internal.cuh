@@ -51,16 +51,36 @@ class Workspace {
   ~Workspace() { release(); }
   Workspace(const Workspace &) = delete;
   Workspace &operator=(const Workspace &) = delete;
+  // Buffers of up to kChunk bytes are carved out of kChunk-byte chunks (one allocator call per
+  // chunk); larger ones get an allocation of their own. Every buffer starts on a 256-byte boundary.
+  // With a scratch arena active, every buffer is allocated exactly (no chunk slack).
   template <class T>
   int get(T **out, size_t count) {
     size_t bytes = (count ? count : 1) * sizeof(T);
     bytes = (bytes + 255) & ~size_t(255);
-    void *p = dev_alloc(bytes, s_);
-    if (!p) {
-      set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
-      return GP_ERR_OOM;
+    void *p = nullptr;
+    if (bytes <= kChunk && !arena_active()) {
+      if (chunk_left_ < bytes) {
+        void *c = dev_alloc(kChunk, s_);
+        if (!c) {
+          set_error("device allocation of " + std::to_string(kChunk) + " bytes failed");
+          return GP_ERR_OOM;
+        }
+        items_.push_back({c, kChunk});
+        chunk_ptr_ = static_cast<char *>(c);
+        chunk_left_ = kChunk;
+      }
+      p = chunk_ptr_;
+      chunk_ptr_ += bytes;
+      chunk_left_ -= bytes;
+    } else {
+      p = dev_alloc(bytes, s_);
+      if (!p) {
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed");
+        return GP_ERR_OOM;
+      }
+      items_.push_back({p, bytes});
     }
-    items_.push_back({p, bytes});
     *out = static_cast<T *>(p);
     return GP_OK;
   }
@@ -73,16 +93,21 @@ class Workspace {
   void release() {
     for (auto it = items_.rbegin(); it != items_.rend(); ++it) dev_free(it->p, it->bytes, s_);
     items_.clear();
+    chunk_ptr_ = nullptr;
+    chunk_left_ = 0;
   }
   cudaStream_t stream() const { return s_; }
 
  private:
+  static constexpr size_t kChunk = size_t(2) << 20;
   struct Item {
     void *p;
     size_t bytes;
   };
   cudaStream_t s_;
   std::vector<Item> items_;
+  char *chunk_ptr_ = nullptr;
+  size_t chunk_left_ = 0;
 };
 
 // ------------------------------------------------------------------------------------------ hash
@@ -194,16 +219,14 @@ __device__ __forceinline__ T block_excl_scan64(T x, T *tmp, T *total) {
   return r;
 }
 
-// Bounded two-level barrier over `nblocks` blocks of a cooperatively launched kernel (all blocks
-// co-resident). Blocks arrive on one counter per group of kBarrierGroup blocks; the last block of a
-// group arrives on the root counter; the last root arrival advances `gen`, on which everyone waits.
-// Counters are kBarrierStride words apart (separate cache lines). `err` receives GP_ERR_TIMEOUT when
-// a wait gives up (about 2^24 polls), in which case every waiting block returns false.
-constexpr unsigned kBarrierGroup = 16;
+// Bounded barrier over `nblocks` blocks of a cooperatively launched kernel (all blocks co-resident).
+// Thread 0 of each block arrives on `count` with an acquire-release atomic (its release covers the
+// writes of the whole block, ordered before it by the preceding __syncthreads); the last arrival
+// resets the counter and advances `gen` with a release; the others poll `gen` with acquire loads.
+// A problem of one block needs only __syncthreads. `err` receives GP_ERR_TIMEOUT when a wait gives
+// up (about 2^24 polls), in which case every waiting block returns false.
 constexpr unsigned kBarrierStride = 32;
-inline unsigned barrier_words(unsigned nblocks) {
-  return ((nblocks + kBarrierGroup - 1) / kBarrierGroup + 1) * kBarrierStride;
-}
+inline unsigned barrier_words(unsigned) { return kBarrierStride; }
 
 struct GridBarrier {
   unsigned int *count;  // barrier_words(nblocks) words, zero-initialised
@@ -213,40 +236,37 @@ struct GridBarrier {
   unsigned int rank;    // this block's index among the nblocks
 };
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
   __shared__ int s_ok;
+  if (b.nblocks <= 1) {
+    __syncthreads();
+    return true;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     s_ok = 1;
-    volatile unsigned int *vgen = b.gen;
-    const unsigned int my = *vgen;
-    __threadfence();
-    const unsigned ngroups = (b.nblocks + kBarrierGroup - 1) / kBarrierGroup;
-    const unsigned g = b.rank / kBarrierGroup;
-    const unsigned gsize = min(kBarrierGroup, b.nblocks - g * kBarrierGroup);
-    bool last = false;
-    if (atomicAdd(&b.count[g * kBarrierStride], 1u) == gsize - 1) {
-      b.count[g * kBarrierStride] = 0;
-      if (atomicAdd(&b.count[ngroups * kBarrierStride], 1u) == ngroups - 1) {
-        b.count[ngroups * kBarrierStride] = 0;
-        last = true;
-      }
-    }
-    if (last) {
-      __threadfence();
-      atomicAdd(b.gen, 1u);
+    const unsigned my = ld_acquire_u32(b.gen);
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
+    if (old == b.nblocks - 1) {
+      *b.count = 0;
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" : : "l"(b.gen) : "memory");
     } else {
       long long polls = 0;
-      while (*vgen == my) {
+      while (ld_acquire_u32(b.gen) == my) {
         if (++polls > (1ll << 24) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
           atomicExch(b.err, GP_ERR_TIMEOUT);
           s_ok = 0;
           break;
         }
-        if (polls > 256) __nanosleep(32);
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return s_ok != 0;

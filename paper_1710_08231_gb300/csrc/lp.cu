@@ -54,11 +54,11 @@ struct SubCounters {
 };
 
 struct LpCounters {
-  SubCounters sc[2];                  // by sub-round parity
+  SubCounters sc[3];                  // by sub-round index mod 3 (current, next, previous)
   unsigned long long moves_round[2];  // by round parity
   unsigned long long moves, rounds, movers;
   unsigned long long bin_visits[8], bin_edges[8];
-  unsigned long long phase_ns[8];  // classify, choose, hubs, admit, contest, apply (block 0's view)
+  unsigned long long phase_ns[8];  // classify, choose, hubs, admit, contest, final (block 0's view)
   unsigned long long contest_small, contest_packed, contest_large;
   unsigned int bar_count, bar_gen;
   int err;
@@ -84,6 +84,7 @@ struct LpProblem {
   int32_t *bin[kBins];
   int64_t bin_base[kBins];  // proposal slot of bin position i is bin_base[b] + i
   int32_t *mv_v, *mv_t;
+  int32_t *mv_from;  // label an admitted mover left (its weight is moved in the next sub-round)
   int64_t *mv_gain, *mv_q;
   uint8_t *mv_adm;
   int32_t *mv_of_v;  // vertex -> its proposal index in the current sub-round
@@ -247,6 +248,82 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
   return r;
 }
 
+// ------------------------------------------------------------------------------------ moves
+// Applies the admitted movers of a warp (all lanes call; `adm` marks the lanes whose proposal idx of
+// vertex v to target T was admitted): new label, the left label recorded for the weight update of the
+// next sub-round, neighbours marked active for the next round. Returns the warp's admitted count.
+__device__ __forceinline__ unsigned apply_movers(const LpProblem &P, uint8_t *act_next, bool adm, int64_t idx, int v,
+                                                 int T) {
+  const int lane = threadIdx.x & 31;
+  if (adm) {
+    const int L0 = P.labels[P.vbase + v];
+    P.labels[P.vbase + v] = T;
+    P.mv_from[idx] = L0;
+  }
+  const unsigned am = __ballot_sync(kFull, adm);
+  if (!am) return 0;
+  // mark the neighbours of the admitted movers: the warp walks the concatenation of their rows
+  int64_t rb = 0, deg = 0;
+  if (adm) {
+    rb = P.g.row_begin(v);
+    deg = P.g.row_begin(v + 1) - rb;
+  }
+  int64_t incl = deg;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int64_t excl = incl - deg;
+  const int64_t total = __shfl_sync(kFull, incl, 31);
+  for (int64_t t0 = 0; t0 < total; t0 += 32) {
+    const int64_t t = t0 + lane;
+    // owner: the largest lane j with excl_j <= t
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int64_t ex = __shfl_sync(kFull, excl, j + step);
+      if (j + step < 32 && ex <= t) j += step;
+    }
+    const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
+    if (t < total) act_next[__ldg(P.g.adj + rbj + (t - exj))] = 1;
+  }
+  return (unsigned)__popc(am);
+}
+
+// Weight side of the moves of a finished sub-round (Vp: the block's copy of its counters): every
+// proposed target's demand is cleared, and each admitted mover's weight moves from the label it left
+// to its target.
+__device__ void settle_moves(const LpProblem &P, const SubCounters &Vp, int lb, int nb) {
+  unsigned start[kBins + 1];
+  start[0] = 0;
+#pragma unroll
+  for (int b = 0; b < kBins; b++) start[b + 1] = start[b] + Vp.bin_count[b];
+  const unsigned na = start[kBins];
+  for (unsigned base = (unsigned)lb * kThreads; base < na; base += (unsigned)nb * kThreads) {
+    const unsigned k = base + threadIdx.x;
+    int64_t i = 0;
+    if (k < na) {
+      int b = 0;
+#pragma unroll
+      for (int x = 1; x < kBins; x++)
+        if (k >= start[x]) b = x;
+      i = P.bin_base[b] + (k - start[b]);
+    }
+    const int T = k < na ? P.mv_t[i] : -1;
+    const bool adm = T >= 0 && P.mv_adm[i];
+    if (T >= 0) P.demand[T] = 0;
+    long long c = 0;
+    int L0 = -1;
+    if (adm) {
+      c = P.g.vweight(P.mv_v[i]);
+      L0 = P.mv_from[i];
+    }
+    warp_add_by_key(P.lw, adm, T, c);
+    warp_add_by_key(P.lw, adm, L0, -c);
+  }
+}
+
 // ------------------------------------------------------------------------------------ phases
 // Classify the active vertices of sub-round (r, s) into degree bins. Each block takes a contiguous
 // chunk of vertices, counts them per bin, reserves space with one atomic per bin and then fills it.
@@ -258,9 +335,10 @@ __device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const u
   return d == 0 ? kBinZero : bin_of(d, P.deg_warp, P.deg_cta);
 }
 
-__device__ void phase_classify(const LpProblem &P, SubCounters &C, int r, int s, uint64_t rmix, int lb, int nb,
-                               Smem &sm) {
+__device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCounters *Vp, int r, int s, uint64_t rmix,
+                               int lb, int nb, Smem &sm) {
   __shared__ unsigned s_cnt[8], s_base[8];
+  if (Vp) settle_moves(P, *Vp, lb, nb);
   if (threadIdx.x < 8) {
     sm.vis[threadIdx.x] = 0;
     sm.edg[threadIdx.x] = 0;
@@ -316,32 +394,55 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, int r, int s,
   }
 }
 
-// Groups of G lanes, one vertex per group, d <= G. Equal neighbour labels within a group are found
-// with __match_any_sync and their weights summed over the matching lanes. Each group handles U
-// vertices per step and issues all of their loads before using any (memory-level parallelism).
-template <int G, int EW, bool LQ>
-__device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int lb, int nb) {
-  const unsigned cnt = C.bin_count[bin];
-  if (cnt == 0) return;
-  constexpr int U = G == 32 ? 2 : 4;
-  const int32_t *list = P.bin[bin];
-  constexpr unsigned kGpw = 32 / G;
-  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
-  const unsigned sub = (unsigned)lane / G;
+// Groups of G lanes (G = 4, 8, 16 or 32 for bins 0-3), one vertex per group, d <= G. The four bins
+// share one work loop: warp-iteration j of the concatenated bins takes U * 32/G consecutive vertices
+// of one bin, so small bins overlap instead of running one after another. G is a runtime value (one
+// copy of the code serves every width). Equal neighbour labels within a group are found with
+// __match_any_sync and their weights summed over the matching lanes; each group issues the loads of
+// its U vertices before using any (memory-level parallelism).
+template <bool LQ>
+__device__ __forceinline__ Best group_best_rt(Best b, int W) {
+  for (int o = W / 2; o > 0; o >>= 1) {
+    Best x = shfl_best<LQ>(b, o, W);
+    if (better(x, b)) b = x;
+  }
+  return b;
+}
+
+template <int EW, bool LQ>
+__device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, int nb) {
+  constexpr int U = 2;
+  unsigned pre[5];
+  pre[0] = 0;
+#pragma unroll
+  for (int b = 0; b < 4; b++) {
+    const unsigned per = (32u >> (2 + b)) * U;
+    pre[b + 1] = pre[b] + (V.bin_count[b] + per - 1) / per;
+  }
+  const unsigned total = pre[4];
+  if (total == 0) return;
+  const int lane = threadIdx.x & 31;
   const unsigned gw = (unsigned)lb * kWarps + (threadIdx.x >> 5), nw = (unsigned)nb * kWarps;
-  const unsigned stride = nw * kGpw;
-  for (unsigned base = gw * kGpw; base < cnt; base += stride * U) {
+  for (unsigned j = gw; j < total; j += nw) {
+    const int bin = (j >= pre[1]) + (j >= pre[2]) + (j >= pre[3]);
+    const int G = 4 << bin;
+    const unsigned gpw = 32u >> (2 + bin);
+    const unsigned cnt = V.bin_count[bin];
+    const int32_t *list = P.bin[bin];
+    const int gl = lane & (G - 1);
+    const unsigned sub = (unsigned)lane / (unsigned)G;
+    const unsigned base = (j - pre[bin]) * gpw * U;
     int v[U], Lu[U], L0[U], qq[U];
     long long w[U];
     int64_t beg[U], d[U];
     bool valid[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const unsigned i = base + u * stride + sub;
+      const unsigned i = base + u * gpw + sub;
       valid[u] = i < cnt;
       v[u] = valid[u] ? list[i] : 0;
     }
-#pragma unroll
+    #pragma unroll
     for (int u = 0; u < U; u++) {
       beg[u] = 0;
       d[u] = 0;
@@ -369,7 +470,6 @@ __device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int l
     for (int u = 0; u < U; u++) {
       const bool has = gl < d[u];
       long long c0 = (has && Lu[u] == L0[u]) ? w[u] : 0;
-#pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) c0 += __shfl_xor_sync(kFull, c0, o, G);
       const unsigned long long key = ((unsigned long long)sub << 32) | (unsigned)Lu[u];
       const unsigned peers = __match_any_sync(kFull, key);
@@ -390,9 +490,9 @@ __device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int l
       const long long cv = valid[u] ? P.g.vweight(v[u]) : 0;
       Best b = no_best();
       if (has && first) b = make_cand(P, v[u], Lu[u], L0[u], conn, qs, c0, cv);
-      b = group_best<LQ, G>(b);
+      b = group_best_rt<LQ>(b, G);
       const bool mover = valid[u] && gl == 0 && b.L >= 0;
-      if (valid[u] && gl == 0) write_slot(P, P.bin_base[bin] + base + u * stride + sub, v[u], b, c0);
+      if (valid[u] && gl == 0) write_slot(P, P.bin_base[bin] + base + u * gpw + sub, v[u], b, c0);
       warp_add_by_key(P.demand, mover, b.L, cv);
     }
   }
@@ -400,8 +500,8 @@ __device__ void choose_groups(const LpProblem &P, SubCounters &C, int bin, int l
 
 // One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
 template <int EW, bool LQ>
-__device__ void choose_warp(const LpProblem &P, SubCounters &C, int lb, int nb, unsigned char *dsm) {
-  const unsigned cnt = C.bin_count[4];
+__device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm) {
+  const unsigned cnt = V.bin_count[4];
   if (cnt == 0) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kWarpCap;
@@ -467,8 +567,8 @@ __device__ void choose_warp(const LpProblem &P, SubCounters &C, int lb, int nb, 
 
 // One CTA per vertex (deg_warp < d <= deg_cta), table in shared memory.
 template <int EW, bool LQ>
-__device__ void choose_cta(const LpProblem &P, SubCounters &C, int lb, int nb, unsigned char *dsm, Smem &sm) {
-  const unsigned cnt = C.bin_count[5];
+__device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, Smem &sm) {
+  const unsigned cnt = V.bin_count[5];
   if (cnt == 0) return;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm);
   int *keys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
@@ -531,8 +631,8 @@ __device__ void choose_cta(const LpProblem &P, SubCounters &C, int lb, int nb, u
 }
 
 // Hubs (d > deg_cta): exclusive prefix of their work chunks (one block).
-__device__ void hub_prefix(const LpProblem &P, SubCounters &C, Smem &sm) {
-  const unsigned cnt = C.bin_count[6];
+__device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm) {
+  const unsigned cnt = V.bin_count[6];
   if (threadIdx.x == 0) sm.carry = 0;
   __syncthreads();
   for (unsigned base = 0; base < cnt; base += kThreads) {
@@ -554,8 +654,8 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, Smem &sm) {
 }
 
 template <int EW, bool LQ>
-__device__ void hub_accum(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
-  const unsigned cnt = C.bin_count[6], chunks = C.hub_chunks;
+__device__ void hub_accum(const LpProblem &P, const SubCounters &V, int lb, int nb, Smem &sm) {
+  const unsigned cnt = V.bin_count[6], chunks = V.hub_chunks;
   for (unsigned c = lb; c < chunks; c += nb) {
     unsigned lo = 0, hi = cnt;
     while (hi - lo > 1) {
@@ -598,8 +698,8 @@ __device__ void hub_accum(const LpProblem &P, SubCounters &C, int lb, int nb, Sm
 }
 
 template <bool LQ>
-__device__ void hub_choose(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
-  const unsigned cnt = C.bin_count[6];
+__device__ void hub_choose(const LpProblem &P, const SubCounters &V, int lb, int nb, Smem &sm) {
+  const unsigned cnt = V.bin_count[6];
   for (unsigned i = lb; i < cnt; i += nb) {
     const int v = P.bin[6][i];
     const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
@@ -653,22 +753,26 @@ struct SlotMap {
 // Admission check of every proposal; proposals to targets whose total demand does not fit are
 // recorded as contested.
 template <bool LQ>
-__device__ void phase_admit(const LpProblem &P, SubCounters &C, int lb, int nb, Smem &sm) {
+__device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounters &V, int r, int lb, int nb, Smem &sm) {
   SlotMap M;
-  M.init(P, C);
+  M.init(P, V);
   const unsigned na = M.total();
   unsigned long long mg = 0, mq = 0;
-  unsigned movers = 0;
+  unsigned movers = 0, moved = 0;
+  uint8_t *act_next = P.act[(r + 1) & 1];
   for (unsigned base = (unsigned)lb * kThreads; base < na; base += (unsigned)nb * kThreads) {
     const unsigned k = base + threadIdx.x;
-    bool contested = false;
+    bool contested = false, adm = false;
     int64_t i = 0;
+    int T = -1, v = 0;
     if (k < na) {
       i = M.slot(k);
-      const int T = P.mv_t[i];
+      T = P.mv_t[i];
       if (T >= 0) {
         movers++;
         if (P.lw[T] + P.demand[T] <= P.U) {
+          adm = true;
+          v = P.mv_v[i];
           P.mv_adm[i] = 1;
         } else {
           contested = true;
@@ -677,11 +781,13 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, int lb, int nb, 
         }
       }
     }
+    moved += apply_movers(P, act_next, adm, i, v, T);
     const unsigned pos = warp_append(&C.n_contested, contested);
     if (contested) P.ct[pos] = (unsigned)i;
   }
   movers = (unsigned)block_sum_of((long long)movers, sm);
   if (threadIdx.x == 0 && movers) atomicAdd(&P.ctr->movers, (unsigned long long)movers);
+  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&P.ctr->moves_round[r & 1], (unsigned long long)moved);
   for (int o = 16; o > 0; o >>= 1) {
     mg = max(mg, __shfl_xor_sync(kFull, mg, o));
     mq = max(mq, __shfl_xor_sync(kFull, mq, o));
@@ -708,7 +814,9 @@ __device__ __forceinline__ bool mover_less(const LpProblem &P, unsigned x, unsig
 // snapshot weight plus the prefix fits. at(p) gives (target, proposal index) of position p.
 template <class At>
 __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi, long long carry_in,
-                             int carry_target, Smem &sm) {
+                             int carry_target, int r, Smem &sm) {
+  uint8_t *act_next = P.act[(r + 1) & 1];
+  unsigned moved = 0;
   if (threadIdx.x == 0) {
     sm.carry = carry_in;
     sm.carry_t = carry_target;
@@ -758,7 +866,9 @@ __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi
     }
     __syncthreads();
     const long long incl = f ? x : x + sm.sum[wid];
-    if (valid && P.lw[T] + incl <= P.U) P.mv_adm[idx] = 1;
+    const bool adm = valid && P.lw[T] + incl <= P.U;
+    if (adm) P.mv_adm[idx] = 1;
+    moved += apply_movers(P, act_next, adm, idx, adm ? P.mv_v[idx] : 0, T);
     __syncthreads();
     const unsigned last = min(hi, base + (unsigned)kThreads) - 1;
     if (p == last) {
@@ -767,6 +877,7 @@ __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi
     }
     __syncthreads();
   }
+  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&P.ctr->moves_round[r & 1], (unsigned long long)moved);
 }
 
 __device__ __forceinline__ int bits_for(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
@@ -774,7 +885,7 @@ __device__ __forceinline__ int bits_for(unsigned long long x) { return x ? 64 - 
 // Small contested sets (one CTA). When (target, gain desc, score desc, id) packs into 64 bits the
 // keys are sorted in shared memory (bitonic); otherwise proposal indices are sorted with a comparator.
 template <bool LQ>
-__device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, unsigned char *dsm, Smem &sm) {
+__device__ void contest_small(const LpProblem &P, const SubCounters &C, unsigned cnt, int r, unsigned char *dsm, Smem &sm) {
   unsigned Pp = 1;
   while (Pp < cnt) Pp <<= 1;
   const unsigned long long maxg = C.max_gain, maxq = C.max_q;
@@ -820,7 +931,7 @@ __device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, 
           T = (int)((bt ? (long long)(k >> st) : 0) + P.lbase);
           idx = (unsigned)P.mv_of_v[(int)(k & vmask)];
         },
-        0, cnt, 0, -1, sm);
+        0, cnt, 0, -1, r, sm);
     if (threadIdx.x == 0) P.ctr->contest_packed += 1;
     return;
   }
@@ -851,7 +962,7 @@ __device__ void contest_small(const LpProblem &P, SubCounters &C, unsigned cnt, 
         idx = key[p];
         T = P.mv_t[idx];
       },
-      0, cnt, 0, -1, sm);
+      0, cnt, 0, -1, r, sm);
   if (threadIdx.x == 0) P.ctr->contest_small += 1;
 }
 
@@ -868,8 +979,8 @@ __device__ __forceinline__ unsigned long long field_key(const LpProblem &P, unsi
 // Large contested sets: stable LSD radix sort of the proposal indices over the problem's blocks,
 // least significant key first (id, score sum desc, gain desc, target), then segmented admission.
 template <bool LQ>
-__device__ bool contest_large(const LpProblem &P, SubCounters &C, unsigned cnt, int lb, int nb, const GridBarrier &bar,
-                              Smem &sm) {
+__device__ bool contest_large(const LpProblem &P, const SubCounters &C, unsigned cnt, int r, int lb, int nb,
+                              const GridBarrier &bar, Smem &sm) {
   const unsigned long long maxg = C.max_gain, maxq = C.max_q;
   const int nbits[4] = {bits_for((unsigned long long)(P.g.n > 0 ? P.g.n - 1 : 0)), LQ ? bits_for(maxq) : 0,
                         bits_for(maxg), bits_for((unsigned long long)(P.nl > 0 ? P.nl - 1 : 0))};
@@ -993,74 +1104,11 @@ __device__ bool contest_large(const LpProblem &P, SubCounters &C, unsigned cnt, 
           idx = src[p];
           T = P.mv_t[idx];
         },
-        lo, hi, carry, carry_t, sm);
+        lo, hi, carry, carry_t, r, sm);
   if (lb == 0 && threadIdx.x == 0) P.ctr->contest_large += 1;
   return true;
 }
 
-// Apply admitted moves (32 proposals per warp), update label weights, mark neighbours for the next
-// round and clear the demand of every proposed target.
-__device__ void phase_apply(const LpProblem &P, SubCounters &C, int r, int lb, int nb, Smem &sm) {
-  if (threadIdx.x == 0) sm.moves = 0;
-  __syncthreads();
-  SlotMap M;
-  M.init(P, C);
-  const unsigned na = M.total();
-  uint8_t *act_next = P.act[(r + 1) & 1];
-  const int lane = threadIdx.x & 31;
-  const unsigned gw = (unsigned)lb * kWarps + (threadIdx.x >> 5), nw = (unsigned)nb * kWarps;
-  for (unsigned base = gw * 32; base < na; base += nw * 32) {
-    const unsigned k = base + lane;
-    const int64_t i = k < na ? M.slot(k) : 0;
-    const int T = k < na ? P.mv_t[i] : -1;
-    const bool valid = T >= 0;
-    const bool adm = valid && P.mv_adm[i];
-    const int v = valid ? P.mv_v[i] : 0;
-    if (valid) P.demand[T] = 0;
-    int L0 = -1;
-    long long c = 0;
-    if (adm) {
-      L0 = P.labels[P.vbase + v];
-      c = P.g.vweight(v);
-      P.labels[P.vbase + v] = T;
-    }
-    warp_add_by_key(P.lw, adm, T, c);
-    warp_add_by_key(P.lw, adm, L0, -c);
-    const unsigned am = __ballot_sync(kFull, adm);
-    if (lane == 0 && am) atomicAdd(&sm.moves, (unsigned long long)__popc(am));
-    if (!am) continue;
-    // mark the neighbours of the admitted movers: the warp walks the concatenation of their rows
-    int64_t rb = 0, deg = 0;
-    if (adm) {
-      rb = P.g.row_begin(v);
-      deg = P.g.row_begin(v + 1) - rb;
-    }
-    int64_t incl = deg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int64_t excl = incl - deg;
-    const int64_t total = __shfl_sync(kFull, incl, 31);
-    for (int64_t t0 = 0; t0 < total; t0 += 32) {
-      const int64_t t = t0 + lane;
-      // owner: the largest lane j with excl_j <= t
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int64_t ex = __shfl_sync(kFull, excl, j + step);
-        if (j + step < 32 && ex <= t) j += step;
-      }
-      const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
-      if (t < total) act_next[__ldg(P.g.adj + rbj + (t - exj))] = 1;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && sm.moves) atomicAdd(&P.ctr->moves_round[r & 1], sm.moves);
-}
-
-// ------------------------------------------------------------------------------------ the kernel
 template <int EW, bool LQ>
 __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, const int *block_prob) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -1086,15 +1134,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
       tmark = now;
     }
   };
+  // block-local copies of the sub-round counters (thread 0 reads them once after a barrier)
+  __shared__ SubCounters sV, sVp;
+  auto load_view = [&](const SubCounters &src) {
+    if (threadIdx.x == 0) {
+      const volatile SubCounters &vs = src;
+      for (int b = 0; b < 8; b++) sV.bin_count[b] = vs.bin_count[b];
+      sV.n_movers = vs.n_movers;
+      sV.n_contested = vs.n_contested;
+      sV.hub_chunks = vs.hub_chunks;
+      sV.max_gain = vs.max_gain;
+      sV.max_q = vs.max_q;
+    }
+    __syncthreads();
+  };
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 8; b++) sV.bin_count[b] = 0;
+    sV.n_movers = sV.n_contested = sV.hub_chunks = 0;
+    sV.max_gain = sV.max_q = 0;
+  }
   tick(-1);
+  int t_last = -1;
   for (int r = 0; r < P.rounds; r++) {
     const uint64_t rmix = mix64(P.smix ^ (uint64_t)r);
     for (int s = 0; s < 2; s++) {
       const int t = 2 * r + s;
-      SubCounters &C = ctr->sc[t & 1];
-      SubCounters &Cn = ctr->sc[(t + 1) & 1];
+      SubCounters &C = ctr->sc[t % 3];
+      SubCounters &Cn = ctr->sc[(t + 1) % 3];
       if (lb == 0) {
-        // the other counter set was last used by sub-round t-1, which every block has finished
+        // counter set t+1 was last used by sub-round t-2, which every block has finished
         if (threadIdx.x < 8) Cn.bin_count[threadIdx.x] = 0;
         if (threadIdx.x == 0) {
           Cn.n_movers = 0;
@@ -1104,57 +1172,64 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
           Cn.max_q = 0;
         }
       }
-      phase_classify(P, C, r, s, rmix, lb, nb, sm);
+      if (threadIdx.x == 0) sVp = sV;  // the counters of sub-round t-1
+      __syncthreads();
+      phase_classify(P, C, t > 0 ? &sVp : nullptr, r, s, rmix, lb, nb, sm);
       if (!grid_sync(bar)) return;
+      load_view(C);
       tick(0);
+      t_last = t;
       unsigned active = 0;
-      for (int b = 0; b < kBins; b++) active += *(volatile unsigned *)&C.bin_count[b];
+      for (int b = 0; b < kBins; b++) active += sV.bin_count[b];
       if (active > 0) {
-        if (lb == 0 && P.has_hubs && C.bin_count[6]) hub_prefix(P, C, sm);
-        choose_groups<4, EW, LQ>(P, C, 0, lb, nb);
-        choose_groups<8, EW, LQ>(P, C, 1, lb, nb);
-        choose_groups<16, EW, LQ>(P, C, 2, lb, nb);
-        choose_groups<32, EW, LQ>(P, C, 3, lb, nb);
-        choose_warp<EW, LQ>(P, C, lb, nb, dsm);
-        choose_cta<EW, LQ>(P, C, lb, nb, dsm, sm);
+        if (lb == 0 && P.has_hubs && sV.bin_count[6]) hub_prefix(P, C, sV, sm);
+        choose_groups<EW, LQ>(P, sV, lb, nb);
+        choose_warp<EW, LQ>(P, sV, lb, nb, dsm);
+        choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm);
         if (!grid_sync(bar)) return;
         tick(1);
-        if (P.has_hubs && C.bin_count[6]) {
-          hub_accum<EW, LQ>(P, C, lb, nb, sm);
+        if (P.has_hubs && sV.bin_count[6]) {
+          load_view(C);  // hub_chunks
+          hub_accum<EW, LQ>(P, sV, lb, nb, sm);
           if (!grid_sync(bar)) return;
-          hub_choose<LQ>(P, C, lb, nb, sm);
+          hub_choose<LQ>(P, sV, lb, nb, sm);
           if (!grid_sync(bar)) return;
           tick(2);
         }
         if (lb == 0 && threadIdx.x == 0 && s == 0) ctr->moves_round[(r + 1) & 1] = 0;
-        phase_admit<LQ>(P, C, lb, nb, sm);
+        phase_admit<LQ>(P, C, sV, r, lb, nb, sm);
         if (!grid_sync(bar)) return;
+        load_view(C);  // contested count and key ranges
         tick(3);
-        const unsigned nc = *(volatile unsigned *)&C.n_contested;
+        const unsigned nc = sV.n_contested;
         if (nc > 0) {
           if (nc <= kContestSmall) {
-            if (lb == 0) contest_small<LQ>(P, C, nc, dsm, sm);
+            if (lb == 0) contest_small<LQ>(P, sV, nc, r, dsm, sm);
           } else {
-            if (!contest_large<LQ>(P, C, nc, lb, nb, bar, sm)) return;
+            if (!contest_large<LQ>(P, sV, nc, r, lb, nb, bar, sm)) return;
           }
           if (!grid_sync(bar)) return;
           tick(4);
         }
-        phase_apply(P, C, r, lb, nb, sm);
-        if (!grid_sync(bar)) return;
-        tick(5);
       } else if (lb == 0 && threadIdx.x == 0 && s == 0) {
         ctr->moves_round[(r + 1) & 1] = 0;
       }
     }
     // round end: every block reads the round's move count (final after the last barrier)
-    const unsigned long long mr = *(volatile unsigned long long *)&ctr->moves_round[r & 1];
+    __shared__ unsigned long long s_mr;
+    if (threadIdx.x == 0) s_mr = *(volatile unsigned long long *)&ctr->moves_round[r & 1];
+    __syncthreads();
+    const unsigned long long mr = s_mr;
     if (lb == 0 && threadIdx.x == 0) {
       ctr->rounds += 1;
       ctr->moves += mr;
     }
+    __syncthreads();
     if (mr == 0) break;
   }
+  // label weights of the last sub-round's moves (every block has passed its final barrier)
+  if (t_last >= 0) settle_moves(P, sV, lb, nb);
+  tick(5);
 }
 
 // ------------------------------------------------------------------------------------ host helpers
@@ -1335,6 +1410,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     }
     GP_TRY(ws.get(&P.mv_v, n));
     GP_TRY(ws.get(&P.mv_t, n));
+    GP_TRY(ws.get(&P.mv_from, n));
     GP_TRY(ws.get(&P.mv_gain, n));
     GP_TRY(ws.get(&P.mv_q, n));
     GP_TRY(ws.get(&P.mv_adm, n));
@@ -1431,7 +1507,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
   if (profiling()) {
     static const char *names[6] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hubs", "lp_phase_admit",
-                                   "lp_phase_contest", "lp_phase_apply"};
+                                   "lp_phase_contest", "lp_phase_final"};
     for (int ph = 0; ph < 6; ph++) {
       double ms = 0;
       for (int j = 0; j < njobs; j++) ms += hc[j].phase_ns[ph] * 1e-6;
