@@ -43,6 +43,36 @@ __device__ __forceinline__ int find_graph(const int64_t *base, int count, int64_
   return lo;
 }
 
+// Warp-aggregated atomics: every lane calls; lanes with `on` add (or max/min) their value into the
+// element at `addr`, one atomic per distinct address in the warp. Graphs of a union are contiguous,
+// so the 32 vertices of a warp mostly update the same per-graph counter.
+__device__ __forceinline__ void wadd(unsigned long long *addr, bool on, unsigned long long val) {
+  const unsigned peers = __match_any_sync(kFull, on ? (unsigned long long)addr : 0ull);
+  if (!on) return;
+  unsigned long long sum = 0;
+  for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, val, __ffs(m) - 1);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && sum) atomicAdd(addr, sum);
+}
+__device__ __forceinline__ void wmax(unsigned long long *addr, bool on, unsigned long long val) {
+  const unsigned peers = __match_any_sync(kFull, on ? (unsigned long long)addr : 0ull);
+  if (!on) return;
+  unsigned long long mx = 0;
+  for (unsigned m = peers; m; m &= m - 1) mx = max(mx, __shfl_sync(peers, val, __ffs(m) - 1));
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(addr, mx);
+}
+__device__ __forceinline__ void wmin(unsigned long long *addr, bool on, unsigned long long val) {
+  const unsigned peers = __match_any_sync(kFull, on ? (unsigned long long)addr : 0ull);
+  if (!on) return;
+  unsigned long long mn = ~0ull;
+  for (unsigned m = peers; m; m &= m - 1) mn = min(mn, __shfl_sync(peers, val, __ffs(m) - 1));
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(addr, mn);
+}
+
+// Grid-stride loop in which every lane of a warp runs the same iterations (warp collectives inside).
+#define FOR_WARP_UNIFORM(i, n, valid)                                                                     \
+  for (int64_t i##0 = blockIdx.x * (int64_t)blockDim.x; i##0 < (n); i##0 += (int64_t)gridDim.x * blockDim.x) \
+    for (int64_t i = i##0 + threadIdx.x, valid = i < (n); valid >= 0; valid = -1)
+
 __global__ void k_union_rows(const BatchDesc *d, int count, const int64_t *vb, const int64_t *eb, int64_t N,
                              int64_t *off, int64_t *vw, bool want_vw) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
@@ -80,8 +110,10 @@ __global__ void k_gather_at(const int32_t *src, const int64_t *idx, int count, i
 // first[gi] = smallest coarse id of graph gi's vertices (coarse ids of one graph are contiguous, and
 // below those of the next graph, but f2c of the graph's first vertex need not be the smallest)
 __global__ void k_graph_first(const int32_t *f2c, const int64_t *vb, int count, int64_t n, unsigned long long *first) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    atomicMin(&first[find_graph(vb, count, v)], (unsigned long long)f2c[v]);
+  FOR_WARP_UNIFORM(v, n, ok) {
+    const int gi = ok ? find_graph(vb, count, v) : 0;
+    wmin(&first[gi], ok, ok ? (unsigned long long)f2c[v] : 0);
+  }
 }
 
 __global__ void k_gather_off(const int64_t *off, const int64_t *idx, int count, int64_t *out) {
@@ -90,11 +122,11 @@ __global__ void k_gather_off(const int64_t *off, const int64_t *idx, int count, 
 
 __global__ void k_graph_vstats(DGraph g, const int64_t *vb, int count, unsigned long long *maxc,
                                unsigned long long *wsum) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int gi = find_graph(vb, count, v);
-    const unsigned long long c = (unsigned long long)g.vweight(v);
-    if (maxc) atomicMax(&maxc[gi], c);
-    if (wsum) atomicAdd(&wsum[gi], c);
+  FOR_WARP_UNIFORM(v, g.n, ok) {
+    const int gi = ok ? find_graph(vb, count, v) : 0;
+    const unsigned long long c = ok ? (unsigned long long)g.vweight(v) : 0;
+    if (maxc) wmax(&maxc[gi], ok, c);
+    if (wsum) wadd(&wsum[gi], ok, c);
   }
 }
 
@@ -118,20 +150,21 @@ struct TryEval {
 
 __global__ void k_try_eval(DGraph g, const int64_t *vb, int count, const TryEval *te, int tries,
                            unsigned long long *cut2) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int gi = find_graph(vb, count, v);
+  FOR_WARP_UNIFORM(v, g.n, ok) {
+    const int gi = ok ? find_graph(vb, count, v) : 0;
     const TryEval T = te[gi];
     const int64_t l = v - T.vbase;
-    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
     for (int t = 0; t < tries; t++) {
       const int32_t *p = T.parts + (size_t)t * T.n;
-      const int pv = p[l];
-      atomicAdd(reinterpret_cast<unsigned long long *>(&T.bw[(size_t)t * T.k + pv]), (unsigned long long)g.vweight(v));
+      const int pv = ok ? p[l] : 0;
+      wadd(reinterpret_cast<unsigned long long *>(&T.bw[(size_t)t * T.k + pv]), ok,
+           ok ? (unsigned long long)g.vweight(v) : 0);
       if (!cut2) continue;
       long long c = 0;
-      for (int64_t j = b; j < e; j++)
-        if (p[g.adj[j] - T.vbase] != pv) c += g.eweight(j);
-      if (c) atomicAdd(&cut2[(size_t)gi * tries + t], (unsigned long long)c);
+      if (ok)
+        for (int64_t j = g.row_begin(v); j < g.row_begin(v + 1); j++)
+          if (p[g.adj[j] - T.vbase] != pv) c += g.eweight(j);
+      wadd(&cut2[(size_t)gi * tries + t], ok && c, (unsigned long long)c);
     }
   }
 }
@@ -139,15 +172,16 @@ __global__ void k_try_eval(DGraph g, const int64_t *vb, int count, const TryEval
 // Union partition (local block ids) -> per-graph block weights (bwoff[gi] .. + k_gi) and doubled cuts.
 __global__ void k_union_eval(DGraph g, const int64_t *vb, int count, const int32_t *part, const int64_t *bwoff,
                              int64_t *bw, unsigned long long *cut2) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int gi = find_graph(vb, count, v);
-    const int pv = part[v];
-    atomicAdd(reinterpret_cast<unsigned long long *>(&bw[bwoff[gi] + pv]), (unsigned long long)g.vweight(v));
+  FOR_WARP_UNIFORM(v, g.n, ok) {
+    const int gi = ok ? find_graph(vb, count, v) : 0;
+    const int pv = ok ? part[v] : 0;
+    wadd(reinterpret_cast<unsigned long long *>(&bw[bwoff[gi] + pv]), ok, ok ? (unsigned long long)g.vweight(v) : 0);
     if (cut2) {
       long long c = 0;
-      for (int64_t j = g.row_begin(v); j < g.row_begin(v + 1); j++)
-        if (part[g.adj[j]] != pv) c += g.eweight(j);
-      if (c) atomicAdd(&cut2[gi], (unsigned long long)c);
+      if (ok)
+        for (int64_t j = g.row_begin(v); j < g.row_begin(v + 1); j++)
+          if (part[g.adj[j]] != pv) c += g.eweight(j);
+      wadd(&cut2[gi], ok && c, (unsigned long long)c);
     }
   }
 }
@@ -259,14 +293,10 @@ int to_device(Workspace &ws, const std::vector<T> &h, T **d, cudaStream_t s) {
   return GP_OK;
 }
 
-// Runs LP jobs in launches that fit the co-resident capacity.
+// Runs LP jobs in one launch (small jobs share blocks).
 int run_lp_chunks(std::vector<LpJob> &jobs, cudaStream_t s, const LpConfig &cfg) {
-  const size_t chunk = 256;
-  for (size_t i = 0; i < jobs.size(); i += chunk) {
-    const int cnt = (int)std::min(chunk, jobs.size() - i);
-    GP_TRY(run_lp_multi(jobs.data() + i, cnt, s, cfg));
-  }
-  return GP_OK;
+  if (jobs.empty()) return GP_OK;
+  return run_lp_multi(jobs.data(), (int)jobs.size(), s, cfg);
 }
 
 }  // namespace
@@ -504,10 +534,7 @@ int partition_batch_device(const gp_batch_item *items, int count, const gp_param
     j.parts = parts[i];
     ipj.push_back(j);
   }
-  for (size_t i = 0; i < ipj.size(); i += 128) {
-    const int cnt = (int)std::min<size_t>(128, ipj.size() - i);
-    GP_TRY(initial_partition_multi(ipj.data() + i, cnt, tries, (int)p.repair_rounds, s));
-  }
+  if (!ipj.empty()) GP_TRY(initial_partition_multi(ipj.data(), (int)ipj.size(), tries, (int)p.repair_rounds, s));
   // LP refinement of every try
   TryEval *d_te;
   GP_TRY(to_device(ws, te, &d_te, s));

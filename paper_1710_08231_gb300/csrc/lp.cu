@@ -1110,13 +1110,13 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, unsigned
 }
 
 template <int EW, bool LQ>
-__global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, const int *block_prob) {
-  extern __shared__ __align__(16) unsigned char dsm[];
+__device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   __shared__ __align__(16) unsigned char p_raw[sizeof(LpProblem)];
   __shared__ Smem sm;
   LpProblem &P = *reinterpret_cast<LpProblem *>(p_raw);
+  __syncthreads();  // the block's previous problem is done with the shared state
   {
-    const unsigned *src = reinterpret_cast<const unsigned *>(probs + block_prob[blockIdx.x]);
+    const unsigned *src = reinterpret_cast<const unsigned *>(prob);
     unsigned *dst = reinterpret_cast<unsigned *>(p_raw);
     for (unsigned i = threadIdx.x; i < sizeof(LpProblem) / 4; i += kThreads) dst[i] = src[i];
   }
@@ -1175,7 +1175,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
       if (threadIdx.x == 0) sVp = sV;  // the counters of sub-round t-1
       __syncthreads();
       phase_classify(P, C, t > 0 ? &sVp : nullptr, r, s, rmix, lb, nb, sm);
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar)) return false;
       load_view(C);
       tick(0);
       t_last = t;
@@ -1186,19 +1186,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
         choose_groups<EW, LQ>(P, sV, lb, nb);
         choose_warp<EW, LQ>(P, sV, lb, nb, dsm);
         choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm);
-        if (!grid_sync(bar)) return;
+        if (!grid_sync(bar)) return false;
         tick(1);
         if (P.has_hubs && sV.bin_count[6]) {
           load_view(C);  // hub_chunks
           hub_accum<EW, LQ>(P, sV, lb, nb, sm);
-          if (!grid_sync(bar)) return;
+          if (!grid_sync(bar)) return false;
           hub_choose<LQ>(P, sV, lb, nb, sm);
-          if (!grid_sync(bar)) return;
+          if (!grid_sync(bar)) return false;
           tick(2);
         }
         if (lb == 0 && threadIdx.x == 0 && s == 0) ctr->moves_round[(r + 1) & 1] = 0;
         phase_admit<LQ>(P, C, sV, r, lb, nb, sm);
-        if (!grid_sync(bar)) return;
+        if (!grid_sync(bar)) return false;
         load_view(C);  // contested count and key ranges
         tick(3);
         const unsigned nc = sV.n_contested;
@@ -1206,9 +1206,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
           if (nc <= kContestSmall) {
             if (lb == 0) contest_small<LQ>(P, sV, nc, r, dsm, sm);
           } else {
-            if (!contest_large<LQ>(P, sV, nc, r, lb, nb, bar, sm)) return;
+            if (!contest_large<LQ>(P, sV, nc, r, lb, nb, bar, sm)) return false;
           }
-          if (!grid_sync(bar)) return;
+          if (!grid_sync(bar)) return false;
           tick(4);
         }
       } else if (lb == 0 && threadIdx.x == 0 && s == 0) {
@@ -1230,19 +1230,51 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
   // label weights of the last sub-round's moves (every block has passed its final barrier)
   if (t_last >= 0) settle_moves(P, sV, lb, nb);
   tick(5);
+  return true;
+}
+
+// One launch runs every problem: block b runs the problems blk_list[blk_start[b] .. blk_start[b+1])
+// in order. A problem of several blocks is the only problem of each of its blocks; problems of one
+// block may share a block with others (small graphs of a batch).
+template <int EW, bool LQ>
+__global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, const int *blk_start, const int *blk_list) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  for (int q = blk_start[blockIdx.x]; q < blk_start[blockIdx.x + 1]; q++)
+    if (!lp_problem<EW, LQ>(probs + blk_list[q], dsm)) return;
 }
 
 // ------------------------------------------------------------------------------------ host helpers
-__global__ void k_degree_classes(DGraph g, int deg_warp, int deg_cta, unsigned *counts) {
-  __shared__ unsigned int cnt[8];
-  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
-    if (d > 0) atomicAdd(&cnt[bin_of(d, deg_warp, deg_cta)], 1u);
+// Degree classes and CSR entries of every job of a launch: counts[9 j + bin] vertices per bin and
+// counts64[j] entries. Vertex x of the concatenation belongs to the job j with pre[j] <= x < pre[j+1].
+__global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs, int deg_warp, int deg_cta,
+                                 unsigned *counts, unsigned long long *entries) {
+  const int64_t total = pre[njobs];
+  const int lane = threadIdx.x & 31;
+  for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total; x0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = x0 + threadIdx.x;
+    int j = -1, bin = -1;
+    int64_t d = 0;
+    if (x < total) {
+      int lo = 0, hi = njobs;  // largest j with pre[j] <= x
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= x) lo = mid;
+        else hi = mid;
+      }
+      j = lo;
+      const DGraph &g = gs[j];
+      const int64_t v = x - pre[j];
+      d = g.row_begin(v + 1) - g.row_begin(v);
+      if (d > 0) bin = bin_of(d, deg_warp, deg_cta);
+    }
+    // one atomic per distinct (job, bin) and per distinct job in the warp
+    const unsigned pk = __match_any_sync(kFull, (j << 3) | (bin & 7));
+    if (bin >= 0 && lane == __ffs(pk) - 1) atomicAdd(&counts[9 * j + bin], (unsigned)__popc(pk));
+    const unsigned pj = __match_any_sync(kFull, j);
+    unsigned long long dsum = 0;
+    for (unsigned m = pj; m; m &= m - 1) dsum += (unsigned long long)__shfl_sync(pj, d, __ffs(m) - 1);
+    if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&entries[j], dsum);
   }
-  __syncthreads();
-  if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], cnt[threadIdx.x]);
 }
 
 __global__ void k_hub_mark(DGraph g, int deg_cta, int32_t *hub_of, int64_t *hub_cap, unsigned *count) {
@@ -1304,8 +1336,8 @@ int coop_capacity(int ew, bool lq, int *out) {
 }
 
 template <int EW, bool LQ>
-int launch_lp(const LpProblem *probs_dev, const int *block_prob_dev, int grid, cudaStream_t s) {
-  void *args[] = {(void *)&probs_dev, (void *)&block_prob_dev};
+int launch_lp(const LpProblem *probs_dev, const int *blk_start_dev, const int *blk_list_dev, int grid, cudaStream_t s) {
+  void *args[] = {(void *)&probs_dev, (void *)&blk_start_dev, (void *)&blk_list_dev};
   count_launch();
   GP_CUDA(cudaLaunchCooperativeKernel((void *)k_lp<EW, LQ>, grid, kThreads, args, kDynSmem, s));
   return GP_OK;
@@ -1352,36 +1384,124 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   Workspace ws(s);
   int cap_blocks = 0;
   GP_TRY(coop_capacity(ew, lq, &cap_blocks));
-  if (njobs > cap_blocks) {
-    set_error("run_lp_multi: more jobs than co-resident blocks");
-    return GP_ERR_UNSUPPORTED;
-  }
   const int nsm = num_sms();
-  // blocks per job: about one block per 256 vertices, within the co-resident capacity
-  std::vector<int64_t> want(njobs);
-  int64_t total_want = 0;
+  // degree classes and entry counts of all jobs (one kernel, one copy back)
+  std::vector<DGraph> hg(njobs);
+  std::vector<int64_t> pre(njobs + 1, 0);
   for (int j = 0; j < njobs; j++) {
-    want[j] = std::max<int64_t>(1, std::min<int64_t>(cap_blocks, (jobs[j].g.n + 255) / 256));
-    total_want += want[j];
+    hg[j] = jobs[j].g;
+    pre[j + 1] = pre[j] + jobs[j].g.n;
   }
-  if (total_want > cap_blocks)
-    for (int j = 0; j < njobs; j++) want[j] = std::max<int64_t>(1, want[j] * (cap_blocks - njobs) / total_want);
-  std::vector<LpProblem> hp(njobs);
-  std::vector<int> block_prob;
+  DGraph *gs_dev;
+  int64_t *pre_dev;
   unsigned *classes;
-  GP_TRY(ws.zeros(&classes, (size_t)8 * njobs));
+  unsigned long long *entries;
+  GP_TRY(ws.get(&gs_dev, (size_t)njobs));
+  GP_TRY(ws.get(&pre_dev, (size_t)njobs + 1));
+  GP_TRY(ws.zeros(&classes, (size_t)9 * njobs));
+  GP_TRY(ws.zeros(&entries, (size_t)njobs));
+  GP_CUDA(cudaMemcpyAsync(gs_dev, hg.data(), sizeof(DGraph) * njobs, cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(pre_dev, pre.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, s));
+  if (pre[njobs] > 0) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((pre[njobs] + 255) / 256, nsm * 8));
+    (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, njobs, cfg.deg_warp, cfg.deg_cta,
+                                                                     classes, entries));
+    GP_LAUNCH_CHECK();
+  }
+  std::vector<unsigned> hcls(9 * (size_t)njobs);
+  std::vector<unsigned long long> hent(njobs);
+  GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaMemcpyAsync(hent.data(), entries, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  // Blocks: a job gets at most one block per 256 vertices. When all jobs fit the co-resident
+  // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
+  // + a fixed per-problem latency term): jobs above twice the mean block load get several blocks,
+  // the rest run one block each, packed onto the remaining blocks longest first.
+  std::vector<int64_t> useful(njobs);
+  int64_t sum_useful = 0;
   for (int j = 0; j < njobs; j++) {
-    const DGraph &g = jobs[j].g;
-    if (g.n > 0) {
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, nsm * 8));
-      (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(g, cfg.deg_warp, cfg.deg_cta, classes + 8 * j));
-      GP_LAUNCH_CHECK();
+    useful[j] = std::max<int64_t>(1, std::min<int64_t>(cap_blocks, (jobs[j].g.n + 255) / 256));
+    sum_useful += useful[j];
+  }
+  std::vector<int> nblk(njobs, 1), home(njobs, -1);
+  std::vector<std::vector<int>> packed;
+  if (sum_useful <= cap_blocks) {
+    for (int j = 0; j < njobs; j++) nblk[j] = (int)useful[j];
+  } else {
+    constexpr double kProblemCost = 65536.0;
+    std::vector<double> cost(njobs);
+    double total = 0;
+    for (int j = 0; j < njobs; j++) {
+      cost[j] = (double)hent[j] + 4.0 * (double)jobs[j].g.n + kProblemCost;
+      total += cost[j];
+    }
+    const double wstar = total / cap_blocks;
+    int64_t multi = 0;
+    for (int j = 0; j < njobs; j++)
+      if (cost[j] > 2 * wstar) {
+        nblk[j] = (int)std::min<int64_t>(useful[j], std::max<int64_t>(2, (int64_t)(cost[j] / wstar)));
+        multi += nblk[j];
+      }
+    int nsingle = 0;
+    for (int j = 0; j < njobs; j++) nsingle += nblk[j] == 1 ? 1 : 0;
+    const int64_t want_single = nsingle ? std::max<int64_t>(1, cap_blocks / 8) : 0;
+    if (multi + want_single > cap_blocks) {
+      // shrink the multi-block jobs proportionally
+      const double f = (double)(cap_blocks - want_single) / (double)multi;
+      multi = 0;
+      for (int j = 0; j < njobs; j++)
+        if (nblk[j] > 1) {
+          nblk[j] = std::max(1, (int)(nblk[j] * f));
+          multi += nblk[j];
+        }
+    }
+    nsingle = 0;
+    for (int j = 0; j < njobs; j++) nsingle += nblk[j] == 1 ? 1 : 0;
+    const int nb_single = (int)std::min<int64_t>(nsingle, cap_blocks - multi);
+    packed.assign(nb_single, {});
+    std::vector<int> order;
+    for (int j = 0; j < njobs; j++)
+      if (nblk[j] == 1) order.push_back(j);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y] || (cost[x] == cost[y] && x < y); });
+    std::vector<double> load(nb_single, 0.0);
+    for (int j : order) {
+      int best = 0;
+      for (int b = 1; b < nb_single; b++)
+        if (load[b] < load[best]) best = b;
+      load[best] += cost[j];
+      packed[best].push_back(j);
+      home[j] = best;
     }
   }
-  std::vector<unsigned> hcls(8 * (size_t)njobs);
-  GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
-  std::vector<LpCounters *> ctrs(njobs);
+  // block lists: multi-block (and, without packing, all) jobs first, then the packed blocks
+  std::vector<int> blk_start{0}, blk_list;
+  std::vector<int> first_block(njobs, -1);
+  for (int j = 0; j < njobs; j++) {
+    if (home[j] >= 0) continue;
+    first_block[j] = (int)blk_start.size() - 1;
+    for (int b = 0; b < nblk[j]; b++) {
+      blk_list.push_back(j);
+      blk_start.push_back((int)blk_list.size());
+    }
+  }
+  for (auto &pb : packed) {
+    const int blk = (int)blk_start.size() - 1;
+    for (int j : pb) {
+      first_block[j] = blk;
+      blk_list.push_back(j);
+    }
+    blk_start.push_back((int)blk_list.size());
+  }
+  const int grid = (int)blk_start.size() - 1;
+  if (grid > cap_blocks) {
+    set_error("run_lp_multi: block assignment exceeds the co-resident capacity");
+    return GP_ERR_INTERNAL;
+  }
+  std::vector<LpProblem> hp(njobs);
+  LpCounters *ctr_all;
+  unsigned *bar_all;
+  GP_TRY(ws.zeros(&ctr_all, (size_t)njobs));
+  GP_TRY(ws.zeros(&bar_all, (size_t)njobs * kBarrierStride));
   for (int j = 0; j < njobs; j++) {
     const LpJob &jb = jobs[j];
     LpProblem &P = hp[j];
@@ -1398,15 +1518,14 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.labels = jb.labels;
     P.lw = jb.lw;
     P.q = jb.q;
-    P.block_begin = (int)block_prob.size();
-    P.block_count = (int)want[j];
-    for (int64_t b = 0; b < want[j]; b++) block_prob.push_back(j);
+    P.block_begin = first_block[j];
+    P.block_count = nblk[j];
     const size_t n = (size_t)std::max<int64_t>(jb.g.n, 1);
     int64_t slots_total = 0;
     for (int b = 0; b < kBins; b++) {
-      GP_TRY(ws.get(&P.bin[b], (size_t)std::max<unsigned>(hcls[8 * j + b], 1)));
+      GP_TRY(ws.get(&P.bin[b], (size_t)std::max<unsigned>(hcls[9 * j + b], 1)));
       P.bin_base[b] = slots_total;
-      slots_total += hcls[8 * j + b];
+      slots_total += hcls[9 * j + b];
     }
     GP_TRY(ws.get(&P.mv_v, n));
     GP_TRY(ws.get(&P.mv_t, n));
@@ -1423,12 +1542,11 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.act[1], n));
     P.act[0] -= jb.vbase;  // indexed by global vertex id
     P.act[1] -= jb.vbase;
-    GP_TRY(ws.get(&P.hist, (size_t)want[j] * 256 + 16));
-    GP_TRY(ws.get(&P.hoff, (size_t)want[j] * 256 + 256 + 16));
-    GP_TRY(ws.zeros(&P.ctr, 1));
-    GP_TRY(ws.zeros(&P.bar, barrier_words((unsigned)want[j])));
-    ctrs[j] = P.ctr;
-    const unsigned nhub = hcls[8 * j + 6];
+    GP_TRY(ws.get(&P.hist, (size_t)nblk[j] * 256 + 16));
+    GP_TRY(ws.get(&P.hoff, (size_t)nblk[j] * 256 + 256 + 16));
+    P.ctr = ctr_all + j;
+    P.bar = bar_all + (size_t)j * kBarrierStride;
+    const unsigned nhub = hcls[9 * j + 6];
     if (nhub) {
       int32_t *hub_of;
       int64_t *hub_cap, *hub_base, *total;
@@ -1457,26 +1575,26 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     }
   }
   LpProblem *probs_dev;
-  int *bp_dev;
+  int *bs_dev, *bl_dev;
   GP_TRY(ws.get(&probs_dev, hp.size()));
-  GP_TRY(ws.get(&bp_dev, block_prob.size()));
+  GP_TRY(ws.get(&bs_dev, blk_start.size()));
+  GP_TRY(ws.get(&bl_dev, blk_list.size()));
   GP_CUDA(cudaMemcpyAsync(probs_dev, hp.data(), sizeof(LpProblem) * hp.size(), cudaMemcpyHostToDevice, s));
-  GP_CUDA(cudaMemcpyAsync(bp_dev, block_prob.data(), sizeof(int) * block_prob.size(), cudaMemcpyHostToDevice, s));
-  const int grid = (int)block_prob.size();
+  GP_CUDA(cudaMemcpyAsync(bs_dev, blk_start.data(), sizeof(int) * blk_start.size(), cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(bl_dev, blk_list.data(), sizeof(int) * blk_list.size(), cudaMemcpyHostToDevice, s));
   {
     ProfScope ps("lp_persistent", s);
     int st;
-    if (lq) st = ew == 0 ? launch_lp<0, true>(probs_dev, bp_dev, grid, s)
-               : ew == 1 ? launch_lp<1, true>(probs_dev, bp_dev, grid, s)
-                         : launch_lp<2, true>(probs_dev, bp_dev, grid, s);
-    else st = ew == 0 ? launch_lp<0, false>(probs_dev, bp_dev, grid, s)
-              : ew == 1 ? launch_lp<1, false>(probs_dev, bp_dev, grid, s)
-                        : launch_lp<2, false>(probs_dev, bp_dev, grid, s);
+    if (lq) st = ew == 0 ? launch_lp<0, true>(probs_dev, bs_dev, bl_dev, grid, s)
+               : ew == 1 ? launch_lp<1, true>(probs_dev, bs_dev, bl_dev, grid, s)
+                         : launch_lp<2, true>(probs_dev, bs_dev, bl_dev, grid, s);
+    else st = ew == 0 ? launch_lp<0, false>(probs_dev, bs_dev, bl_dev, grid, s)
+              : ew == 1 ? launch_lp<1, false>(probs_dev, bs_dev, bl_dev, grid, s)
+                        : launch_lp<2, false>(probs_dev, bs_dev, bl_dev, grid, s);
     GP_TRY(st);
   }
   std::vector<LpCounters> hc(njobs);
-  for (int j = 0; j < njobs; j++)
-    GP_CUDA(cudaMemcpyAsync(&hc[j], ctrs[j], sizeof(LpCounters), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaMemcpyAsync(hc.data(), ctr_all, sizeof(LpCounters) * njobs, cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
   int64_t tot_edges = 0, tot_vis = 0, tot_bytes = 0;
   for (int j = 0; j < njobs; j++) {
