@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_row_warp(RowArgs a) {
 
 
 
-__device__ __forceinline__ unsigned row_slot(int cu) { return (unsigned)cu * 0x9E3779B1u; }
+__device__ __forceinline__ unsigned row_slot(int cu) { return mix32((unsigned)cu); }
 
 // Rows with 32 < pairs <= 256: one warp sums the pairs by neighbour id in a shared-memory hash
 // table, compacts the distinct ids and sorts them (bitonic) before writing the row.

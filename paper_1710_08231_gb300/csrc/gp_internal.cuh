@@ -122,6 +122,18 @@ __host__ __device__ __forceinline__ uint64_t hash3(uint64_t a, uint64_t b, uint6
   return mix64(mix64(mix64(a) ^ b) ^ c);
 }
 
+// Slot hash for open-addressing tables: the 32-bit finalizer of MurmurHash3 (Appleby), a bijection
+// whose low bits depend on every input bit. Vertex ids of skewed generators (R-MAT) share their low
+// bits far more often than uniform ids, so a table index must not be taken from them directly.
+__host__ __device__ __forceinline__ unsigned mix32(unsigned h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
 // ------------------------------------------------------------------------------------------ graph
 // Device view of a CSR graph with runtime-typed offsets and weights.
 struct DGraph {

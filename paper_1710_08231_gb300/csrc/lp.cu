@@ -38,8 +38,11 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpCap = 256;   // table slots per warp (d <= 128)
 constexpr int kCtaCap = 2048;   // table slots per CTA (d <= 1024)
-constexpr int kHubChunk = 4096; // CSR entries per hub work item
+constexpr int kHubChunk = 1024; // CSR entries per hub work item (pre-aggregated in a 2048-slot table)
+constexpr int64_t kHubBatchSlots = int64_t(1) << 22;  // hub table slots per batch (tables stay in L2)
+constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
+constexpr int64_t kBigDeg = 2048;  // movers above this degree mark their neighbours with every block
 constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
 static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
@@ -49,6 +52,8 @@ struct SubCounters {
   unsigned int n_movers;
   unsigned int n_contested;
   unsigned int hub_chunks;
+  unsigned int n_big;  // admitted movers of degree > kBigDeg (their neighbours are marked by all blocks)
+  unsigned int hub_batches;
   unsigned int pad;
   unsigned long long max_gain, max_q;
 };
@@ -58,8 +63,10 @@ struct LpCounters {
   unsigned long long moves_round[2];  // by round parity
   unsigned long long moves, rounds, movers;
   unsigned long long bin_visits[8], bin_edges[8];
-  unsigned long long phase_ns[8];  // classify, choose, hubs, admit, contest, final (block 0's view)
+  unsigned long long phase_ns[8];  // classify, choose, hub accumulation, admit, contest, final, hub choice,
+                                   // hub prefix (block 0's view)
   unsigned long long contest_small, contest_packed, contest_large;
+  unsigned long long contest_large_items, hub_entries, hub_slots;
   unsigned int bar_count, bar_gen;
   int err;
   int pad;
@@ -90,13 +97,22 @@ struct LpProblem {
   int32_t *mv_of_v;  // vertex -> its proposal index in the current sub-round
   int64_t *demand;
   uint32_t *ct, *ct2;
-  const int32_t *hub_of;
-  const int64_t *hub_base;
+  unsigned long long *ck, *ck2;  // packed contest keys (large contests)
+  int32_t *big;                  // admitted movers of degree > kBigDeg in the current sub-round
+  // hubs (bin 6), per position i of the sub-round's hub list: own-label connection, prefixes of
+  // chunks, table slots and choice items, table base inside its batch; first position of each batch
+  long long *hub_c0;
+  unsigned int *hub_prefix;
+  long long *hub_capx;
+  unsigned int *hub_scx;
+  long long *hub_tb;
+  unsigned int *hub_bstart;
+  long long *hub_bbase;
+  // one batch's tables (reused by every batch; cleared by the choice scan) and partial choices
   int32_t *hub_keys;
   unsigned long long *hub_vals;
   unsigned int *hub_qv;
-  long long *hub_c0;
-  unsigned int *hub_prefix;
+  unsigned char *hub_part;
   unsigned int *hist;        // block_count * 256
   unsigned long long *hoff;  // block_count * 256 + 256
   unsigned int *bar;         // barrier_words(block_count)
@@ -208,7 +224,7 @@ __device__ __forceinline__ void write_slot(const LpProblem &P, int64_t idx, int 
   }
 }
 
-__device__ __forceinline__ unsigned slot_hash(int L) { return (unsigned)L * 0x9E3779B1u; }
+__device__ __forceinline__ unsigned slot_hash(int L) { return mix32((unsigned)L); }
 
 struct Smem {
   Best best[kWarps];
@@ -251,23 +267,29 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
 // ------------------------------------------------------------------------------------ moves
 // Applies the admitted movers of a warp (all lanes call; `adm` marks the lanes whose proposal idx of
 // vertex v to target T was admitted): new label, the left label recorded for the weight update of the
-// next sub-round, neighbours marked active for the next round. Returns the warp's admitted count.
-__device__ __forceinline__ unsigned apply_movers(const LpProblem &P, uint8_t *act_next, bool adm, int64_t idx, int v,
-                                                 int T) {
+// next sub-round, neighbours marked active for the next round. Movers of degree above kBigDeg are
+// listed in P.big instead (counter C.n_big); every block marks their neighbours after the phase.
+// Returns the warp's admitted count.
+__device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters &C, uint8_t *act_next, bool adm,
+                                                 int64_t idx, int v, int T) {
   const int lane = threadIdx.x & 31;
+  int64_t rb = 0, deg = 0;
   if (adm) {
     const int L0 = P.labels[P.vbase + v];
     P.labels[P.vbase + v] = T;
     P.mv_from[idx] = L0;
-  }
-  const unsigned am = __ballot_sync(kFull, adm);
-  if (!am) return 0;
-  // mark the neighbours of the admitted movers: the warp walks the concatenation of their rows
-  int64_t rb = 0, deg = 0;
-  if (adm) {
     rb = P.g.row_begin(v);
     deg = P.g.row_begin(v + 1) - rb;
   }
+  const unsigned am = __ballot_sync(kFull, adm);
+  if (!am) return 0;
+  const bool big = adm && deg > kBigDeg;
+  const unsigned pos = warp_append(&C.n_big, big);
+  if (big) {
+    P.big[pos] = v;
+    deg = 0;
+  }
+  // mark the neighbours of the other admitted movers: the warp walks the concatenation of their rows
   int64_t incl = deg;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -289,6 +311,17 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, uint8_t *ac
     if (t < total) act_next[__ldg(P.g.adj + rbj + (t - exj))] = 1;
   }
   return (unsigned)__popc(am);
+}
+
+// Neighbours of the listed high-degree movers, marked by all blocks of the problem together.
+__device__ void mark_big(const LpProblem &P, unsigned nbig, int r, int lb, int nb) {
+  uint8_t *act_next = P.act[(r + 1) & 1];
+  for (unsigned i = 0; i < nbig; i++) {
+    const int v = P.big[i];
+    const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+    for (int64_t e = rb + (int64_t)lb * kThreads + threadIdx.x; e < re; e += (int64_t)nb * kThreads)
+      act_next[__ldg(P.g.adj + e)] = 1;
+  }
 }
 
 // Weight side of the moves of a finished sub-round (Vp: the block's copy of its counters): every
@@ -498,6 +531,37 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
   }
 }
 
+// Warp-cooperative insert of (label L, weight w, score q) into an open-addressing table in shared
+// memory (slots keys/vals/qv, `mask` = slots - 1). Lanes are grouped by label first, so each distinct
+// label of the warp costs one insert however many neighbours carry it. All lanes call; lanes with
+// `on` false contribute nothing.
+template <int EW, bool LQ>
+__device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals, unsigned *qv, unsigned mask, bool on,
+                                            int L, long long w, unsigned q) {
+  const unsigned peers = __match_any_sync(kFull, on ? L : -1);
+  if (!on) return;
+  long long sum;
+  if constexpr (EW == 0) {
+    sum = __popc(peers);
+  } else {
+    sum = 0;
+    for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, w, __ffs(m) - 1);
+  }
+  unsigned qs = 0;
+  if constexpr (LQ) qs = __reduce_add_sync(peers, q);
+  if ((int)(threadIdx.x & 31) != __ffs(peers) - 1) return;
+  unsigned sl = slot_hash(L) & mask;
+  while (true) {
+    const int k = atomicCAS(&keys[sl], -1, L);
+    if (k == -1 || k == L) {
+      atomicAdd(&vals[sl], (unsigned long long)sum);
+      if (LQ) atomicAdd(&qv[sl], qs);
+      return;
+    }
+    sl = (sl + 1) & mask;
+  }
+}
+
 // One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
 template <int EW, bool LQ>
 __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm) {
@@ -524,23 +588,13 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
     const unsigned mask = (unsigned)cap - 1;
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      const int L = P.labels[__ldg(P.g.adj + e)];
-      const long long w = load_ew<EW>(P.g.ew, e);
-      if (L == L0) {
-        c0 += w;
-        continue;
-      }
-      unsigned s = slot_hash(L) & mask;
-      while (true) {
-        const int k = atomicCAS(&keys[s], -1, L);
-        if (k == -1 || k == L) {
-          atomicAdd(&vals[s], (unsigned long long)w);
-          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(P.q + e));
-          break;
-        }
-        s = (s + 1) & mask;
-      }
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool in = e < end;
+      const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
+      const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
+      if (in && L == L0) c0 += w;
+      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
     }
     c0 = warp_sum64(c0);
     __syncwarp();
@@ -590,23 +644,13 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
     const unsigned mask = (unsigned)cap - 1;
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
-      const int L = P.labels[__ldg(P.g.adj + e)];
-      const long long w = load_ew<EW>(P.g.ew, e);
-      if (L == L0) {
-        c0 += w;
-        continue;
-      }
-      unsigned s = slot_hash(L) & mask;
-      while (true) {
-        const int k = atomicCAS(&keys[s], -1, L);
-        if (k == -1 || k == L) {
-          atomicAdd(&vals[s], (unsigned long long)w);
-          if (LQ) atomicAdd(&qv[s], (unsigned)__ldg(P.q + e));
-          break;
-        }
-        s = (s + 1) & mask;
-      }
+    for (int64_t e0 = beg + (threadIdx.x & ~31); e0 < end; e0 += kThreads) {
+      const int64_t e = e0 + (threadIdx.x & 31);
+      const bool in = e < end;
+      const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
+      const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
+      if (in && L == L0) c0 += w;
+      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
     }
     c0 = block_sum_of(c0, sm);  // also completes the table
     const long long cv = P.g.vweight(v);
@@ -630,101 +674,195 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
   __syncthreads();
 }
 
-// Hubs (d > deg_cta): exclusive prefix of their work chunks (one block).
+// Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (kHubChunk
+// entries), table slots (next_pow2(2d) each) and choice items (kSlotChunk slots); cut into batches of
+// about kHubBatchSlots slots (a hub starts a new batch when its slot prefix crosses a multiple of
+// kHubBatchSlots); table base of each hub inside its batch.
 __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm) {
   const unsigned cnt = V.bin_count[6];
-  if (threadIdx.x == 0) sm.carry = 0;
+  __shared__ long long s_cap, s_ch, s_sc, s_nbat, s_prev_bid;
+  __shared__ long long t_bid[kThreads];
+  if (threadIdx.x == 0) {
+    s_cap = s_ch = s_sc = s_nbat = 0;
+    s_prev_bid = -1;
+  }
   __syncthreads();
+  long long sum_d = 0, sum_cap = 0;
   for (unsigned base = 0; base < cnt; base += kThreads) {
     const unsigned i = base + threadIdx.x;
-    long long c = 0;
-    if (i < cnt) {
+    const bool valid = i < cnt;
+    long long d = 0, cap = 0, ch = 0, sc = 0;
+    if (valid) {
       const int v = P.bin[6][i];
-      const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
-      c = (d + kHubChunk - 1) / kHubChunk;
+      d = P.g.row_begin(v + 1) - P.g.row_begin(v);
+      cap = 64;
+      while (cap < 2 * d) cap <<= 1;
+      ch = (d + kHubChunk - 1) / kHubChunk;
+      sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
+      sum_d += d;
+      sum_cap += cap;
     }
-    const long long ex = block_excl_scan64(c, sm.tmp, &sm.tot);
-    if (i < cnt) P.hub_prefix[i] = (unsigned)(sm.carry + ex);
+    const long long capx = s_cap + block_excl_scan64(cap, sm.tmp, &sm.tot);
+    const long long cap_t = sm.tot;
+    const long long chx = s_ch + block_excl_scan64(ch, sm.tmp, &sm.tot);
+    const long long ch_t = sm.tot;
+    const long long scx = s_sc + block_excl_scan64(sc, sm.tmp, &sm.tot);
+    const long long sc_t = sm.tot;
+    const long long bid = capx / kHubBatchSlots;
+    t_bid[threadIdx.x] = bid;
     __syncthreads();
-    if (threadIdx.x == 0) sm.carry += sm.tot;
+    const long long prev = threadIdx.x > 0 ? t_bid[threadIdx.x - 1] : s_prev_bid;
+    const long long flag = (valid && bid != prev) ? 1 : 0;
+    const long long bx = s_nbat + block_excl_scan64(flag, sm.tmp, &sm.tot);
+    const long long nb_t = sm.tot;
+    if (valid) {
+      P.hub_prefix[i] = (unsigned)chx;
+      P.hub_capx[i] = capx;
+      P.hub_scx[i] = (unsigned)scx;
+    }
+    if (flag) {
+      P.hub_bstart[bx] = i;
+      P.hub_bbase[bx] = capx;
+    }
+    __syncthreads();
+    if (valid) P.hub_tb[i] = capx - P.hub_bbase[bx + flag - 1];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_cap += cap_t;
+      s_ch += ch_t;
+      s_sc += sc_t;
+      s_nbat += nb_t;
+      s_prev_bid = t_bid[min(kThreads, (int)(cnt - base)) - 1];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) C.hub_chunks = (unsigned)sm.carry;
+  if (threadIdx.x == 0) {
+    P.hub_prefix[cnt] = (unsigned)s_ch;
+    P.hub_capx[cnt] = s_cap;
+    P.hub_scx[cnt] = (unsigned)s_sc;
+    P.hub_bstart[s_nbat] = cnt;
+    C.hub_chunks = (unsigned)s_ch;
+    C.hub_batches = (unsigned)s_nbat;
+  }
+  sum_d = block_sum_of(sum_d, sm);
+  sum_cap = block_sum_of(sum_cap, sm);
+  if (threadIdx.x == 0) {
+    P.ctr->hub_entries += (unsigned long long)sum_d;
+    P.ctr->hub_slots += (unsigned long long)sum_cap;
+  }
 }
 
+// largest position i in [lo, hi) with pre[i] <= x
+template <class T>
+__device__ __forceinline__ unsigned search_prefix(const T *pre, unsigned lo, unsigned hi, unsigned long long x) {
+  while (hi - lo > 1) {
+    const unsigned mid = (lo + hi) >> 1;
+    if ((unsigned long long)pre[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunk entries. A block aggregates
+// its chunk's labels in a shared-memory table first and then adds one entry per distinct label to the
+// hub's table, so labels that many neighbours share cost one global atomic per chunk.
 template <int EW, bool LQ>
-__device__ void hub_accum(const LpProblem &P, const SubCounters &V, int lb, int nb, Smem &sm) {
-  const unsigned cnt = V.bin_count[6], chunks = V.hub_chunks;
-  for (unsigned c = lb; c < chunks; c += nb) {
-    unsigned lo = 0, hi = cnt;
-    while (hi - lo > 1) {
-      const unsigned mid = (lo + hi) >> 1;
-      if (P.hub_prefix[mid] <= c) lo = mid;
-      else hi = mid;
-    }
-    const unsigned i = lo;
+__device__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm, unsigned char *dsm) {
+  unsigned long long *svals = reinterpret_cast<unsigned long long *>(dsm);
+  int *skeys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
+  unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCtaCap * 12);
+  for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
+    skeys[t] = -1;
+    svals[t] = 0;
+    if (LQ) sq[t] = 0;
+  }
+  __syncthreads();
+  const unsigned c_lo = P.hub_prefix[h0], c_hi = P.hub_prefix[h1];
+  for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
+    const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
     const int v = P.bin[6][i];
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
     const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
     const int64_t end = min(re, beg + kHubChunk);
-    const int64_t tb = P.hub_base[P.hub_of[v]];
-    int64_t cap = 64;
-    while (cap < 2 * (re - rb)) cap <<= 1;
-    const uint64_t mask = (uint64_t)cap - 1;
+    const int64_t tb = P.hub_tb[i];
+    const uint64_t mask = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]) - 1;
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
-      const int L = P.labels[__ldg(P.g.adj + e)];
-      const long long w = load_ew<EW>(P.g.ew, e);
-      if (L == L0) {
-        c0 += w;
-        continue;
-      }
-      uint64_t s = ((uint64_t)slot_hash(L) * 0x100000001ull) & mask;
+    for (int64_t e0 = beg + (threadIdx.x & ~31); e0 < end; e0 += kThreads) {
+      const int64_t e = e0 + (threadIdx.x & 31);
+      const bool in = e < end;
+      const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
+      const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
+      if (in && L == L0) c0 += w;
+      warp_insert<EW, LQ>(skeys, svals, sq, kCtaCap - 1, in && L != L0, L, w,
+                          (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
+    }
+    c0 = block_sum_of(c0, sm);  // also completes the shared table
+    for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
+      const int L = skeys[t];
+      if (L < 0) continue;
+      uint64_t sg = (uint64_t)slot_hash(L) & mask;
       while (true) {
-        const int k = atomicCAS(&P.hub_keys[tb + s], -1, L);
+        const int k = atomicCAS(&P.hub_keys[tb + sg], -1, L);
         if (k == -1 || k == L) {
-          atomicAdd(&P.hub_vals[tb + s], (unsigned long long)w);
-          if (LQ) atomicAdd(&P.hub_qv[tb + s], (unsigned)__ldg(P.q + e));
+          atomicAdd(&P.hub_vals[tb + sg], svals[t]);
+          if (LQ) atomicAdd(&P.hub_qv[tb + sg], sq[t]);
           break;
         }
-        s = (s + 1) & mask;
+        sg = (sg + 1) & mask;
       }
+      skeys[t] = -1;
+      svals[t] = 0;
+      if (LQ) sq[t] = 0;
     }
-    c0 = block_sum_of(c0, sm);
+    __syncthreads();
     if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
   }
 }
 
+// Choice for batch [h0, h1), part 1: the batch's tables are scanned in items of kSlotChunk slots by all
+// blocks; each item keeps its best eligible label (and clears its slots).
 template <bool LQ>
-__device__ void hub_choose(const LpProblem &P, const SubCounters &V, int lb, int nb, Smem &sm) {
-  const unsigned cnt = V.bin_count[6];
-  for (unsigned i = lb; i < cnt; i += nb) {
+__device__ void hub_choose_part(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm) {
+  const unsigned s_lo = P.hub_scx[h0], s_hi = P.hub_scx[h1];
+  Best *part = reinterpret_cast<Best *>(P.hub_part);
+  for (unsigned it = s_lo + lb; it < s_hi; it += nb) {
+    const unsigned i = search_prefix(P.hub_scx, h0, h1, it);
     const int v = P.bin[6][i];
-    const int64_t d = P.g.row_begin(v + 1) - P.g.row_begin(v);
-    int64_t cap = 64;
-    while (cap < 2 * d) cap <<= 1;
-    const int64_t tb = P.hub_base[P.hub_of[v]];
+    const int64_t cap = P.hub_capx[i + 1] - P.hub_capx[i];
+    const int64_t tb = P.hub_tb[i];
+    const int64_t s0 = (int64_t)(it - P.hub_scx[i]) * kSlotChunk, s1 = min(cap, s0 + kSlotChunk);
     const int L0 = P.labels[P.vbase + v];
     const long long c0 = P.hub_c0[i];
     const long long cv = P.g.vweight(v);
     Best b = no_best();
-    for (int64_t s = threadIdx.x; s < cap; s += kThreads) {
-      const int L = P.hub_keys[tb + s];
+    for (int64_t sl = s0 + threadIdx.x; sl < s1; sl += kThreads) {
+      const int L = P.hub_keys[tb + sl];
       if (L >= 0) {
-        const Best x = make_cand(P, v, L, L0, (long long)P.hub_vals[tb + s], LQ ? (long long)P.hub_qv[tb + s] : 0, c0, cv);
+        const Best x = make_cand(P, v, L, L0, (long long)P.hub_vals[tb + sl], LQ ? (long long)P.hub_qv[tb + sl] : 0, c0, cv);
         if (better(x, b)) b = x;
-        P.hub_keys[tb + s] = -1;
-        P.hub_vals[tb + s] = 0;
-        if (LQ) P.hub_qv[tb + s] = 0;
+        P.hub_keys[tb + sl] = -1;
+        P.hub_vals[tb + sl] = 0;
+        if (LQ) P.hub_qv[tb + sl] = 0;
       }
     }
     b = block_best_of<LQ>(b, sm);
-    if (threadIdx.x == 0) {
-      write_slot(P, P.bin_base[6] + i, v, b, c0);
-      if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
-    }
+    if (threadIdx.x == 0) part[it - s_lo] = b;
+  }
+}
+
+// Choice for batch [h0, h1), part 2: one thread per hub combines its items and records the proposal.
+__device__ void hub_choose_final(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb) {
+  const unsigned s_lo = P.hub_scx[h0];
+  const Best *part = reinterpret_cast<const Best *>(P.hub_part);
+  for (unsigned i = h0 + (unsigned)lb * kThreads + threadIdx.x; i < h1; i += (unsigned)nb * kThreads) {
+    Best b = no_best();
+    for (unsigned it = P.hub_scx[i]; it < P.hub_scx[i + 1]; it++)
+      if (better(part[it - s_lo], b)) b = part[it - s_lo];
+    const int v = P.bin[6][i];
+    write_slot(P, P.bin_base[6] + i, v, b, P.hub_c0[i]);
+    if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)P.g.vweight(v));
   }
 }
 
@@ -781,7 +919,7 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounter
         }
       }
     }
-    moved += apply_movers(P, act_next, adm, i, v, T);
+    moved += apply_movers(P, C, act_next, adm, i, v, T);
     const unsigned pos = warp_append(&C.n_contested, contested);
     if (contested) P.ct[pos] = (unsigned)i;
   }
@@ -814,7 +952,7 @@ __device__ __forceinline__ bool mover_less(const LpProblem &P, unsigned x, unsig
 // snapshot weight plus the prefix fits. at(p) gives (target, proposal index) of position p.
 template <class At>
 __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi, long long carry_in,
-                             int carry_target, int r, Smem &sm) {
+                             int carry_target, int r, SubCounters *Cg, Smem &sm) {
   uint8_t *act_next = P.act[(r + 1) & 1];
   unsigned moved = 0;
   if (threadIdx.x == 0) {
@@ -868,7 +1006,7 @@ __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi
     const long long incl = f ? x : x + sm.sum[wid];
     const bool adm = valid && P.lw[T] + incl <= P.U;
     if (adm) P.mv_adm[idx] = 1;
-    moved += apply_movers(P, act_next, adm, idx, adm ? P.mv_v[idx] : 0, T);
+    moved += apply_movers(P, *Cg, act_next, adm, idx, adm ? P.mv_v[idx] : 0, T);
     __syncthreads();
     const unsigned last = min(hi, base + (unsigned)kThreads) - 1;
     if (p == last) {
@@ -885,7 +1023,8 @@ __device__ __forceinline__ int bits_for(unsigned long long x) { return x ? 64 - 
 // Small contested sets (one CTA). When (target, gain desc, score desc, id) packs into 64 bits the
 // keys are sorted in shared memory (bitonic); otherwise proposal indices are sorted with a comparator.
 template <bool LQ>
-__device__ void contest_small(const LpProblem &P, const SubCounters &C, unsigned cnt, int r, unsigned char *dsm, Smem &sm) {
+__device__ void contest_small(const LpProblem &P, const SubCounters &C, SubCounters *Cg, unsigned cnt, int r,
+                              unsigned char *dsm, Smem &sm) {
   unsigned Pp = 1;
   while (Pp < cnt) Pp <<= 1;
   const unsigned long long maxg = C.max_gain, maxq = C.max_q;
@@ -931,7 +1070,7 @@ __device__ void contest_small(const LpProblem &P, const SubCounters &C, unsigned
           T = (int)((bt ? (long long)(k >> st) : 0) + P.lbase);
           idx = (unsigned)P.mv_of_v[(int)(k & vmask)];
         },
-        0, cnt, 0, -1, r, sm);
+        0, cnt, 0, -1, r, Cg, sm);
     if (threadIdx.x == 0) P.ctr->contest_packed += 1;
     return;
   }
@@ -962,7 +1101,7 @@ __device__ void contest_small(const LpProblem &P, const SubCounters &C, unsigned
         idx = key[p];
         T = P.mv_t[idx];
       },
-      0, cnt, 0, -1, r, sm);
+      0, cnt, 0, -1, r, Cg, sm);
   if (threadIdx.x == 0) P.ctr->contest_small += 1;
 }
 
@@ -976,85 +1115,120 @@ __device__ __forceinline__ unsigned long long field_key(const LpProblem &P, unsi
   }
 }
 
-// Large contested sets: stable LSD radix sort of the proposal indices over the problem's blocks,
-// least significant key first (id, score sum desc, gain desc, target), then segmented admission.
+// Large contested sets: stable LSD radix sort over the problem's blocks, then segmented admission.
+// When (target, gain desc, score desc, id) fits 64 bits the key is built once per mover and carried
+// with its proposal index (contiguous reads); otherwise the fields are gathered from the proposal
+// arrays in every pass, least significant first (id, score sum desc, gain desc, target).
 template <bool LQ>
-__device__ bool contest_large(const LpProblem &P, const SubCounters &C, unsigned cnt, int r, int lb, int nb,
-                              const GridBarrier &bar, Smem &sm) {
+__device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCounters *Cg, unsigned cnt, int r, int lb,
+                              int nb, const GridBarrier &bar, Smem &sm, unsigned char *dsm) {
   const unsigned long long maxg = C.max_gain, maxq = C.max_q;
   const int nbits[4] = {bits_for((unsigned long long)(P.g.n > 0 ? P.g.n - 1 : 0)), LQ ? bits_for(maxq) : 0,
                         bits_for(maxg), bits_for((unsigned long long)(P.nl > 0 ? P.nl - 1 : 0))};
+  const int tbits = nbits[0] + nbits[1] + nbits[2] + nbits[3];
+  const bool packed = tbits <= 64;
+  const int sq = nbits[0], sg = nbits[0] + nbits[1], st = nbits[0] + nbits[1] + nbits[2];
   const unsigned chunk = (cnt + nb - 1) / nb;
   const unsigned lo = min(cnt, (unsigned)lb * chunk), hi = min(cnt, lo + chunk);
   unsigned *src = P.ct, *dst = P.ct2;
+  unsigned long long *ks = P.ck, *kd = P.ck2;
   const int wid = threadIdx.x >> 5;
-  for (int field = 0; field < 4; field++) {
-    for (int shift = 0; shift < nbits[field]; shift += 8) {
-      for (int t = threadIdx.x; t < 256; t += kThreads) sm.hist[t] = 0;
-      __syncthreads();
-      for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads)
-        atomicAdd(&sm.hist[(field_key(P, src[p], field, maxg, maxq) >> shift) & 255], 1u);
-      __syncthreads();
-      // digit-major counts: hist[d * nb + block]
-      for (int t = threadIdx.x; t < 256; t += kThreads) P.hist[(size_t)t * nb + lb] = sm.hist[t];
-      if (!grid_sync(bar)) return false;
-      // one warp per digit scans the per-block counts (coalesced, 32 blocks per step)
-      {
-        const int lane = threadIdx.x & 31;
-        for (unsigned d = (unsigned)lb * kWarps + wid; d < 256; d += (unsigned)nb * kWarps) {
-          unsigned long long run = 0;
-          for (int b0 = 0; b0 < nb; b0 += 32) {
-            const int bb = b0 + lane;
-            const unsigned long long h = bb < nb ? P.hist[(size_t)d * nb + bb] : 0;
-            unsigned long long inc = h;
+  if (packed) {
+    for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) {
+      const unsigned idx = src[p];
+      unsigned long long k = (unsigned long long)(unsigned)P.mv_v[idx];
+      if (LQ && nbits[1]) k |= (maxq - (unsigned long long)P.mv_q[idx]) << sq;
+      if (nbits[2]) k |= (maxg - (unsigned long long)P.mv_gain[idx]) << sg;
+      if (nbits[3]) k |= (unsigned long long)(P.mv_t[idx] - P.lbase) << st;
+      ks[p] = k;
+    }
+    __syncthreads();
+  }
+  // passes: packed keys in 8-bit digits; otherwise (field, shift) pairs
+  int field = 0, shift = 0;
+  if (!packed)
+    while (field < 4 && nbits[field] == 0) field++;
+  while (packed ? shift < tbits : field < 4) {
+    auto digit = [&](unsigned p) -> int {
+      return packed ? (int)((ks[p] >> shift) & 255)
+                    : (int)((field_key(P, src[p], field, maxg, maxq) >> shift) & 255);
+    };
+    for (int t = threadIdx.x; t < 256; t += kThreads) sm.hist[t] = 0;
+    __syncthreads();
+    for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) atomicAdd(&sm.hist[digit(p)], 1u);
+    __syncthreads();
+    // digit-major counts: hist[d * nb + block]
+    for (int t = threadIdx.x; t < 256; t += kThreads) P.hist[(size_t)t * nb + lb] = sm.hist[t];
+    if (!grid_sync(bar)) return false;
+    // one warp per digit scans the per-block counts (coalesced, 32 blocks per step)
+    {
+      const int lane = threadIdx.x & 31;
+      for (unsigned d = (unsigned)lb * kWarps + wid; d < 256; d += (unsigned)nb * kWarps) {
+        unsigned long long run = 0;
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+          const int bb = b0 + lane;
+          const unsigned long long h = bb < nb ? P.hist[(size_t)d * nb + bb] : 0;
+          unsigned long long inc = h;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const unsigned long long y = __shfl_up_sync(kFull, inc, o);
-              if (lane >= o) inc += y;
-            }
-            if (bb < nb) P.hoff[(size_t)bb * 256 + d] = run + inc - h;
-            run += __shfl_sync(kFull, inc, 31);
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
           }
-          if (lane == 0) P.hoff[(size_t)nb * 256 + d] = run;
+          if (bb < nb) P.hoff[(size_t)bb * 256 + d] = run + inc - h;
+          run += __shfl_sync(kFull, inc, 31);
         }
+        if (lane == 0) P.hoff[(size_t)nb * 256 + d] = run;
       }
-      if (!grid_sync(bar)) return false;
-      if (threadIdx.x == 0) {
-        unsigned long long acc = 0;
-        for (int t = 0; t < 256; t++) {
-          sm.base[t] = acc + P.hoff[(size_t)lb * 256 + t];
-          acc += P.hoff[(size_t)nb * 256 + t];
-        }
+    }
+    if (!grid_sync(bar)) return false;
+    {
+      // this block's start per digit: digits below (exclusive scan of the totals) + blocks before
+      const int t = threadIdx.x;
+      const long long tot = t < 256 ? (long long)P.hoff[(size_t)nb * 256 + t] : 0;
+      const long long own = t < 256 ? (long long)P.hoff[(size_t)lb * 256 + t] : 0;
+      const long long ex = block_excl_scan64(tot, sm.tmp, (long long *)nullptr);
+      if (t < 256) sm.base[t] = (unsigned long long)(ex + own);
+    }
+    __syncthreads();
+    for (unsigned t0 = lo; t0 < hi; t0 += kThreads) {
+      const unsigned p = t0 + threadIdx.x;
+      const bool valid = p < hi;
+      const unsigned x = valid ? src[p] : 0;
+      const unsigned long long kx = (valid && packed) ? ks[p] : 0;
+      const int dg = valid ? digit(p) : 256;
+      for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) sm.wcnt[k >> 8][k & 255] = 0;
+      __syncthreads();
+      const unsigned peers = __match_any_sync(kFull, dg);
+      const int rank = __popc(peers & lanemask_lt());
+      if (valid && rank == 0) sm.wcnt[wid][dg] = __popc(peers);
+      __syncthreads();
+      if (valid) {
+        unsigned pre = 0;
+        for (int w = 0; w < wid; w++) pre += sm.wcnt[w][dg];
+        const unsigned long long pos = sm.base[dg] + pre + rank;
+        dst[pos] = x;
+        if (packed) kd[pos] = kx;
       }
       __syncthreads();
-      for (unsigned t0 = lo; t0 < hi; t0 += kThreads) {
-        const unsigned p = t0 + threadIdx.x;
-        const bool valid = p < hi;
-        const unsigned x = valid ? src[p] : 0;
-        const int dg = valid ? (int)((field_key(P, x, field, maxg, maxq) >> shift) & 255) : 256;
-        for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) sm.wcnt[k >> 8][k & 255] = 0;
-        __syncthreads();
-        const unsigned peers = __match_any_sync(kFull, dg);
-        const int rank = __popc(peers & lanemask_lt());
-        if (valid && rank == 0) sm.wcnt[wid][dg] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-          unsigned pre = 0;
-          for (int w = 0; w < wid; w++) pre += sm.wcnt[w][dg];
-          dst[sm.base[dg] + pre + rank] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x < 256) {
-          unsigned s = 0;
-          for (int w = 0; w < kWarps; w++) s += sm.wcnt[w][threadIdx.x];
-          sm.base[threadIdx.x] += s;
-        }
-        __syncthreads();
+      if (threadIdx.x < 256) {
+        unsigned s2 = 0;
+        for (int w = 0; w < kWarps; w++) s2 += sm.wcnt[w][threadIdx.x];
+        sm.base[threadIdx.x] += s2;
       }
-      if (!grid_sync(bar)) return false;
-      unsigned *t = src;
-      src = dst;
-      dst = t;
+      __syncthreads();
+    }
+    if (!grid_sync(bar)) return false;
+    unsigned *t = src;
+    src = dst;
+    dst = t;
+    unsigned long long *tk = ks;
+    ks = kd;
+    kd = tk;
+    shift += 8;
+    if (!packed && shift >= nbits[field]) {
+      shift = 0;
+      field++;
+      while (field < 4 && nbits[field] == 0) field++;
     }
   }
   // carries between block slices: per block (sum of the trailing segment, whether the slice has a
@@ -1080,18 +1254,30 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, unsigned
     P.hoff[(size_t)lb * 4 + 3] = (unsigned long long)(hi > lo ? 1 : 0);
   }
   if (!grid_sync(bar)) return false;
-  if (lb == 0 && threadIdx.x == 0) {
-    long long run = 0, run_t = -1;
-    for (int bb = 0; bb < nb; bb++) {
-      P.hoff[(size_t)nb * 4 + bb * 2 + 0] = (unsigned long long)run;
-      P.hoff[(size_t)nb * 4 + bb * 2 + 1] = (unsigned long long)run_t;
-      if (!P.hoff[(size_t)bb * 4 + 3]) continue;
-      const long long t = (long long)P.hoff[(size_t)bb * 4 + 0];
-      const long long lt = (long long)P.hoff[(size_t)bb * 4 + 2];
-      const int hh = (int)P.hoff[(size_t)bb * 4 + 1];
-      if (!hh && lt == run_t) run += t;
-      else run = t;
-      run_t = lt;
+  if (lb == 0) {
+    // stage the per-block summaries in shared memory (coalesced), resolve them in order, write back
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(dsm);  // 4 words per block
+    for (int x = threadIdx.x; x < nb * 4; x += kThreads) stage[x] = P.hoff[x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long run = 0, run_t = -1;
+      for (int bb = 0; bb < nb; bb++) {
+        const long long t = (long long)stage[bb * 4 + 0];
+        const int hh = (int)stage[bb * 4 + 1];
+        const long long lt = (long long)stage[bb * 4 + 2];
+        const bool nonempty = stage[bb * 4 + 3] != 0;
+        stage[bb * 4 + 0] = (unsigned long long)run;  // becomes the carry into block bb
+        stage[bb * 4 + 1] = (unsigned long long)run_t;
+        if (!nonempty) continue;
+        if (!hh && lt == run_t) run += t;
+        else run = t;
+        run_t = lt;
+      }
+    }
+    __syncthreads();
+    for (int bb = threadIdx.x; bb < nb; bb += kThreads) {
+      P.hoff[(size_t)nb * 4 + bb * 2 + 0] = stage[bb * 4 + 0];
+      P.hoff[(size_t)nb * 4 + bb * 2 + 1] = stage[bb * 4 + 1];
     }
   }
   if (!grid_sync(bar)) return false;
@@ -1104,8 +1290,11 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, unsigned
           idx = src[p];
           T = P.mv_t[idx];
         },
-        lo, hi, carry, carry_t, r, sm);
-  if (lb == 0 && threadIdx.x == 0) P.ctr->contest_large += 1;
+        lo, hi, carry, carry_t, r, Cg, sm);
+  if (lb == 0 && threadIdx.x == 0) {
+    P.ctr->contest_large += 1;
+    P.ctr->contest_large_items += cnt;
+  }
   return true;
 }
 
@@ -1143,6 +1332,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       sV.n_movers = vs.n_movers;
       sV.n_contested = vs.n_contested;
       sV.hub_chunks = vs.hub_chunks;
+      sV.n_big = vs.n_big;
+      sV.hub_batches = vs.hub_batches;
       sV.max_gain = vs.max_gain;
       sV.max_q = vs.max_q;
     }
@@ -1150,7 +1341,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   };
   if (threadIdx.x == 0) {
     for (int b = 0; b < 8; b++) sV.bin_count[b] = 0;
-    sV.n_movers = sV.n_contested = sV.hub_chunks = 0;
+    sV.n_movers = sV.n_contested = sV.hub_chunks = sV.n_big = sV.hub_batches = 0;
     sV.max_gain = sV.max_q = 0;
   }
   tick(-1);
@@ -1168,6 +1359,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           Cn.n_movers = 0;
           Cn.n_contested = 0;
           Cn.hub_chunks = 0;
+          Cn.n_big = 0;
+          Cn.hub_batches = 0;
           Cn.max_gain = 0;
           Cn.max_q = 0;
         }
@@ -1182,19 +1375,30 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       unsigned active = 0;
       for (int b = 0; b < kBins; b++) active += sV.bin_count[b];
       if (active > 0) {
-        if (lb == 0 && P.has_hubs && sV.bin_count[6]) hub_prefix(P, C, sV, sm);
+        if (lb == 0 && P.has_hubs && sV.bin_count[6]) {
+          hub_prefix(P, C, sV, sm);
+          tick(7);
+        }
         choose_groups<EW, LQ>(P, sV, lb, nb);
         choose_warp<EW, LQ>(P, sV, lb, nb, dsm);
         choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm);
         if (!grid_sync(bar)) return false;
         tick(1);
         if (P.has_hubs && sV.bin_count[6]) {
-          load_view(C);  // hub_chunks
-          hub_accum<EW, LQ>(P, sV, lb, nb, sm);
+          load_view(C);  // hub batches
+          const unsigned nbat = sV.hub_batches;
+          for (unsigned bt = 0; bt < nbat; bt++) {
+            const unsigned h0 = P.hub_bstart[bt], h1 = P.hub_bstart[bt + 1];
+            hub_accum<EW, LQ>(P, h0, h1, lb, nb, sm, dsm);
+            if (!grid_sync(bar)) return false;
+            tick(2);
+            hub_choose_part<LQ>(P, h0, h1, lb, nb, sm);
+            if (!grid_sync(bar)) return false;
+            hub_choose_final(P, h0, h1, lb, nb);
+            tick(6);
+          }
           if (!grid_sync(bar)) return false;
-          hub_choose<LQ>(P, sV, lb, nb, sm);
-          if (!grid_sync(bar)) return false;
-          tick(2);
+          tick(6);
         }
         if (lb == 0 && threadIdx.x == 0 && s == 0) ctr->moves_round[(r + 1) & 1] = 0;
         phase_admit<LQ>(P, C, sV, r, lb, nb, sm);
@@ -1204,10 +1408,16 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
         const unsigned nc = sV.n_contested;
         if (nc > 0) {
           if (nc <= kContestSmall) {
-            if (lb == 0) contest_small<LQ>(P, sV, nc, r, dsm, sm);
+            if (lb == 0) contest_small<LQ>(P, sV, &C, nc, r, dsm, sm);
           } else {
-            if (!contest_large<LQ>(P, sV, nc, r, lb, nb, bar, sm)) return false;
+            if (!contest_large<LQ>(P, sV, &C, nc, r, lb, nb, bar, sm, dsm)) return false;
           }
+          if (!grid_sync(bar)) return false;
+          load_view(C);  // high-degree movers listed by the contest
+          tick(4);
+        }
+        if (sV.n_big > 0) {
+          mark_big(P, sV.n_big, r, lb, nb);
           if (!grid_sync(bar)) return false;
           tick(4);
         }
@@ -1247,7 +1457,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
 // Degree classes and CSR entries of every job of a launch: counts[9 j + bin] vertices per bin and
 // counts64[j] entries. Vertex x of the concatenation belongs to the job j with pre[j] <= x < pre[j+1].
 __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs, int deg_warp, int deg_cta,
-                                 unsigned *counts, unsigned long long *entries) {
+                                 unsigned *counts, unsigned long long *entries, unsigned long long *hubstat) {
   const int64_t total = pre[njobs];
   const int lane = threadIdx.x & 31;
   for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total; x0 += (int64_t)gridDim.x * blockDim.x) {
@@ -1274,20 +1484,11 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
     unsigned long long dsum = 0;
     for (unsigned m = pj; m; m &= m - 1) dsum += (unsigned long long)__shfl_sync(pj, d, __ffs(m) - 1);
     if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&entries[j], dsum);
-  }
-}
-
-__global__ void k_hub_mark(DGraph g, int deg_cta, int32_t *hub_of, int64_t *hub_cap, unsigned *count) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
-    if (d > deg_cta) {
-      const unsigned h = atomicAdd(count, 1u);
-      hub_of[v] = (int32_t)h;
-      int64_t cap = 64;
-      while (cap < 2 * d) cap <<= 1;
-      hub_cap[h] = cap;
-    } else {
-      hub_of[v] = -1;
+    if (bin == 6) {  // hub: table slots next_pow2(2d); per job the largest table and their sum
+      unsigned long long cap = 64;
+      while (cap < 2ull * (unsigned long long)d) cap <<= 1;
+      atomicMax(&hubstat[2 * j], cap);
+      atomicAdd(&hubstat[2 * j + 1], cap);
     }
   }
 }
@@ -1400,18 +1601,22 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   GP_TRY(ws.get(&pre_dev, (size_t)njobs + 1));
   GP_TRY(ws.zeros(&classes, (size_t)9 * njobs));
   GP_TRY(ws.zeros(&entries, (size_t)njobs));
+  unsigned long long *hubstat;
+  GP_TRY(ws.zeros(&hubstat, (size_t)2 * njobs));
   GP_CUDA(cudaMemcpyAsync(gs_dev, hg.data(), sizeof(DGraph) * njobs, cudaMemcpyHostToDevice, s));
   GP_CUDA(cudaMemcpyAsync(pre_dev, pre.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, s));
   if (pre[njobs] > 0) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((pre[njobs] + 255) / 256, nsm * 8));
     (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, njobs, cfg.deg_warp, cfg.deg_cta,
-                                                                     classes, entries));
+                                                                     classes, entries, hubstat));
     GP_LAUNCH_CHECK();
   }
   std::vector<unsigned> hcls(9 * (size_t)njobs);
   std::vector<unsigned long long> hent(njobs);
   GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaMemcpyAsync(hent.data(), entries, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, s));
+  std::vector<unsigned long long> hhub(2 * (size_t)njobs);
+  GP_CUDA(cudaMemcpyAsync(hhub.data(), hubstat, sizeof(unsigned long long) * hhub.size(), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
   // Blocks: a job gets at most one block per 256 vertices. When all jobs fit the co-resident
   // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
@@ -1420,7 +1625,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   std::vector<int64_t> useful(njobs);
   int64_t sum_useful = 0;
   for (int j = 0; j < njobs; j++) {
-    useful[j] = std::max<int64_t>(1, std::min<int64_t>(cap_blocks, (jobs[j].g.n + 255) / 256));
+    // (the large contest stages 32 bytes per block of a problem in the dynamic shared memory)
+    useful[j] = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(cap_blocks, (int64_t)(kDynSmem / 32)),
+                                                       (jobs[j].g.n + 255) / 256));
     sum_useful += useful[j];
   }
   std::vector<int> nblk(njobs, 1), home(njobs, -1);
@@ -1538,6 +1745,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.demand -= jb.lbase;  // indexed by global label
     GP_TRY(ws.get(&P.ct, n));
     GP_TRY(ws.get(&P.ct2, n));
+    GP_TRY(ws.get(&P.ck, n));
+    GP_TRY(ws.get(&P.ck2, n));
+    GP_TRY(ws.get(&P.big, (size_t)std::max<unsigned>(hcls[9 * j + 5] + hcls[9 * j + 6], 1)));
     GP_TRY(ws.get(&P.act[0], n));
     GP_TRY(ws.get(&P.act[1], n));
     P.act[0] -= jb.vbase;  // indexed by global vertex id
@@ -1548,29 +1758,23 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.bar = bar_all + (size_t)j * kBarrierStride;
     const unsigned nhub = hcls[9 * j + 6];
     if (nhub) {
-      int32_t *hub_of;
-      int64_t *hub_cap, *hub_base, *total;
-      unsigned *hcount;
-      GP_TRY(ws.get(&hub_of, n));
-      GP_TRY(ws.get(&hub_cap, (size_t)nhub + 1));
-      GP_TRY(ws.get(&hub_base, (size_t)nhub + 1));
-      GP_TRY(ws.get(&total, 1));
-      GP_TRY(ws.zeros(&hcount, 1));
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((jb.g.n + 255) / 256, nsm * 8));
-      (::gp::count_launch(), k_hub_mark<<<grid, 256, 0, s>>>(jb.g, cfg.deg_cta, hub_of, hub_cap, hcount));
-      GP_LAUNCH_CHECK();
-      GP_TRY(scan_excl_i64(hub_cap, hub_base, nhub, total, ws));
-      int64_t slots = 0;
-      GP_CUDA(cudaMemcpyAsync(&slots, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      GP_CUDA(cudaStreamSynchronize(s));
+      // tables of one batch of hubs (reused batch after batch), partial choices, per-hub arrays
+      const int64_t max_cap = (int64_t)hhub[2 * j], cap_sum = (int64_t)hhub[2 * j + 1];
+      const int64_t slots = std::min<int64_t>(kHubBatchSlots, cap_sum) + max_cap;
+      // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub
+      const int64_t items = slots / kSlotChunk + (int64_t)nhub + 16;
       GP_TRY(ws.get(&P.hub_keys, (size_t)slots));
-      GP_TRY(ws.zeros(&P.hub_vals, (size_t)slots));
-      GP_TRY(ws.zeros(&P.hub_qv, (size_t)slots));
       GP_CUDA(cudaMemsetAsync(P.hub_keys, 0xff, sizeof(int32_t) * (size_t)slots, s));
+      GP_TRY(ws.zeros(&P.hub_vals, (size_t)slots));
+      if (lq) GP_TRY(ws.zeros(&P.hub_qv, (size_t)slots));
+      GP_TRY(ws.get(&P.hub_part, (size_t)items * sizeof(Best)));
       GP_TRY(ws.get(&P.hub_c0, (size_t)nhub));
       GP_TRY(ws.get(&P.hub_prefix, (size_t)nhub + 1));
-      P.hub_of = hub_of;
-      P.hub_base = hub_base;
+      GP_TRY(ws.get(&P.hub_capx, (size_t)nhub + 1));
+      GP_TRY(ws.get(&P.hub_scx, (size_t)nhub + 1));
+      GP_TRY(ws.get(&P.hub_tb, (size_t)nhub));
+      GP_TRY(ws.get(&P.hub_bstart, (size_t)nhub + 1));
+      GP_TRY(ws.get(&P.hub_bbase, (size_t)nhub + 1));
       P.has_hubs = 1;
     }
   }
@@ -1624,22 +1828,26 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   }
   prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
   if (profiling()) {
-    static const char *names[6] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hubs", "lp_phase_admit",
-                                   "lp_phase_contest", "lp_phase_final"};
-    for (int ph = 0; ph < 6; ph++) {
+    static const char *names[8] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit",
+                                   "lp_phase_contest", "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"};
+    for (int ph = 0; ph < 8; ph++) {
       double ms = 0;
       for (int j = 0; j < njobs; j++) ms += hc[j].phase_ns[ph] * 1e-6;
       prof_add_time(names[ph], ms);
     }
-    double cs = 0, cp = 0, cl = 0;
+    double cs = 0, cp = 0, cl = 0, cli = 0, he = 0, hs = 0;
     for (int j = 0; j < njobs; j++) {
       cs += hc[j].contest_small;
       cp += hc[j].contest_packed;
       cl += hc[j].contest_large;
+      cli += hc[j].contest_large_items;
+      he += hc[j].hub_entries;
+      hs += hc[j].hub_slots;
     }
     prof_add_counts("lp_contest_small_calls", (int64_t)cs, 0, 0);
     prof_add_counts("lp_contest_packed_calls", (int64_t)cp, 0, 0);
-    prof_add_counts("lp_contest_large_calls", (int64_t)cl, 0, 0);
+    prof_add_counts("lp_contest_large_calls", (int64_t)cl, (int64_t)cli, 0);  // edges: contested movers
+    prof_add_counts("lp_hub_work", (int64_t)hs, (int64_t)he, 0);  // items: table slots, edges: entries
   }
   return GP_OK;
 }
