@@ -466,6 +466,7 @@ int partition_batch_device(const gp_batch_item *items, int count, const gp_param
       j.rounds = (int)p.rounds_coarsen;
       j.seed = hash3(items[i].seed, (uint64_t)l, 1);
       j.stats = &stats[i];
+      j.singletons = true;
       jobs.push_back(j);
       job_graph.push_back(i);
     }

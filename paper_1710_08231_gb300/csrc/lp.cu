@@ -81,6 +81,7 @@ struct LpProblem {
   int64_t nl, U;
   uint64_t smix;  // mix64(seed)
   int rounds;
+  int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
   int has_hubs;
   int deg_warp, deg_cta;
   int block_begin, block_count;
@@ -564,7 +565,7 @@ __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals,
 
 // One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
 template <int EW, bool LQ>
-__device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm) {
+__device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, bool direct) {
   const unsigned cnt = V.bin_count[4];
   if (cnt == 0) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -579,6 +580,27 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
   __syncwarp();
   const int32_t *list = P.bin[4];
   const unsigned gw = (unsigned)lb * kWarps + wid, nw = (unsigned)nb * kWarps;
+  if (direct) {
+    // distinct singleton labels: the connection to a label is the weight of its one entry
+    for (unsigned i = gw; i < cnt; i += nw) {
+      const int v = list[i];
+      const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
+      const int L0 = P.labels[P.vbase + v];
+      const long long cv = P.g.vweight(v);
+      Best b = no_best();
+      for (int64_t e = beg + lane; e < end; e += 32) {
+        const Best x = make_cand(P, v, P.labels[__ldg(P.g.adj + e)], L0, load_ew<EW>(P.g.ew, e),
+                                 LQ ? (long long)__ldg(P.q + e) : 0, 0, cv);
+        if (better(x, b)) b = x;
+      }
+      b = group_best<LQ, 32>(b);
+      if (lane == 0) {
+        write_slot(P, P.bin_base[4] + i, v, b, 0);
+        if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
+      }
+    }
+    return;
+  }
   for (unsigned i = gw; i < cnt; i += nw) {
     const int v = list[i];
     const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
@@ -621,7 +643,8 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
 
 // One CTA per vertex (deg_warp < d <= deg_cta), table in shared memory.
 template <int EW, bool LQ>
-__device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, Smem &sm) {
+__device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, Smem &sm,
+                           bool direct) {
   const unsigned cnt = V.bin_count[5];
   if (cnt == 0) return;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm);
@@ -635,6 +658,27 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
   }
   __syncthreads();
   const int32_t *list = P.bin[5];
+  if (direct) {
+    for (unsigned i = lb; i < cnt; i += nb) {
+      const int v = list[i];
+      const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
+      const int L0 = P.labels[P.vbase + v];
+      const long long cv = P.g.vweight(v);
+      Best b = no_best();
+      for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
+        const Best x = make_cand(P, v, P.labels[__ldg(P.g.adj + e)], L0, load_ew<EW>(P.g.ew, e),
+                                 LQ ? (long long)__ldg(P.q + e) : 0, 0, cv);
+        if (better(x, b)) b = x;
+      }
+      b = block_best_of<LQ>(b, sm);
+      if (threadIdx.x == 0) {
+        write_slot(P, P.bin_base[5] + i, v, b, 0);
+        if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (unsigned i = lb; i < cnt; i += nb) {
     const int v = list[i];
     const int64_t beg = P.g.row_begin(v), end = P.g.row_begin(v + 1);
@@ -862,6 +906,43 @@ __device__ void hub_choose_final(const LpProblem &P, unsigned h0, unsigned h1, i
       if (better(part[it - s_lo], b)) b = part[it - s_lo];
     const int v = P.bin[6][i];
     write_slot(P, P.bin_base[6] + i, v, b, P.hub_c0[i]);
+    if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)P.g.vweight(v));
+  }
+}
+
+// Hubs in the first sub-round of a clustering from singletons: every entry is its own candidate, so the rows are
+// scanned in chunks by all blocks (best candidate per chunk) and one thread per hub combines its
+// chunks; no tables.
+template <int EW, bool LQ>
+__device__ void hub_direct_part(const LpProblem &P, unsigned cnt, unsigned chunks, int lb, int nb, Smem &sm) {
+  Best *part = reinterpret_cast<Best *>(P.hub_part);
+  for (unsigned c = lb; c < chunks; c += nb) {
+    const unsigned i = search_prefix(P.hub_prefix, 0, cnt, c);
+    const int v = P.bin[6][i];
+    const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
+    const int64_t end = min(re, beg + kHubChunk);
+    const int L0 = P.labels[P.vbase + v];
+    const long long cv = P.g.vweight(v);
+    Best b = no_best();
+    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
+      const Best x = make_cand(P, v, P.labels[__ldg(P.g.adj + e)], L0, load_ew<EW>(P.g.ew, e),
+                               LQ ? (long long)__ldg(P.q + e) : 0, 0, cv);
+      if (better(x, b)) b = x;
+    }
+    b = block_best_of<LQ>(b, sm);
+    if (threadIdx.x == 0) part[c] = b;
+  }
+}
+
+__device__ void hub_direct_final(const LpProblem &P, unsigned cnt, int lb, int nb) {
+  const Best *part = reinterpret_cast<const Best *>(P.hub_part);
+  for (unsigned i = (unsigned)lb * kThreads + threadIdx.x; i < cnt; i += (unsigned)nb * kThreads) {
+    Best b = no_best();
+    for (unsigned c = P.hub_prefix[i]; c < P.hub_prefix[i + 1]; c++)
+      if (better(part[c], b)) b = part[c];
+    const int v = P.bin[6][i];
+    write_slot(P, P.bin_base[6] + i, v, b, 0);
     if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)P.g.vweight(v));
   }
 }
@@ -1380,11 +1461,21 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           tick(7);
         }
         choose_groups<EW, LQ>(P, sV, lb, nb);
-        choose_warp<EW, LQ>(P, sV, lb, nb, dsm);
-        choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm);
+        // only the first sub-round sees every label as a singleton (the second follows its moves)
+        const bool direct = P.singletons && t == 0;
+        choose_warp<EW, LQ>(P, sV, lb, nb, dsm, direct);
+        choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm, direct);
         if (!grid_sync(bar)) return false;
         tick(1);
-        if (P.has_hubs && sV.bin_count[6]) {
+        if (P.has_hubs && sV.bin_count[6] && direct) {
+          load_view(C);  // hub chunks
+          hub_direct_part<EW, LQ>(P, sV.bin_count[6], sV.hub_chunks, lb, nb, sm);
+          if (!grid_sync(bar)) return false;
+          tick(2);
+          hub_direct_final(P, sV.bin_count[6], lb, nb);
+          if (!grid_sync(bar)) return false;
+          tick(6);
+        } else if (P.has_hubs && sV.bin_count[6]) {
           load_view(C);  // hub batches
           const unsigned nbat = sV.hub_batches;
           for (unsigned bt = 0; bt < nbat; bt++) {
@@ -1720,6 +1811,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.U = jb.U;
     P.smix = mix64(jb.seed);
     P.rounds = jb.g.n > 0 ? jb.rounds : 0;
+    P.singletons = jb.singletons ? 1 : 0;
     P.deg_warp = cfg.deg_warp;
     P.deg_cta = cfg.deg_cta;
     P.labels = jb.labels;
@@ -1761,8 +1853,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       // tables of one batch of hubs (reused batch after batch), partial choices, per-hub arrays
       const int64_t max_cap = (int64_t)hhub[2 * j], cap_sum = (int64_t)hhub[2 * j + 1];
       const int64_t slots = std::min<int64_t>(kHubBatchSlots, cap_sum) + max_cap;
-      // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub
-      const int64_t items = slots / kSlotChunk + (int64_t)nhub + 16;
+      // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub; the
+      // round-0 direct path keeps one item per chunk of every hub row
+      const int64_t items = std::max<int64_t>(slots / kSlotChunk, (int64_t)(hent[j] / kHubChunk)) + (int64_t)nhub + 16;
       GP_TRY(ws.get(&P.hub_keys, (size_t)slots));
       GP_CUDA(cudaMemsetAsync(P.hub_keys, 0xff, sizeof(int32_t) * (size_t)slots, s));
       GP_TRY(ws.zeros(&P.hub_vals, (size_t)slots));
@@ -1853,7 +1946,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
 }
 
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U, int rounds,
-           uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg) {
+           uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg, bool singletons) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (g.n == 0 || rounds <= 0) return GP_OK;
   LpJob j;
@@ -1866,6 +1959,7 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
   j.rounds = rounds;
   j.seed = seed;
   j.stats = stats;
+  j.singletons = singletons;
   return run_lp_multi(&j, 1, s, cfg);
 }
 

@@ -25,6 +25,9 @@ struct LpJob {
   int rounds = 0;
   uint64_t seed = 0;
   gp_lp_stats *stats = nullptr;
+  // labels start as singletons (vertex v in label lbase + v): in the first sub-round every neighbour
+  // label is distinct and no neighbour carries the own label, so connections need no aggregation
+  bool singletons = false;
 };
 
 // Several independent LP runs in one cooperative launch; they must share the edge-weight type and
@@ -37,7 +40,8 @@ LpConfig lp_config_from(const gp_params *p);
 // vertex-weight sums) are device arrays updated in place. q: NULL or per-entry scores.
 // seed is the run's hash seed. stats (host) may be NULL.
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
-           int rounds, uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg);
+           int rounds, uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg,
+           bool singletons = false);
 
 // Block weights of a partition: bw[k] = sum of c(v) over part[v] = b (device). Sets *bad_dev
 // (device int, may be NULL) when a block id is outside [0,k).

@@ -207,7 +207,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
       gp_lp_stats ls;
       GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1),
-                    &ls, s, cfg));
+                    &ls, s, cfg, true));
       lp_edges += ls.edges;
       lp_moves += ls.moves;
       Level lev;
@@ -438,7 +438,7 @@ int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, 
     (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
     GP_LAUNCH_CHECK();
   }
-  GP_TRY(run_lp(g, edge_q, labels_out, lw, g.n, U, rounds, seed, stats, s, schedule_for(nullptr)));
+  GP_TRY(run_lp(g, edge_q, labels_out, lw, g.n, U, rounds, seed, stats, s, schedule_for(nullptr), true));
   GP_TRY(prof_flush(s));
   GP_CUDA(cudaStreamSynchronize(s));
   return GP_OK;
@@ -602,7 +602,7 @@ int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg
         (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
       }
       GP_CUDA(cudaEventRecord(a, s));
-      const int st = run_lp(g, nullptr, labels, lw, g.n, U, 3, 0x5eedULL, nullptr, s, cfg);
+      const int st = run_lp(g, nullptr, labels, lw, g.n, U, 3, 0x5eedULL, nullptr, s, cfg, true);
       GP_CUDA(cudaEventRecord(b, s));
       if (st != GP_OK) {
         cudaEventDestroy(a);
