@@ -22,7 +22,8 @@ namespace gp {
 namespace {
 
 constexpr int kRowSmall = 32;     // <= 32 pairs: one warp, registers
-constexpr int kRowWarp = 256;     // <= 256 pairs: one warp, shared-memory hash
+constexpr int kRowWarp = 256;     // <= 256 pairs: one warp, shared-memory hash of 512 slots
+constexpr int kRowWarpBig = 1024; // <= 1024 pairs: one warp, shared-memory hash of 2048 slots
 constexpr int kRowMedium = 4096;  // <= 4096 pairs: one CTA, shared-memory hash
 constexpr int kRowThreads = 256;
 constexpr int kWarpSlots = 2 * kRowWarp;
@@ -60,16 +61,16 @@ __global__ void k_members(int64_t n, const int32_t *f2c, const int64_t *mstart, 
 }
 
 __global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2, int32_t *l3,
-                               unsigned *counts) {
+                               int32_t *l4, unsigned *counts) {
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = base + threadIdx.x;
     int b = -1;
     if (c < nc) {
       const int64_t D = dsum[c];
-      b = D <= kRowSmall ? 0 : (D <= kRowWarp ? 3 : (D <= kRowMedium ? 1 : 2));
+      b = D <= kRowSmall ? 0 : (D <= kRowWarp ? 3 : (D <= kRowWarpBig ? 4 : (D <= kRowMedium ? 1 : 2)));
     }
-    int32_t *lists[4] = {l0, l1, l2, l3};
-    for (int bb = 0; bb < 4; bb++) {
+    int32_t *lists[5] = {l0, l1, l2, l3, l4};
+    for (int bb = 0; bb < 5; bb++) {
       const unsigned m = __ballot_sync(kFull, b == bb);
       if (!m) continue;
       const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
@@ -170,13 +171,18 @@ __device__ __forceinline__ unsigned row_slot(int cu) { return mix32((unsigned)cu
 
 // Rows with 32 < pairs <= 256: one warp sums the pairs by neighbour id in a shared-memory hash
 // table, compacts the distinct ids and sorts them (bitonic) before writing the row.
-template <int EW>
+// Rows of up to S/2 pairs: one warp per row, an S-slot hash table per warp in shared memory (the
+// CTA's warps are laid out one table after another). The warp walks the concatenated rows of 32
+// members at a time, 64 entries per step (all lanes busy whatever the members' degrees, adjacency
+// read contiguously); equal coarse neighbours of one step are combined in the warp before they touch
+// the table.
+template <int EW, int S>
 __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  long long *vals = reinterpret_cast<long long *>(smem) + wid * kWarpSlots;
-  int *keys = reinterpret_cast<int *>(smem + (kRowThreads / 32) * kWarpSlots * 8) + wid * kWarpSlots;
-  for (int t = lane; t < kWarpSlots; t += 32) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwb = blockDim.x >> 5;
+  long long *vals = reinterpret_cast<long long *>(smem) + wid * S;
+  int *keys = reinterpret_cast<int *>(smem + nwb * S * 8) + wid * S;
+  for (int t = lane; t < S; t += 32) {
     keys[t] = -1;
     vals[t] = 0;
   }
@@ -189,21 +195,62 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
     int cap = 64;
     while (cap < 2 * a.dsum[cv]) cap <<= 1;
     const unsigned mask = (unsigned)cap - 1;
-    for (int64_t m = mb; m < me; m++) {
-      const int v = a.members[m];
-      const int64_t b = a.g.row_begin(v), e = a.g.row_begin(v + 1);
-      for (int64_t x = b + lane; x < e; x += 32) {
-        const int cu = a.f2c[__ldg(a.g.adj + x)];
-        if (cu == cv) continue;
-        const long long w = load_ew<EW>(a.g.ew, x);
-        unsigned sl = row_slot(cu) & mask;
-        while (true) {
-          const int k = atomicCAS(&keys[sl], -1, cu);
-          if (k == -1 || k == cu) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&vals[sl]), (unsigned long long)w);
-            break;
+    for (int64_t m0 = mb; m0 < me; m0 += 32) {
+      // the warp walks the concatenation of the rows of members m0 .. m0+31, 64 entries per step
+      const int64_t m = m0 + lane;
+      int64_t rb = 0, deg = 0;
+      if (m < me) {
+        const int v = a.members[m];
+        rb = a.g.row_begin(v);
+        deg = a.g.row_begin(v + 1) - rb;
+      }
+      int64_t incl = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int64_t excl = incl - deg;
+      const int64_t total = __shfl_sync(kFull, incl, 31);
+      for (int64_t t0 = 0; t0 < total; t0 += 64) {
+        int cu[2];
+        long long w[2];
+        bool on[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int64_t t = t0 + h * 32 + lane;
+          int j = 0;  // owner: the largest lane j with excl_j <= t
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int64_t ex = __shfl_sync(kFull, excl, j + step);
+            if (j + step < 32 && ex <= t) j += step;
           }
-          sl = (sl + 1) & mask;
+          const int64_t x = __shfl_sync(kFull, rb, j) + (t - __shfl_sync(kFull, excl, j));
+          on[h] = t < total;
+          cu[h] = on[h] ? a.f2c[__ldg(a.g.adj + x)] : -1;
+          w[h] = on[h] ? load_ew<EW>(a.g.ew, x) : 0;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const bool ok = on[h] && cu[h] != cv;
+          const unsigned peers = __match_any_sync(kFull, ok ? cu[h] : -1);
+          if (!ok) continue;
+          long long sum = 0;
+          if constexpr (EW == 0) {
+            sum = __popc(peers);
+          } else {
+            for (unsigned pm = peers; pm; pm &= pm - 1) sum += __shfl_sync(peers, w[h], __ffs(pm) - 1);
+          }
+          if (lane != __ffs(peers) - 1) continue;
+          unsigned sl = row_slot(cu[h]) & mask;
+          while (true) {
+            const int k = atomicCAS(&keys[sl], -1, cu[h]);
+            if (k == -1 || k == cu[h]) {
+              atomicAdd(reinterpret_cast<unsigned long long *>(&vals[sl]), (unsigned long long)sum);
+              break;
+            }
+            sl = (sl + 1) & mask;
+          }
         }
       }
     }
@@ -445,7 +492,7 @@ void set_smem(K kernel, int bytes) {
 }
 
 template <int EW>
-int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[4], int32_t *lists[4], cudaStream_t s) {
+int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[5], int32_t *lists[5], cudaStream_t s) {
   const int nsm = num_sms();
   auto grid_for = [&](int64_t items, int per_block, int limit) {
     int64_t g = (items + per_block - 1) / per_block;
@@ -463,8 +510,17 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[4], 
     b.list = lists[3];
     b.count = counts_dev + 3;
     const int sm = (kRowThreads / 32) * kWarpSlots * 12;
-    set_smem(k_row_whash<EW>, sm);
-    (::gp::count_launch(), k_row_whash<EW><<<grid_for(counts[3], 8, nsm * 4), kRowThreads, sm, s>>>(b));
+    set_smem(k_row_whash<EW, kWarpSlots>, sm);
+    (::gp::count_launch(), k_row_whash<EW, kWarpSlots><<<grid_for(counts[3], 8, nsm * 4), kRowThreads, sm, s>>>(b));
+  }
+  if (counts[4]) {
+    RowArgs b = a;
+    b.list = lists[4];
+    b.count = counts_dev + 4;
+    constexpr int kBigSlots = 2 * kRowWarpBig;
+    const int sm = 4 * kBigSlots * 12;  // 4 warps per CTA
+    set_smem(k_row_whash<EW, kBigSlots>, sm);
+    (::gp::count_launch(), k_row_whash<EW, kBigSlots><<<grid_for(counts[4], 4, nsm * 2), 128, sm, s>>>(b));
   }
   if (counts[1]) {
     RowArgs b = a;
@@ -554,13 +610,14 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_TRY(ws.get(&members, (size_t)n));
   (::gp::count_launch(), k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members));
   // 4. rows binned by pair count
-  int32_t *lists[4];
+  int32_t *lists[5];
   unsigned *counts_dev;
-  for (int b = 0; b < 4; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
-  GP_TRY(ws.zeros(&counts_dev, 4));
-  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], lists[3], counts_dev));
+  for (int b = 0; b < 5; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
+  GP_TRY(ws.zeros(&counts_dev, 5));
+  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], lists[3],
+                                                                    lists[4], counts_dev));
   GP_LAUNCH_CHECK();
-  unsigned counts[4];
+  unsigned counts[5];
   GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
   RowArgs a;

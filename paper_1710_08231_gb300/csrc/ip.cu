@@ -385,32 +385,26 @@ __global__ void k_deg_flags(DGraph g, uint32_t *keep, int64_t *deg0) {
   }
 }
 
-__global__ void k_strip_rows(DGraph g, const int32_t *rank, const uint32_t *keep, int64_t *deg_kept) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
-    if (keep[v]) deg_kept[rank[v]] = g.row_begin(v + 1) - g.row_begin(v);
-}
-
-__global__ void k_strip_copy(DGraph g, const int32_t *rank, const uint32_t *keep, const int64_t *off0,
-                             int32_t *adj0, void *vw0, void *ew0) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = gw; v < g.n; v += nw) {
+// Degree-0 vertices own no CSR entries, so the kept vertices' rows keep their entries in the same
+// order: the stripped offsets are the kept vertices' offsets, the stripped adjacency is the renamed
+// adjacency and the edge weights are unchanged.
+__global__ void k_strip_rows(DGraph g, const int32_t *rank, const uint32_t *keep, int64_t n0, int64_t *off0,
+                             void *vw0) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
     if (!keep[v]) continue;
     const int r = rank[v];
-    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1), dst = off0[r];
-    if (lane == 0 && vw0) {
+    off0[r] = g.row_begin(v);
+    if (vw0) {
       if (g.vw64) static_cast<int64_t *>(vw0)[r] = static_cast<const int64_t *>(g.vw)[v];
       else static_cast<int32_t *>(vw0)[r] = static_cast<const int32_t *>(g.vw)[v];
     }
-    for (int64_t j = b + lane; j < e; j += 32) {
-      adj0[dst + (j - b)] = rank[g.adj[j]];
-      if (ew0) {
-        if (g.ew64) static_cast<int64_t *>(ew0)[dst + (j - b)] = static_cast<const int64_t *>(g.ew)[j];
-        else static_cast<int32_t *>(ew0)[dst + (j - b)] = static_cast<const int32_t *>(g.ew)[j];
-      }
-    }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) off0[n0] = g.row_begin(g.n);
+}
+
+__global__ void k_strip_adj(const int32_t *adj, int64_t m, const int32_t *rank, int32_t *adj0) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+    adj0[j] = rank[adj[j]];
 }
 
 // Degree-0 vertex placement with unit weights, closed form of the greedy rule: at water level x
@@ -640,39 +634,25 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
   out->n0 = n0;
   out->n_iso = g.n - n0;
   out->rank = rank;
-  // rank of kept vertices = exclusive count of kept before v; mark degree-0 ones with -1 later
-  int64_t *deg0, *off0;
-  GP_TRY(ws.get(&deg0, (size_t)std::max<int64_t>(n0, 1)));
+  // rank of kept vertices = exclusive count of kept before v; degree-0 ones are marked -1 later
+  int64_t *off0;
   GP_TRY(ws.get(&off0, (size_t)n0 + 1));
-  (::gp::count_launch(), k_strip_rows<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, keep, deg0));
-  GP_LAUNCH_CHECK();
-  GP_TRY(scan_excl_i64(deg0, off0, n0, off0 + n0, ws));
-  int32_t *adj0;
-  void *vw0 = nullptr, *ew0 = nullptr;
-  GP_TRY(ws.get(&adj0, (size_t)std::max<int64_t>(g.m, 1)));
+  void *vw0 = nullptr;
   if (g.vw) {
     if (g.vw64) {
       int64_t *p;
-      GP_TRY(ws.get(&p, (size_t)n0));
+      GP_TRY(ws.get(&p, (size_t)std::max<int64_t>(n0, 1)));
       vw0 = p;
     } else {
       int32_t *p;
-      GP_TRY(ws.get(&p, (size_t)n0));
+      GP_TRY(ws.get(&p, (size_t)std::max<int64_t>(n0, 1)));
       vw0 = p;
     }
   }
-  if (g.ew) {
-    if (g.ew64) {
-      int64_t *p;
-      GP_TRY(ws.get(&p, (size_t)g.m));
-      ew0 = p;
-    } else {
-      int32_t *p;
-      GP_TRY(ws.get(&p, (size_t)g.m));
-      ew0 = p;
-    }
-  }
-  (::gp::count_launch(), k_strip_copy<<<grid_for_n(g.n * 32), 256, 0, s>>>(g, rank, keep, off0, adj0, vw0, ew0));
+  int32_t *adj0;
+  GP_TRY(ws.get(&adj0, (size_t)std::max<int64_t>(g.m, 1)));
+  (::gp::count_launch(), k_strip_rows<<<grid_for_n(g.n), 256, 0, s>>>(g, rank, keep, n0, off0, vw0));
+  if (g.m > 0) (::gp::count_launch(), k_strip_adj<<<grid_for_n(g.m), 256, 0, s>>>(g.adj, g.m, rank, adj0));
   GP_LAUNCH_CHECK();
   DGraph d;
   d.n = n0;
@@ -682,7 +662,7 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
   d.adj = adj0;
   d.vw = vw0;
   d.vw64 = g.vw64;
-  d.ew = ew0;
+  d.ew = g.ew;  // same entries in the same order
   d.ew64 = g.ew64;
   out->g0 = d;
   return GP_OK;

@@ -385,6 +385,76 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
   const int64_t chunk = (n + nb - 1) / nb;
   const int64_t lo = min(n, (int64_t)lb * chunk), hi = min(n, lo + chunk);
   const int lane = threadIdx.x & 31;
+  constexpr int kCls = 8;
+  if (hi - lo <= (int64_t)kCls * kThreads) {
+    // chunks of up to kCls vertices per thread: all flag loads first, then the offsets of the active
+    // ones, then the per-bin aggregation; the bins stay in a register (4 bits per vertex) for pass 2
+    const int niter = (int)((hi - lo + kThreads - 1) / kThreads);
+    unsigned flag = 0;
+#pragma unroll
+    for (int it = 0; it < kCls; it++) {
+      const int64_t v = lo + (int64_t)it * kThreads + threadIdx.x;
+      if (it < niter && v < hi && (r == 0 || act[P.vbase + v])) flag |= 1u << it;
+    }
+    if (s == 0) {
+#pragma unroll
+      for (int it = 0; it < kCls; it++) {
+        const int64_t v = lo + (int64_t)it * kThreads + threadIdx.x;
+        if (it < niter && v < hi) act_next[P.vbase + v] = 0;  // the marks of round r go there
+      }
+    }
+    int dd[kCls];
+#pragma unroll
+    for (int it = 0; it < kCls; it++) {
+      const int64_t v = lo + (int64_t)it * kThreads + threadIdx.x;
+      dd[it] = 0;
+      if ((flag >> it & 1) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == s) {
+        dd[it] = (int)(P.g.row_begin(v + 1) - P.g.row_begin(v));
+      } else {
+        flag &= ~(1u << it);
+      }
+    }
+    unsigned codes = 0xffffffffu;
+#pragma unroll
+    for (int it = 0; it < kCls; it++) {
+      if (it >= niter) break;
+      int b = -1;
+      if (flag >> it & 1) b = dd[it] == 0 ? kBinZero : bin_of(dd[it], P.deg_warp, P.deg_cta);
+      if (b >= 0) codes = (codes & ~(15u << (4 * it))) | ((unsigned)b << (4 * it));
+      const unsigned peers = __match_any_sync(kFull, b);
+      if (b >= 0 && lane == __ffs(peers) - 1) {
+        atomicAdd(&sm.vis[b], (unsigned long long)__popc(peers));
+        if (b < kBins) atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+      }
+      if (b >= 0 && dd[it]) atomicAdd(&sm.edg[b], (unsigned long long)dd[it]);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+      s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&C.bin_count[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+      s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kCls; it++) {
+      if (it >= niter) break;
+      const int64_t v = lo + (int64_t)it * kThreads + threadIdx.x;
+      const int c = (int)(codes >> (4 * it) & 15u);
+      const int b = c == 15 ? -1 : c;
+      const bool put = b >= 0 && b < kBins;
+      const unsigned peers = __match_any_sync(kFull, put ? b : -1);
+      const int leader = __ffs(peers) - 1;
+      unsigned pos = 0;
+      if (put && lane == leader) pos = atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+      pos = __shfl_sync(kFull, pos, leader);
+      if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      if (sm.vis[threadIdx.x]) atomicAdd(&P.ctr->bin_visits[threadIdx.x], sm.vis[threadIdx.x]);
+      if (sm.edg[threadIdx.x]) atomicAdd(&P.ctr->bin_edges[threadIdx.x], sm.edg[threadIdx.x]);
+    }
+    return;
+  }
   // pass 1: counts
   for (int64_t v0 = lo; v0 < hi; v0 += kThreads) {
     const int64_t v = v0 + threadIdx.x;
@@ -1394,13 +1464,16 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   const int lb = (int)blockIdx.x - P.block_begin, nb = P.block_count;
   LpCounters *ctr = P.ctr;
   const GridBarrier bar{P.bar, &ctr->bar_gen, &ctr->err, (unsigned)nb, (unsigned)lb};
-  // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there)
+  // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there) in
+  // shared memory and writes the totals once at the end
+  __shared__ unsigned long long pacc[8];
+  if (threadIdx.x < 8) pacc[threadIdx.x] = 0;
   unsigned long long tmark = 0;
   auto tick = [&](int phase) {
     if (lb == 0 && threadIdx.x == 0) {
       unsigned long long now;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-      if (phase >= 0) ctr->phase_ns[phase] += now - tmark;
+      if (phase >= 0) pacc[phase] += now - tmark;
       tmark = now;
     }
   };
@@ -1531,6 +1604,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   // label weights of the last sub-round's moves (every block has passed its final barrier)
   if (t_last >= 0) settle_moves(P, sV, lb, nb);
   tick(5);
+  if (lb == 0 && threadIdx.x == 0)
+    for (int k = 0; k < 8; k++) ctr->phase_ns[k] = pacc[k];
   return true;
 }
 
