@@ -227,6 +227,13 @@ __device__ __forceinline__ void write_slot(const LpProblem &P, int64_t idx, int 
 
 __device__ __forceinline__ unsigned slot_hash(int L) { return mix32((unsigned)L); }
 
+// Hub tables: round_up(2 d, 64) slots (a hub row has at most d distinct labels, so the load stays at
+// or below 1/2), indexed by a multiply-shift range reduction of the mixed label.
+__host__ __device__ __forceinline__ int64_t hub_cap(int64_t d) { return ((2 * d + 63) / 64) * 64; }
+__device__ __forceinline__ uint64_t hub_slot(int L, uint64_t cap) {
+  return ((uint64_t)slot_hash(L) * cap) >> 32;
+}
+
 struct Smem {
   Best best[kWarps];
   long long sum[kWarps];
@@ -789,7 +796,7 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
 }
 
 // Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (kHubChunk
-// entries), table slots (next_pow2(2d) each) and choice items (kSlotChunk slots); cut into batches of
+// entries), table slots (hub_cap(d) each) and choice items (kSlotChunk slots); cut into batches of
 // about kHubBatchSlots slots (a hub starts a new batch when its slot prefix crosses a multiple of
 // kHubBatchSlots); table base of each hub inside its batch.
 __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm) {
@@ -809,8 +816,7 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     if (valid) {
       const int v = P.bin[6][i];
       d = P.g.row_begin(v + 1) - P.g.row_begin(v);
-      cap = 64;
-      while (cap < 2 * d) cap <<= 1;
+      cap = hub_cap(d);
       ch = (d + kHubChunk - 1) / kHubChunk;
       sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
@@ -900,23 +906,38 @@ __device__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, 
     const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
     const int64_t end = min(re, beg + kHubChunk);
     const int64_t tb = P.hub_tb[i];
-    const uint64_t mask = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]) - 1;
+    const uint64_t cap = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]);
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    for (int64_t e0 = beg + (threadIdx.x & ~31); e0 < end; e0 += kThreads) {
-      const int64_t e = e0 + (threadIdx.x & 31);
-      const bool in = e < end;
-      const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
-      const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
-      if (in && L == L0) c0 += w;
-      warp_insert<EW, LQ>(skeys, svals, sq, kCtaCap - 1, in && L != L0, L, w,
-                          (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
+    // a chunk is at most kHubChunk = 4 * kThreads entries: each thread takes four, loads first
+    static_assert(kHubChunk == 4 * kThreads, "one step of four entries per thread covers a chunk");
+    {
+      int64_t e[4];
+      int L[4];
+      long long w[4];
+      unsigned q4[4];
+      bool in[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        e[u] = beg + u * kThreads + threadIdx.x;
+        in[u] = e[u] < end;
+        L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
+        w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
+        q4[u] = (LQ && in[u]) ? (unsigned)__ldg(P.q + e[u]) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) L[u] = in[u] ? P.labels[L[u]] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (in[u] && L[u] == L0) c0 += w[u];
+        warp_insert<EW, LQ>(skeys, svals, sq, kCtaCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u]);
+      }
     }
     c0 = block_sum_of(c0, sm);  // also completes the shared table
     for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
       const int L = skeys[t];
       if (L < 0) continue;
-      uint64_t sg = (uint64_t)slot_hash(L) & mask;
+      uint64_t sg = hub_slot(L, cap);
       while (true) {
         const int k = atomicCAS(&P.hub_keys[tb + sg], -1, L);
         if (k == -1 || k == L) {
@@ -924,7 +945,7 @@ __device__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, 
           if (LQ) atomicAdd(&P.hub_qv[tb + sg], sq[t]);
           break;
         }
-        sg = (sg + 1) & mask;
+        sg = sg + 1 == cap ? 0 : sg + 1;
       }
       skeys[t] = -1;
       svals[t] = 0;
@@ -1650,9 +1671,8 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
     unsigned long long dsum = 0;
     for (unsigned m = pj; m; m &= m - 1) dsum += (unsigned long long)__shfl_sync(pj, d, __ffs(m) - 1);
     if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&entries[j], dsum);
-    if (bin == 6) {  // hub: table slots next_pow2(2d); per job the largest table and their sum
-      unsigned long long cap = 64;
-      while (cap < 2ull * (unsigned long long)d) cap <<= 1;
+    if (bin == 6) {  // hub: table slots hub_cap(d); per job the largest table and their sum
+      const unsigned long long cap = (unsigned long long)hub_cap(d);
       atomicMax(&hubstat[2 * j], cap);
       atomicAdd(&hubstat[2 * j + 1], cap);
     }
