@@ -60,6 +60,14 @@ __global__ void k_members(int64_t n, const int32_t *f2c, const int64_t *mstart, 
   }
 }
 
+__global__ void k_max_i64(const int64_t *x, int64_t n, unsigned long long *out) {
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)x[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2, int32_t *l3,
                                int32_t *l4, unsigned *counts) {
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
@@ -234,10 +242,14 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
         for (int h = 0; h < 2; h++) {
           const bool ok = on[h] && cu[h] != cv;
           const unsigned peers = __match_any_sync(kFull, ok ? cu[h] : -1);
+          // weights below 2^26 sum exactly in 32 bits over at most 32 lanes: one warp reduction
+          const bool wide = EW != 0 && __any_sync(kFull, ok && (w[h] >= (1ll << 26) || w[h] < 0));
           if (!ok) continue;
           long long sum = 0;
           if constexpr (EW == 0) {
             sum = __popc(peers);
+          } else if (!wide) {
+            sum = (long long)__reduce_add_sync(peers, (unsigned)w[h]);
           } else {
             for (unsigned pm = peers; pm; pm &= pm - 1) sum += __shfl_sync(peers, w[h], __ffs(pm) - 1);
           }
@@ -617,8 +629,13 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], lists[3],
                                                                     lists[4], counts_dev));
   GP_LAUNCH_CHECK();
+  unsigned long long *maxvw_dev;
+  GP_TRY(ws.zeros(&maxvw_dev, 1));
+  (::gp::count_launch(), k_max_i64<<<grid_n(nc), 256, 0, s>>>(cw, nc, maxvw_dev));
   unsigned counts[5];
+  unsigned long long maxvw = 0;
   GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaMemcpyAsync(&maxvw, maxvw_dev, sizeof(maxvw), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
   RowArgs a;
   a.g = g;
@@ -690,6 +707,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_CUDA(cudaMemcpyAsync(&mc, off_tmp + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
   GP_TRY(alloc_graph(out, nc, mc, s));
+  out->max_vw = (int64_t)maxvw;
   GP_CUDA(cudaMemcpyAsync(out->off, off_tmp, sizeof(int64_t) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
   GP_CUDA(cudaMemcpyAsync(out->vw, cw, sizeof(int64_t) * (size_t)nc, cudaMemcpyDeviceToDevice, s));
   {
@@ -702,8 +720,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
     prof_add_counts("contract_rows", nc, g.m, rb);
     prof_add_counts("contract_compact", nc, mc, mc * 12 + nc * 8);
   }
-  GP_CUDA(cudaStreamSynchronize(s));
-  return GP_OK;
+  return GP_OK;  // stream-ordered: the temporary buffers are released on s after the kernels
 }
 
 }  // namespace gp

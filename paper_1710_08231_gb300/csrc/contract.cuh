@@ -8,6 +8,7 @@ namespace gp {
 // A device-resident coarse graph: int64 offsets, int32 adjacency, int64 vertex and edge weights.
 struct OwnedGraph {
   int64_t n = 0, m = 0;
+  int64_t max_vw = 0;  // largest vertex weight (filled by contract_graph)
   int64_t *off = nullptr;
   int32_t *adj = nullptr;
   int64_t *vw = nullptr;

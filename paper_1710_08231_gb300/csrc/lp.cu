@@ -617,10 +617,14 @@ template <int EW, bool LQ>
 __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals, unsigned *qv, unsigned mask, bool on,
                                             int L, long long w, unsigned q) {
   const unsigned peers = __match_any_sync(kFull, on ? L : -1);
+  // weights below 2^26 sum exactly in 32 bits over at most 32 lanes: one warp reduction
+  const bool wide = EW != 0 && __any_sync(kFull, on && (w >= (1ll << 26) || w < 0));
   if (!on) return;
   long long sum;
   if constexpr (EW == 0) {
     sum = __popc(peers);
+  } else if (!wide) {
+    sum = (long long)__reduce_add_sync(peers, (unsigned)w);
   } else {
     sum = 0;
     for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, w, __ffs(m) - 1);

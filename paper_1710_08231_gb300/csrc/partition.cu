@@ -76,6 +76,22 @@ __global__ void k_validate(DGraph g, int *err) {
   }
 }
 
+// Doubled cut of every try partition (parts: tries * n): cut2[t] += weight of each entry whose ends
+// lie in different blocks of try t.
+__global__ void k_tries_cut(DGraph g, const int32_t *parts, int tries, unsigned long long *cut2) {
+  for (int t = 0; t < tries; t++) {
+    const int32_t *p = parts + (size_t)t * g.n;
+    unsigned long long c = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+      const int pv = p[v];
+      for (int64_t j = g.row_begin(v); j < g.row_begin(v + 1); j++)
+        if (p[g.adj[j]] != pv) c += (unsigned long long)g.eweight(j);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cut2[t], c);
+  }
+}
+
 gp_params g_schedule = {};
 
 LpConfig schedule_for(const gp_params *p) {
@@ -199,7 +215,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       const int l = (int)f2c.size();
       const DGraph &gl = G.back();
       int64_t maxc = 0;
-      GP_TRY(vertex_weight_stats(gl, &maxc, nullptr, s));
+      if (l == 0) GP_TRY(vertex_weight_stats(gl, &maxc, nullptr, s));
+      else maxc = H.levels.back().g.max_vw;  // reported by the contraction that built this level
       const int64_t U = std::max<int64_t>(maxc, lmax / p.cluster_div);
       (::gp::count_launch(), k_iota<<<grid_n(gl.n), 256, 0, s>>>(labels, gl.n));
       (::gp::count_launch(), k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw));
@@ -238,7 +255,6 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     GP_TRY(initial_partition(gc, k, lmax, seed, levels, tries, (int)p.repair_rounds, parts, s));
     int best = -1;
     int64_t best_cut = 0, best_imb = 0;
-    std::vector<int64_t> hbw(k);
     // the tries' LP refinements run as independent problems of one launch
     int64_t *bws;
     GP_TRY(ws.get(&bws, (size_t)tries * k));
@@ -258,15 +274,26 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       jobs[t].stats = &tstats[t];
     }
     if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg));
+    // cuts of all tries in one pass; their block weights are the label weights the refinement kept
+    std::vector<unsigned long long> hcut2(tries);
+    std::vector<int64_t> hbws((size_t)tries * k);
+    {
+      unsigned long long *cut2;
+      GP_TRY(ws.zeros(&cut2, (size_t)tries));
+      if (gc.n > 0) {
+        (::gp::count_launch(), k_tries_cut<<<grid_n(gc.n), 256, 0, s>>>(gc, parts, tries, cut2));
+        GP_LAUNCH_CHECK();
+      }
+      GP_CUDA(cudaMemcpyAsync(hcut2.data(), cut2, sizeof(unsigned long long) * tries, cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaMemcpyAsync(hbws.data(), bws, sizeof(int64_t) * (size_t)tries * k, cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+    }
     for (int t = 0; t < tries; t++) {
-      int32_t *pt = parts + (size_t)t * gc.n;
       lp_edges += tstats[t].edges;
       lp_moves += tstats[t].moves;
-      int64_t cut = 0;
-      GP_TRY(eval_cut(gc, pt, k, &cut, bw, s));
-      GP_CUDA(cudaMemcpyAsync(hbw.data(), bw, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, s));
-      GP_CUDA(cudaStreamSynchronize(s));
-      const int64_t imb = *std::max_element(hbw.begin(), hbw.end()) > lmax ? 1 : 0;
+      const int64_t cut = (int64_t)(hcut2[t] / 2);
+      const int64_t imb =
+          *std::max_element(hbws.begin() + (size_t)t * k, hbws.begin() + (size_t)(t + 1) * k) > lmax ? 1 : 0;
       res->try_cut[t] = cut;
       res->try_imbalanced[t] = imb;
       if (best < 0 || cut < best_cut || (cut == best_cut && imb < best_imb)) {
