@@ -42,7 +42,8 @@ constexpr int kHubChunk = 1024; // CSR entries per hub work item (pre-aggregated
 constexpr int64_t kHubBatchSlots = int64_t(1) << 22;  // hub table slots per batch (tables stay in L2)
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
-constexpr int64_t kBigDeg = 2048;  // movers above this degree mark their neighbours with every block
+constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
+constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
 constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
 static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
@@ -52,7 +53,7 @@ struct SubCounters {
   unsigned int n_movers;
   unsigned int n_contested;
   unsigned int hub_chunks;
-  unsigned int n_big;  // admitted movers of degree > kBigDeg (their neighbours are marked by all blocks)
+  unsigned int n_big;  // marking items of admitted movers of degree > kBigDeg (done by all blocks)
   unsigned int hub_batches;
   unsigned int pad;
   unsigned long long max_gain, max_q;
@@ -99,7 +100,8 @@ struct LpProblem {
   int64_t *demand;
   uint32_t *ct, *ct2;
   unsigned long long *ck, *ck2;  // packed contest keys (large contests)
-  int32_t *big;                  // admitted movers of degree > kBigDeg in the current sub-round
+  unsigned long long *big;       // marking items of the sub-round's admitted movers of degree > kBigDeg:
+                                 // (vertex << 32) | item, one item per kBigChunk entries of its row
   // hubs (bin 6), per position i of the sub-round's hub list: own-label connection, prefixes of
   // chunks, table slots and choice items, table base inside its batch; first position of each batch
   long long *hub_c0;
@@ -292,10 +294,22 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters
   const unsigned am = __ballot_sync(kFull, adm);
   if (!am) return 0;
   const bool big = adm && deg > kBigDeg;
-  const unsigned pos = warp_append(&C.n_big, big);
-  if (big) {
-    P.big[pos] = v;
-    deg = 0;
+  if (__any_sync(kFull, big)) {
+    // one marking item per kBigChunk entries; the warp reserves all of its items with one atomic
+    const unsigned nit = big ? (unsigned)((deg + kBigChunk - 1) / kBigChunk) : 0u;
+    unsigned ex = nit;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, ex, o);
+      if (lane >= o) ex += y;
+    }
+    const unsigned tot = __shfl_sync(kFull, ex, 31);
+    ex -= nit;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&C.n_big, tot);
+    base = __shfl_sync(kFull, base, 0);
+    for (unsigned x = 0; x < nit; x++) P.big[base + ex + x] = ((unsigned long long)(unsigned)v << 32) | x;
+    if (big) deg = 0;
   }
   // mark the neighbours of the other admitted movers: the warp walks the concatenation of their rows
   int64_t incl = deg;
@@ -321,14 +335,16 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters
   return (unsigned)__popc(am);
 }
 
-// Neighbours of the listed high-degree movers, marked by all blocks of the problem together.
-__device__ void mark_big(const LpProblem &P, unsigned nbig, int r, int lb, int nb) {
+// Neighbours of the high-degree movers: every block takes marking items (kBigChunk entries of one
+// mover's row) in turn.
+__device__ void mark_big(const LpProblem &P, unsigned nitems, int r, int lb, int nb) {
   uint8_t *act_next = P.act[(r + 1) & 1];
-  for (unsigned i = 0; i < nbig; i++) {
-    const int v = P.big[i];
+  for (unsigned i = lb; i < nitems; i += nb) {
+    const unsigned long long it = P.big[i];
+    const int v = (int)(it >> 32);
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-    for (int64_t e = rb + (int64_t)lb * kThreads + threadIdx.x; e < re; e += (int64_t)nb * kThreads)
-      act_next[__ldg(P.g.adj + e)] = 1;
+    const int64_t beg = rb + (int64_t)(unsigned)(it & 0xffffffffu) * kBigChunk, end = min(re, beg + kBigChunk);
+    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) act_next[__ldg(P.g.adj + e)] = 1;
   }
 }
 
@@ -1938,7 +1954,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.ct2, n));
     GP_TRY(ws.get(&P.ck, n));
     GP_TRY(ws.get(&P.ck2, n));
-    GP_TRY(ws.get(&P.big, (size_t)std::max<unsigned>(hcls[9 * j + 5] + hcls[9 * j + 6], 1)));
+    // marking items: at most one per kBigChunk entries of every row plus one per high-degree vertex
+    GP_TRY(ws.get(&P.big, (size_t)(hent[j] / kBigChunk + hcls[9 * j + 5] + hcls[9 * j + 6] + 1)));
     GP_TRY(ws.get(&P.act[0], n));
     GP_TRY(ws.get(&P.act[1], n));
     P.act[0] -= jb.vbase;  // indexed by global vertex id
