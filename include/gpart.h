@@ -172,7 +172,7 @@ int64_t gp_lmax(int64_t total_weight, int64_t k, double eps);
  *   rounds    : >= 0
  *   seed      : hash seed of this run (the partitioner passes H(seed, level, 1))
  *   edge_q    : NULL, or m_dir int32 per-entry scores (learned tie-break; symmetric)
- *   labels_out: n int32, caller-allocated; receives C[v] in [0, n)
+ *   labels_out: n int32, caller-allocated; receives C[v] in [0, n) (may be NULL when n = 0)
  *   stats     : NULL or host struct receiving counters
  * Degree bins (thread group, warp, CTA or multi-CTA per vertex) change the schedule only. */
 int gp_lp_cluster(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
@@ -205,7 +205,7 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta);
 
 /* LP refinement of a k-way partition (Section III-C, Section IV-C): the same rounds with labels
  * = blocks 0..k-1 and U = lmax.
- *   part_inout : n int32 block ids in [0,k) (device), improved in place
+ *   part_inout : n int32 block ids in [0,k) (device), improved in place (may be NULL when n = 0)
  *   block_w_out: NULL or k int64 (device) receiving the final block weights
  * Returns GP_ERR_INVALID_ARG when a block id is out of range. */
 int gp_lp_refine(const gp_graph *g, int32_t k, int64_t lmax, int32_t rounds, uint64_t seed,
@@ -215,7 +215,7 @@ int gp_lp_refine(const gp_graph *g, int32_t k, int64_t lmax, int32_t rounds, uin
  * are renumbered by their rank among the used ids (prefix sum over a used-flag array), the coarse
  * vertex weight is the cluster weight, and the coarse edge (a,b), a != b, weighs the total weight
  * of fine edges between clusters a and b. Rows of the coarse CSR are sorted by neighbour id.
- *   labels : n int32 in [0, n) (device)
+ *   labels : n int32 in [0, n) (device; may be NULL when n = 0)
  *   coarse : receives a library-owned coarse graph (int64 offsets, int64 vertex and edge weights);
  *            release it with gp_coarse_free
  *   f2c_out: NULL or n int32 (device) receiving the coarse id of every fine vertex */

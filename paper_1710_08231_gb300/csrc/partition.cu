@@ -445,7 +445,7 @@ int gp_validate_graph(const gp_graph *gd, gp_stream stream) {
 int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, const int32_t *edge_q,
                   int32_t *labels_out, gp_lp_stats *stats, gp_stream stream) {
   GP_TRY(check_graph_desc(gd));
-  if (!labels_out || rounds < 0 || U < 1) {
+  if ((!labels_out && gd->n > 0) || rounds < 0 || U < 1) {
     set_error("gp_lp_cluster: labels_out, rounds or U out of range");
     return GP_ERR_INVALID_ARG;
   }
@@ -474,7 +474,7 @@ int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, 
 int gp_lp_refine(const gp_graph *gd, int32_t k, int64_t lmax, int32_t rounds, uint64_t seed, int32_t *part,
                  int64_t *block_w_out, gp_lp_stats *stats, gp_stream stream) {
   GP_TRY(check_graph_desc(gd));
-  if (!part || k < 1 || rounds < 0 || lmax < 0) {
+  if ((!part && gd->n > 0) || k < 1 || rounds < 0 || lmax < 0) {
     set_error("gp_lp_refine: part, k, rounds or lmax out of range");
     return GP_ERR_INVALID_ARG;
   }
@@ -502,8 +502,8 @@ int gp_lp_refine(const gp_graph *gd, int32_t k, int64_t lmax, int32_t rounds, ui
 
 int gp_contract(const gp_graph *gd, const int32_t *labels, gp_coarse **coarse, int32_t *f2c_out, gp_stream stream) {
   GP_TRY(check_graph_desc(gd));
-  if (!labels || !coarse) {
-    set_error("gp_contract: labels and coarse are required");
+  if ((!labels && gd->n > 0) || !coarse) {
+    set_error("gp_contract: labels (unless n = 0) and coarse are required");
     return GP_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
