@@ -265,20 +265,26 @@ def barrier(dist):
     torch.cuda.synchronize()
 
 
+def _reduce_device(dist) -> str:
+    return "cpu" if dist.get_backend() == "gloo" else "cuda"
+
+
 def max_over_ranks(x: float, dist) -> float:
+    """Largest value over the ranks (the slowest rank's time)."""
     import torch
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def sum_over_ranks(x: float, dist) -> float:
+    """Sum over the ranks (the work all replicas did)."""
     import torch
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
