@@ -147,6 +147,12 @@ typedef void *(*gp_alloc_fn)(size_t bytes, gp_stream stream, void *ctx);
 typedef void (*gp_free_fn)(void *ptr, size_t bytes, gp_stream stream, void *ctx);
 int gp_set_allocator(gp_alloc_fn alloc, gp_free_fn release, void *ctx);
 
+/* Freed device blocks of up to 64 MiB are kept by the library (at most 1 GiB in all) and reused for
+ * allocations of exactly the same size on the same stream, so repeated calls on graphs of one shape
+ * make no allocator calls after the first. gp_free_cached returns every kept block to the allocator
+ * (stream-ordered on the stream that freed it). gp_set_allocator does the same before switching. */
+void gp_free_cached(void);
+
 void gp_default_params(gp_params *params);
 
 /* Check the CSR conventions on the device. Returns GP_OK or GP_ERR_BAD_GRAPH. */

@@ -139,6 +139,8 @@ def lib():
         L.gp_lp_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int]
         L.gp_autotune_schedule.restype = ctypes.c_int
         L.gp_autotune_schedule.argtypes = [ctypes.POINTER(GpGraph), VP, VP, VP, VP]
+        L.gp_free_cached.restype = None
+        L.gp_free_cached.argtypes = []
         L.gp_launch_count.restype = I64
         L.gp_launch_count.argtypes = [ctypes.c_int]
         L.gp_profile_enable.restype = ctypes.c_int
@@ -170,6 +172,11 @@ def _install_torch_allocator(L):
 
     _keep.extend([_alloc, _free])
     L.gp_set_allocator(ctypes.cast(_alloc, VP), ctypes.cast(_free, VP), None)
+
+
+def free_cached():
+    """Returns the device blocks the library keeps for reuse to the allocator."""
+    lib().gp_free_cached()
 
 
 def use_default_allocator():

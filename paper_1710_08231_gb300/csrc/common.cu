@@ -20,7 +20,48 @@ static gp_alloc_fn g_alloc = nullptr;
 static gp_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 
+static void *raw_alloc(size_t bytes, cudaStream_t s) {
+  if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void raw_free(void *p, size_t bytes, cudaStream_t s) {
+  if (g_alloc) {
+    if (g_free) g_free(p, bytes, s, g_alloc_ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+// Freed blocks of up to kCacheMaxBlock bytes are kept (at most kCacheMaxTotal bytes in all) and
+// handed out again for an allocation of exactly the same size on the same stream, so repeated calls
+// on graphs of one shape make no allocator calls after the first; reuse on the freeing stream keeps
+// it stream-ordered. free_cached() returns them all to the allocator.
+struct CachedBlock {
+  void *p;
+  size_t bytes;
+  cudaStream_t s;
+};
+static std::mutex g_cache_mu;
+static std::vector<CachedBlock> g_cache;
+static size_t g_cache_bytes = 0;
+constexpr size_t kCacheMaxBlock = size_t(64) << 20;
+constexpr size_t kCacheMaxTotal = size_t(1) << 30;
+
+void free_cached() {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (const CachedBlock &b : g_cache) raw_free(b.p, b.bytes, b.s);
+  g_cache.clear();
+  g_cache_bytes = 0;
+}
+
 void set_allocator(gp_alloc_fn a, gp_free_fn f, void *ctx) {
+  free_cached();  // cached blocks belong to the allocator being replaced
   g_alloc = a;
   g_free = a ? f : nullptr;
   g_alloc_ctx = a ? ctx : nullptr;
@@ -40,22 +81,32 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
     if (t_arena->used > t_arena->high) t_arena->high = t_arena->used;
     return t_arena->base + off;
   }
-  if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
-  void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
+  if (bytes <= kCacheMaxBlock) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (size_t i = g_cache.size(); i-- > 0;) {
+      if (g_cache[i].bytes == bytes && g_cache[i].s == s) {
+        void *p = g_cache[i].p;
+        g_cache[i] = g_cache.back();
+        g_cache.pop_back();
+        g_cache_bytes -= bytes;
+        return p;
+      }
+    }
   }
-  return p;
+  return raw_alloc(bytes, s);
 }
 
 void dev_free(void *p, size_t bytes, cudaStream_t s) {
   if (!p || t_arena) return;
-  if (g_alloc) {
-    if (g_free) g_free(p, bytes, s, g_alloc_ctx);
-    return;
+  if (bytes <= kCacheMaxBlock) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (g_cache_bytes + bytes <= kCacheMaxTotal) {
+      g_cache.push_back({p, bytes, s});
+      g_cache_bytes += bytes;
+      return;
+    }
   }
-  cudaFreeAsync(p, s);
+  raw_free(p, bytes, s);
 }
 
 // ------------------------------------------------------------------------------------------ device

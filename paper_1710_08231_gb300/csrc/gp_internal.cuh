@@ -43,6 +43,7 @@ void set_thread_arena(ScratchArena *a);
 bool arena_active();
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
+void free_cached();  // returns the blocks the library keeps for reuse to the allocator
 
 // Scoped set of temporary allocations, released in stream order when the scope ends.
 class Workspace {

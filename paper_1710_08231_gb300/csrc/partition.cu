@@ -593,6 +593,8 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta) {
 
 int64_t gp_launch_count(int reset) { return gp::launch_count(reset); }
 
+void gp_free_cached(void) { gp::free_cached(); }
+
 int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
                          gp_stream stream) {
   GP_TRY(check_graph_desc(gd));
