@@ -1772,8 +1772,84 @@ int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, 
   return GP_OK;
 }
 
+// Statistics, error flags and profile entries of n counter blocks (host copies). vb/eb: algorithmic
+// bytes per visit and per scanned entry of each job; stats: NULL or per-job outputs; edges/moves:
+// NULL or summed totals.
+static int account_counters(const LpCounters *hc, int n, const int64_t *vb, const int64_t *eb, gp_lp_stats *const *stats,
+                            int64_t *edges_sum, int64_t *moves_sum) {
+  int64_t tot_edges = 0, tot_vis = 0, tot_bytes = 0, tot_moves = 0;
+  for (int j = 0; j < n; j++) {
+    const LpCounters &h = hc[j];
+    if (h.err) {
+      set_error("label propagation: a bounded device barrier gave up");
+      return GP_ERR_TIMEOUT;
+    }
+    int64_t vis = 0, edg = 0;
+    for (int b = 0; b < 8; b++) {
+      vis += (int64_t)h.bin_visits[b];
+      edg += (int64_t)h.bin_edges[b];
+    }
+    // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read;
+    // per scanned entry: adjacency, neighbour label, edge weight (and score)
+    tot_bytes += vis * vb[j] + edg * eb[j];
+    tot_edges += edg;
+    tot_vis += vis;
+    tot_moves += (int64_t)h.moves;
+    if (stats && stats[j]) {
+      stats[j]->rounds = (int64_t)h.rounds;
+      stats[j]->moves = (int64_t)h.moves;
+      stats[j]->movers = (int64_t)h.movers;
+      stats[j]->visits = vis;
+      stats[j]->edges = edg;
+    }
+  }
+  if (edges_sum) *edges_sum = tot_edges;
+  if (moves_sum) *moves_sum = tot_moves;
+  prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
+  if (profiling()) {
+    static const char *names[8] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit",
+                                   "lp_phase_contest", "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"};
+    for (int ph = 0; ph < 8; ph++) {
+      double ms = 0;
+      for (int j = 0; j < n; j++) ms += hc[j].phase_ns[ph] * 1e-6;
+      prof_add_time(names[ph], ms);
+    }
+    double cs = 0, cp = 0, cl = 0, cli = 0, he = 0, hs = 0;
+    for (int j = 0; j < n; j++) {
+      cs += hc[j].contest_small;
+      cp += hc[j].contest_packed;
+      cl += hc[j].contest_large;
+      cli += hc[j].contest_large_items;
+      he += hc[j].hub_entries;
+      hs += hc[j].hub_slots;
+    }
+    prof_add_counts("lp_contest_small_calls", (int64_t)cs, 0, 0);
+    prof_add_counts("lp_contest_packed_calls", (int64_t)cp, 0, 0);
+    prof_add_counts("lp_contest_large_calls", (int64_t)cl, (int64_t)cli, 0);  // edges: contested movers
+    prof_add_counts("lp_hub_work", (int64_t)hs, (int64_t)he, 0);  // items: table slots, edges: entries
+  }
+  return GP_OK;
+}
+
+size_t lp_counters_bytes() { return sizeof(LpCounters); }
+
+int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves) {
+  if (edges) *edges = 0;
+  if (moves) *moves = 0;
+  if (def.count == 0) return GP_OK;
+  std::vector<LpCounters> hc(def.count);
+  GP_CUDA(cudaMemcpyAsync(hc.data(), def.dev, sizeof(LpCounters) * def.count, cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  const int st = account_counters(hc.data(), def.count, def.visit_bytes.data(), def.entry_bytes.data(), nullptr, edges,
+                                  moves);
+  def.count = 0;
+  def.visit_bytes.clear();
+  def.entry_bytes.clear();
+  return st;
+}
+
 // Several independent LP runs in one cooperative launch (same edge-weight type and score use).
-int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg) {
+int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg, LpDeferred *deferred) {
   if (njobs <= 0) return GP_OK;
   const int ew = jobs[0].g.ew_mode();
   const bool lq = jobs[0].q != nullptr;
@@ -1792,38 +1868,65 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   int cap_blocks = 0;
   GP_TRY(coop_capacity(ew, lq, &cap_blocks));
   const int nsm = num_sms();
-  // degree classes and entry counts of all jobs (one kernel, one copy back)
-  std::vector<DGraph> hg(njobs);
-  std::vector<int64_t> pre(njobs + 1, 0);
-  for (int j = 0; j < njobs; j++) {
-    hg[j] = jobs[j].g;
-    pre[j + 1] = pre[j] + jobs[j].g.n;
-  }
-  DGraph *gs_dev;
-  int64_t *pre_dev;
-  unsigned *classes;
-  unsigned long long *entries;
-  GP_TRY(ws.get(&gs_dev, (size_t)njobs));
-  GP_TRY(ws.get(&pre_dev, (size_t)njobs + 1));
-  GP_TRY(ws.zeros(&classes, (size_t)9 * njobs));
-  GP_TRY(ws.zeros(&entries, (size_t)njobs));
-  unsigned long long *hubstat;
-  GP_TRY(ws.zeros(&hubstat, (size_t)2 * njobs));
-  GP_CUDA(cudaMemcpyAsync(gs_dev, hg.data(), sizeof(DGraph) * njobs, cudaMemcpyHostToDevice, s));
-  GP_CUDA(cudaMemcpyAsync(pre_dev, pre.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, s));
-  if (pre[njobs] > 0) {
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((pre[njobs] + 255) / 256, nsm * 8));
-    (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, njobs, cfg.deg_warp, cfg.deg_cta,
-                                                                     classes, entries, hubstat));
-    GP_LAUNCH_CHECK();
-  }
+  // degree classes and entry counts of all jobs (one kernel, one copy back), unless every job brings
+  // them from an earlier call on the same graph and schedule
   std::vector<unsigned> hcls(9 * (size_t)njobs);
   std::vector<unsigned long long> hent(njobs);
-  GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaMemcpyAsync(hent.data(), entries, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, s));
   std::vector<unsigned long long> hhub(2 * (size_t)njobs);
-  GP_CUDA(cudaMemcpyAsync(hhub.data(), hubstat, sizeof(unsigned long long) * hhub.size(), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  bool cached = true;
+  for (int j = 0; j < njobs; j++) {
+    const LpClassInfo *ci = jobs[j].classes;
+    cached = cached && ci && ci->valid && ci->deg_warp == cfg.deg_warp && ci->deg_cta == cfg.deg_cta;
+  }
+  if (cached) {
+    for (int j = 0; j < njobs; j++) {
+      const LpClassInfo &ci = *jobs[j].classes;
+      for (int b = 0; b < 9; b++) hcls[9 * (size_t)j + b] = ci.cls[b];
+      hent[j] = ci.entries;
+      hhub[2 * (size_t)j] = ci.hub_max_cap;
+      hhub[2 * (size_t)j + 1] = ci.hub_cap_sum;
+    }
+  } else {
+    std::vector<DGraph> hg(njobs);
+    std::vector<int64_t> pre(njobs + 1, 0);
+    for (int j = 0; j < njobs; j++) {
+      hg[j] = jobs[j].g;
+      pre[j + 1] = pre[j] + jobs[j].g.n;
+    }
+    DGraph *gs_dev;
+    int64_t *pre_dev;
+    unsigned *classes;
+    unsigned long long *entries;
+    GP_TRY(ws.get(&gs_dev, (size_t)njobs));
+    GP_TRY(ws.get(&pre_dev, (size_t)njobs + 1));
+    GP_TRY(ws.zeros(&classes, (size_t)9 * njobs));
+    GP_TRY(ws.zeros(&entries, (size_t)njobs));
+    unsigned long long *hubstat;
+    GP_TRY(ws.zeros(&hubstat, (size_t)2 * njobs));
+    GP_CUDA(cudaMemcpyAsync(gs_dev, hg.data(), sizeof(DGraph) * njobs, cudaMemcpyHostToDevice, s));
+    GP_CUDA(cudaMemcpyAsync(pre_dev, pre.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, s));
+    if (pre[njobs] > 0) {
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((pre[njobs] + 255) / 256, nsm * 8));
+      (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, njobs, cfg.deg_warp, cfg.deg_cta,
+                                                                       classes, entries, hubstat));
+      GP_LAUNCH_CHECK();
+    }
+    GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(hent.data(), entries, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(hhub.data(), hubstat, sizeof(unsigned long long) * hhub.size(), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < njobs; j++) {
+      LpClassInfo *ci = jobs[j].classes;
+      if (!ci) continue;
+      ci->valid = true;
+      ci->deg_warp = cfg.deg_warp;
+      ci->deg_cta = cfg.deg_cta;
+      for (int b = 0; b < 9; b++) ci->cls[b] = hcls[9 * (size_t)j + b];
+      ci->entries = hent[j];
+      ci->hub_max_cap = hhub[2 * (size_t)j];
+      ci->hub_cap_sum = hhub[2 * (size_t)j + 1];
+    }
+  }
   // Blocks: a job gets at most one block per 256 vertices. When all jobs fit the co-resident
   // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
   // + a fixed per-problem latency term): jobs above twice the mean block load get several blocks,
@@ -2006,63 +2109,40 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
                         : launch_lp<2, false>(probs_dev, bs_dev, bl_dev, grid, s);
     GP_TRY(st);
   }
+  if (deferred) {
+    // keep the counters on the device for lp_collect
+    if (deferred->count + njobs > deferred->capacity) {
+      set_error("run_lp_multi: deferred counter buffer is full");
+      return GP_ERR_INTERNAL;
+    }
+    GP_CUDA(cudaMemcpyAsync(static_cast<LpCounters *>(deferred->dev) + deferred->count, ctr_all,
+                            sizeof(LpCounters) * njobs, cudaMemcpyDeviceToDevice, s));
+    deferred->count += njobs;
+    for (int j = 0; j < njobs; j++) {
+      const DGraph &g = jobs[j].g;
+      deferred->visit_bytes.push_back(2 * g.offset_bytes() + 4 + g.vw_bytes() + 8);
+      deferred->entry_bytes.push_back(8 + g.ew_bytes() + (jobs[j].q ? 4 : 0));
+    }
+    return GP_OK;
+  }
   std::vector<LpCounters> hc(njobs);
   GP_CUDA(cudaMemcpyAsync(hc.data(), ctr_all, sizeof(LpCounters) * njobs, cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
-  int64_t tot_edges = 0, tot_vis = 0, tot_bytes = 0;
+  std::vector<int64_t> vb(njobs), eb(njobs);
   for (int j = 0; j < njobs; j++) {
-    const LpCounters &h = hc[j];
-    if (h.err) {
-      set_error("label propagation: a bounded device barrier gave up");
-      return GP_ERR_TIMEOUT;
-    }
-    int64_t vis = 0, edg = 0;
-    for (int b = 0; b < 8; b++) {
-      vis += (int64_t)h.bin_visits[b];
-      edg += (int64_t)h.bin_edges[b];
-    }
     const DGraph &g = jobs[j].g;
-    // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read;
-    // per scanned entry: adjacency, neighbour label, edge weight (and score)
-    tot_bytes += vis * (2 * g.offset_bytes() + 4 + g.vw_bytes() + 8) + edg * (8 + g.ew_bytes() + (jobs[j].q ? 4 : 0));
-    tot_edges += edg;
-    tot_vis += vis;
-    if (jobs[j].stats) {
-      jobs[j].stats->rounds = (int64_t)h.rounds;
-      jobs[j].stats->moves = (int64_t)h.moves;
-      jobs[j].stats->movers = (int64_t)h.movers;
-      jobs[j].stats->visits = vis;
-      jobs[j].stats->edges = edg;
-    }
+    vb[j] = 2 * g.offset_bytes() + 4 + g.vw_bytes() + 8;
+    eb[j] = 8 + g.ew_bytes() + (jobs[j].q ? 4 : 0);
   }
-  prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
-  if (profiling()) {
-    static const char *names[8] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit",
-                                   "lp_phase_contest", "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"};
-    for (int ph = 0; ph < 8; ph++) {
-      double ms = 0;
-      for (int j = 0; j < njobs; j++) ms += hc[j].phase_ns[ph] * 1e-6;
-      prof_add_time(names[ph], ms);
-    }
-    double cs = 0, cp = 0, cl = 0, cli = 0, he = 0, hs = 0;
-    for (int j = 0; j < njobs; j++) {
-      cs += hc[j].contest_small;
-      cp += hc[j].contest_packed;
-      cl += hc[j].contest_large;
-      cli += hc[j].contest_large_items;
-      he += hc[j].hub_entries;
-      hs += hc[j].hub_slots;
-    }
-    prof_add_counts("lp_contest_small_calls", (int64_t)cs, 0, 0);
-    prof_add_counts("lp_contest_packed_calls", (int64_t)cp, 0, 0);
-    prof_add_counts("lp_contest_large_calls", (int64_t)cl, (int64_t)cli, 0);  // edges: contested movers
-    prof_add_counts("lp_hub_work", (int64_t)hs, (int64_t)he, 0);  // items: table slots, edges: entries
-  }
+  std::vector<gp_lp_stats *> st(njobs);
+  for (int j = 0; j < njobs; j++) st[j] = jobs[j].stats;
+  return account_counters(hc.data(), njobs, vb.data(), eb.data(), st.data(), nullptr, nullptr);
   return GP_OK;
 }
 
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U, int rounds,
-           uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg, bool singletons) {
+           uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg, bool singletons,
+           LpClassInfo *classes, LpDeferred *deferred) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (g.n == 0 || rounds <= 0) return GP_OK;
   LpJob j;
@@ -2076,7 +2156,8 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
   j.seed = seed;
   j.stats = stats;
   j.singletons = singletons;
-  return run_lp_multi(&j, 1, s, cfg);
+  j.classes = classes;
+  return run_lp_multi(&j, 1, s, cfg, deferred);
 }
 
 }  // namespace gp

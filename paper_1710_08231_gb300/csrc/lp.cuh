@@ -1,6 +1,8 @@
 // lp.cuh -- size-constrained label propagation engine (clustering and refinement).
 #pragma once
 
+#include <vector>
+
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -10,6 +12,28 @@ struct LpConfig {
   int deg_cta = 1024;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 1024)
                         // d > deg_cta: several CTAs per vertex, global-memory hash
 };
+
+// Degree classes of a graph under one schedule (vertices per bin, CSR entries, largest hub table and
+// the sum of hub tables). run_lp_multi fills it when `valid` is false and a later call on the same
+// graph and schedule reuses it, skipping the class kernel and its copy back.
+struct LpClassInfo {
+  bool valid = false;
+  int deg_warp = 0, deg_cta = 0;
+  unsigned cls[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long entries = 0, hub_max_cap = 0, hub_cap_sum = 0;
+};
+
+// Counters of several LP calls kept on the device and read back once (lp_collect) instead of after
+// every call. `dev` holds `capacity` counter blocks (lp_counters_bytes() each, from the caller).
+struct LpDeferred {
+  void *dev = nullptr;
+  int capacity = 0, count = 0;
+  std::vector<int64_t> visit_bytes, entry_bytes;  // algorithmic bytes per visit and per entry, by job
+};
+size_t lp_counters_bytes();
+// Reads every deferred counter block back (one synchronisation), checks the device error flags and
+// returns the summed LP edges and admitted moves; adds the LP profile entries when profiling.
+int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves);
 
 // One LP run for run_lp_multi. With vbase/lbase != 0 the job is one graph of a disjoint union:
 // g is its view (g.n local vertices, offsets and vertex weights shifted to its first vertex, adjacency
@@ -28,11 +52,12 @@ struct LpJob {
   // labels start as singletons (vertex v in label lbase + v): in the first sub-round every neighbour
   // label is distinct and no neighbour carries the own label, so connections need no aggregation
   bool singletons = false;
+  LpClassInfo *classes = nullptr;  // optional cache of the graph's degree classes (see LpClassInfo)
 };
 
 // Several independent LP runs in one cooperative launch; they must share the edge-weight type and
 // whether scores are given.
-int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg);
+int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg, LpDeferred *deferred = nullptr);
 
 LpConfig lp_config_from(const gp_params *p);
 
@@ -41,7 +66,7 @@ LpConfig lp_config_from(const gp_params *p);
 // seed is the run's hash seed. stats (host) may be NULL.
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
            int rounds, uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg,
-           bool singletons = false);
+           bool singletons = false, LpClassInfo *classes = nullptr, LpDeferred *deferred = nullptr);
 
 // Block weights of a partition: bw[k] = sum of c(v) over part[v] = b (device). Sets *bad_dev
 // (device int, may be NULL) when a block id is outside [0,k).

@@ -202,6 +202,16 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
   std::vector<const int32_t *> f2c;
   int32_t *cur = nullptr;  // partition of the current level (device, from ws)
   int64_t lp_edges = 0, lp_moves = 0;
+  // LP counters stay on the device until the end (one read back for the whole partition), and each
+  // level's degree classes computed by its coarsening call are reused by its refinement call
+  LpDeferred lpdef;
+  lpdef.capacity = 2 * (int)p.max_levels + (int)p.ip_tries + 4;
+  {
+    unsigned char *buf;
+    GP_TRY(ws.get(&buf, lp_counters_bytes() * (size_t)lpdef.capacity));
+    lpdef.dev = buf;
+  }
+  std::vector<LpClassInfo> level_cls((size_t)p.max_levels + 1);
   const double t_coarse0 = now_ms();
   if (st.n0 > 0) {
     const int64_t T = std::max<int64_t>(p.coarse_min, p.coarse_per_k * (int64_t)k);
@@ -222,11 +232,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       (::gp::count_launch(), k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw));
       GP_LAUNCH_CHECK();
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
-      gp_lp_stats ls;
       GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1),
-                    &ls, s, cfg, true));
-      lp_edges += ls.edges;
-      lp_moves += ls.moves;
+                    nullptr, s, cfg, true, &level_cls[l], &lpdef));
       Level lev;
       lev.f2c_bytes = sizeof(int32_t) * (size_t)gl.n;
       lev.f2c = (int32_t *)dev_alloc(lev.f2c_bytes, s);
@@ -259,7 +266,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     int64_t *bws;
     GP_TRY(ws.get(&bws, (size_t)tries * k));
     std::vector<LpJob> jobs(tries);
-    std::vector<gp_lp_stats> tstats(tries);
+
     for (int t = 0; t < tries; t++) {
       int32_t *pt = parts + (size_t)t * gc.n;
       const uint64_t s_try = hash3(seed, (uint64_t)levels, (uint64_t)(4 + t));
@@ -271,9 +278,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       jobs[t].U = lmax;
       jobs[t].rounds = (int)p.rounds_refine;
       jobs[t].seed = hash3(s_try, (uint64_t)levels, 3);
-      jobs[t].stats = &tstats[t];
     }
-    if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg));
+    if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg, &lpdef));
     // cuts of all tries in one pass; their block weights are the label weights the refinement kept
     std::vector<unsigned long long> hcut2(tries);
     std::vector<int64_t> hbws((size_t)tries * k);
@@ -289,8 +295,6 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       GP_CUDA(cudaStreamSynchronize(s));
     }
     for (int t = 0; t < tries; t++) {
-      lp_edges += tstats[t].edges;
-      lp_moves += tstats[t].moves;
       const int64_t cut = (int64_t)(hcut2[t] / 2);
       const int64_t imb =
           *std::max_element(hbws.begin() + (size_t)t * k, hbws.begin() + (size_t)(t + 1) * k) > lmax ? 1 : 0;
@@ -314,10 +318,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       int32_t *fine = (cur == bufA) ? bufB : bufA;
       GP_TRY(project(cur, f2c[l], G[l].n, fine, s));
       GP_TRY(block_weights(G[l], fine, k, bw, nullptr, s));
-      gp_lp_stats ls;
-      GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), &ls, s, cfg));
-      lp_edges += ls.edges;
-      lp_moves += ls.moves;
+      GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), nullptr, s, cfg,
+                    false, &level_cls[l], &lpdef));
       cur = fine;
     }
     res->ms_refine = now_ms() - t_ref0;
@@ -343,6 +345,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
   res->cut = cut;
   res->max_block_weight = *std::max_element(hbw.begin(), hbw.end());
   res->imbalanced = res->max_block_weight > lmax ? 1 : 0;
+  GP_TRY(lp_collect(lpdef, s, &lp_edges, &lp_moves));
   res->lp_edges = lp_edges;
   res->lp_moves = lp_moves;
   if (learned) res->learned_cut = cut;
