@@ -40,15 +40,43 @@ __global__ void k_mark_used(const int32_t *labels, int64_t n, int64_t nl, uint32
   }
 }
 
-__global__ void k_f2c(DGraph g, const int32_t *labels, const int32_t *newid, int32_t *f2c, int64_t *cnt,
-                      int64_t *cw, int64_t *dsum) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int cv = newid[labels[v]];
-    f2c[v] = cv;
-    atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[cv]), 1ull);
-    atomicAdd(reinterpret_cast<unsigned long long *>(&cw[cv]), (unsigned long long)g.vweight(v));
-    atomicAdd(reinterpret_cast<unsigned long long *>(&dsum[cv]),
-              (unsigned long long)(g.row_begin(v + 1) - g.row_begin(v)));
+// Fine -> coarse map and, per coarse vertex, member count, weight and degree sum. Members of one
+// cluster are mostly neighbours in id order, so the warp combines equal coarse ids before its atomics.
+// A label outside [0, nl) sets *bad and maps its vertex to 0 (the caller reports the error).
+__global__ void k_f2c(DGraph g, const int32_t *labels, int64_t nl, const int32_t *newid, int32_t *f2c, int64_t *cnt,
+                      int64_t *cw, int64_t *dsum, int *bad) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = v0 + threadIdx.x;
+    bool ok = v < g.n;
+    int cv = 0;
+    long long c = 0, d = 0;
+    if (ok) {
+      const int L = labels[v];
+      if (L < 0 || L >= nl) {
+        atomicExch(bad, 1);
+        f2c[v] = 0;
+        ok = false;
+      } else {
+        cv = newid[L];
+        f2c[v] = cv;
+        c = g.vweight(v);
+        d = g.row_begin(v + 1) - g.row_begin(v);
+      }
+    }
+    const unsigned peers = __match_any_sync(kFull, ok ? cv : -1);
+    if (!ok) continue;
+    long long cs = 0, ds = 0;
+    for (unsigned m = peers; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      cs += __shfl_sync(peers, c, src);
+      ds += __shfl_sync(peers, d, src);
+    }
+    if (lane == __ffs(peers) - 1) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[cv]), (unsigned long long)__popc(peers));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&cw[cv]), (unsigned long long)cs);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&dsum[cv]), (unsigned long long)ds);
+    }
   }
 }
 
@@ -611,7 +639,7 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   GP_TRY(ws.zeros(&cw, (size_t)nc));
   GP_TRY(ws.get(&mstart, (size_t)nc + 1));
   GP_TRY(ws.get(&tstart, (size_t)nc + 1));
-  (::gp::count_launch(), k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, newid, f2c, cnt, cw, dsum));
+  (::gp::count_launch(), k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, nl, newid, f2c, cnt, cw, dsum, bad));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_i64(cnt, mstart, nc, mstart + nc, ws));
   GP_TRY(scan_excl_i64(dsum, tstart, nc, tstart + nc, ws));
