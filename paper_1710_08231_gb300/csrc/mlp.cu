@@ -79,33 +79,23 @@ __global__ void __launch_bounds__(256) k_features(DGraph g, int level, const flo
     const float cv = (float)g.vweight(v);
     const float wv = wdeg[v];
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      // lane j takes entry e0 + j: it walks the first (up to) 64 neighbours of u and looks each up in
+      // the first 64 neighbours of v (sorted, in shared memory)
       const int64_t e = e0 + lane;
       const bool has = e < end;
       const int u = has ? g.adj[e] : 0;
-      const int nstep = (int)gp_min64(32, end - e0);
+      const int64_t bu = has ? g.row_begin(u) : 0;
+      const int lenu = has ? (int)gp_min64(g.row_begin(u + 1) - bu, 64) : 0;
       int mine = 0;
-      for (int j = 0; j < nstep; j++) {
-        const int uj = __shfl_sync(kFull, u, j);
-        const int64_t bj = g.row_begin(uj);
-        const int lenj = (int)gp_min64(g.row_begin(uj + 1) - bj, 64);
-        int c = 0;
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const int kk = lane + 32 * h;
-          if (kk < lenj) {
-            const int x = g.adj[bj + kk];
-            int lo = 0, hi = lenv;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (nv[mid] < x) lo = mid + 1;
-              else hi = mid;
-            }
-            c += (lo < lenv && nv[lo] == x) ? 1 : 0;
-          }
+      for (int kk = 0; kk < lenu; kk++) {
+        const int x = g.adj[bu + kk];
+        int lo = 0, hi = lenv;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (nv[mid] < x) lo = mid + 1;
+          else hi = mid;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        if (lane == j) mine = c;
+        mine += (lo < lenv && nv[lo] == x) ? 1 : 0;
       }
       if (!has) continue;
       const float du = (float)(g.row_begin(u + 1) - g.row_begin(u));
