@@ -96,16 +96,30 @@ def time_steps(fn, steps, flush):
 
 
 def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res):
+    """Learned against plain LP on the same graph at seeds 1..10 (geometric means of the per-seed cut
+    and time ratios), plus the timed learned run at the bench's own seed."""
+    import math
     mlp, loss = train_scorer(gp, name, k)
     params = gp.default_params(mode=gp.MODE_LEARNED)
     params.mlp = mlp.data_ptr()
     for _ in range(2):
         gp.partition(dg, k, EPS, SEED, params)
     ms, (_, res) = time_steps(lambda: gp.partition(dg, k, EPS, SEED, params), steps, flush)
+    per_seed = []
+    for sd in range(1, 11):
+        pm, (_, rp) = time_steps(lambda: gp.partition(dg, k, EPS, sd), 1, flush)
+        lm, (_, rl) = time_steps(lambda: gp.partition(dg, k, EPS, sd, params), 1, flush)
+        per_seed.append({"seed": sd, "plain_cut": rp.cut, "learned_cut": rl.cut, "plain_ms": pm, "learned_ms": lm,
+                         "learned_imbalanced": rl.imbalanced})
+    gm = lambda xs: math.exp(sum(math.log(x) for x in xs) / len(xs))
     return {"ms_per_partition": ms / steps, "gteps": res.lp_edges * steps / (ms * 1e-3) / 1e9, "cut": res.cut,
             "imbalanced": res.imbalanced, "plain_cut": plain_res.cut, "plain_ms_per_partition": plain_ms,
             "cut_ratio_learned_over_plain": res.cut / max(plain_res.cut, 1),
             "time_ratio_learned_over_plain": (ms / steps) / plain_ms, "levels": res.levels,
+            "seeds_1_10": {"geomean_cut_ratio": gm([x["learned_cut"] / max(x["plain_cut"], 1) for x in per_seed]),
+                           "geomean_time_ratio": gm([x["learned_ms"] / x["plain_ms"] for x in per_seed]),
+                           "learned_better_or_equal": sum(x["learned_cut"] <= x["plain_cut"] for x in per_seed),
+                           "per_seed": per_seed},
             "training": {"graphs": "2 same-family graphs, seeds 101-102", "steps": 300, "lr": 1e-2,
                          "bce_first_last": loss},
             "note": "learned is reported as measured; worse cuts are not hidden"}
@@ -429,9 +443,12 @@ def main():
         res0 = step()
     lp_edges_step = res0.lp_edges
 
-    # ---- pass A: the timed region (device time per step, L2 flushed between steps)
+    # ---- pass A: the timed region (device time per step, L2 flushed between steps). The library's
+    # per-launch CUDA events (on the launching stream) give each kernel's time inside this region.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = gp.launch_count()
+    gp.profile_read(reset=True)
+    gp.profile_enable(True)
     barrier(dist)
     with ClockSampler(torch.cuda.current_device()) as clk:
         wall0 = time.perf_counter()
@@ -443,21 +460,14 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     barrier(dist)
+    gp.profile_enable(False)
+    prof = gp.profile_read(reset=True)
     launches = gp.launch_count() - launches0
     ms_local = sum(a.elapsed_time(b) for a, b in ev)
     ms_total = max_over_ranks(ms_local, dist)
     edges_all = sum_over_ranks(float(lp_edges_step * args.steps), dist)
     value = edges_all / (ms_total * 1e-3) / 1e9
 
-    # ---- pass B: same steps with per-launch CUDA events around the LP scan kernels
-    gp.profile_read(reset=True)
-    gp.profile_enable(True)
-    for i in range(args.steps):
-        flush.fill_(i)
-        step()
-    torch.cuda.synchronize()
-    gp.profile_enable(False)
-    prof = gp.profile_read(reset=True)
     kernels = [e for e in prof if e["launches"] > 0 and e["bytes"] > 0 and not e["name"].startswith("lp_phase")]
     top = max(kernels, key=lambda e: e["ms"]) if kernels else None
     peak, peak_kind = peaks()
@@ -472,10 +482,13 @@ def main():
                     "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
                     "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                     "kernels_ms_per_step": {e["name"]: e["ms"] / args.steps for e in prof if e["launches"] > 0 and not e["name"].startswith("lp_phase")},
+                    "kernels_achieved_gbs": {e["name"]: {"gbs": e["bytes"] / (e["ms"] * 1e-3) / 1e9,
+                                                         "frac": e["bytes"] / (e["ms"] * 1e-3) / 1e9 / peak}
+                                             for e in prof if e["launches"] > 0 and e["bytes"] > 0 and e["ms"] > 0},
                     "lp_phases_ms_per_step": {e["name"][9:]: e["ms"] / args.steps for e in prof if e["name"].startswith("lp_phase")},
                     "contest_calls_per_step": {e["name"][11:-6]: e["items"] / args.steps for e in prof if e["name"].startswith("lp_contest")}}
 
-    # ---- pass C: end to end through the C ABI with host buffers (copies inside the timed region)
+    # ---- pass B: end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e and is_batch:
         # host CSR in pinned memory; every step copies all graphs in, partitions, copies the parts out

@@ -315,7 +315,8 @@ int gp_profile_enable(int on);
 /* Number of kernel launches the library has issued since load (or since the last reset != 0). */
 int64_t gp_launch_count(int reset);
 /* Copies up to max_entries entries into out and returns how many were written; reset != 0 clears
- * the accumulated entries. */
+ * the accumulated entries. Launches recorded by the calls are resolved here (this call waits for
+ * them); the calls themselves only record CUDA events on their stream. */
 int gp_profile_read(gp_profile_entry *out, int max_entries, int reset);
 
 #ifdef __cplusplus

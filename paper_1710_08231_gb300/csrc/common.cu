@@ -295,11 +295,13 @@ void prof_add_time(const char *name, double ms) {
   e.launches += 1;
 }
 
-int prof_flush(cudaStream_t s) {
-  if (!g_prof_on) return GP_OK;
-  GP_CUDA(cudaStreamSynchronize(s));
-  std::lock_guard<std::mutex> lk(g_prof_mu);
+// Recorded launches are resolved lazily: a call only records its events, and prof_read waits for
+// them, so profiling adds no synchronisation to the calls it measures.
+int prof_flush(cudaStream_t) { return GP_OK; }
+
+static void resolve_pending() {
   for (const Pending &p : g_pending) {
+    cudaEventSynchronize(p.b);
     float ms = 0;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       g_entries[p.entry].ms += ms;
@@ -311,17 +313,26 @@ int prof_flush(cudaStream_t s) {
     g_event_pool.push_back(p.b);
   }
   g_pending.clear();
-  return GP_OK;
 }
 
 int prof_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof_on = on != 0;
+  // events are created here, not inside the calls being measured
+  while (g_prof_on && g_event_pool.size() + 2 * g_pending.size() < 4096) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    g_event_pool.push_back(e);
+  }
   return GP_OK;
 }
 
 int prof_read(gp_profile_entry *out, int max_entries, int reset) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  resolve_pending();
   int n = 0;
   for (const ProfEntry &e : g_entries) {
     if (n >= max_entries) break;

@@ -305,6 +305,6 @@ struct ProfScope {
 };
 void prof_add_counts(const char *name, int64_t items, int64_t edges, int64_t bytes);
 void prof_add_time(const char *name, double ms);  // device time measured inside a kernel
-int prof_flush(cudaStream_t s);  // resolve recorded events (synchronises s)
+int prof_flush(cudaStream_t s);  // kept for call sites; events are resolved by prof_read
 
 }  // namespace gp
