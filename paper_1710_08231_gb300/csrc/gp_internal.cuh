@@ -233,17 +233,20 @@ __device__ __forceinline__ T block_excl_scan64(T x, T *tmp, T *total) {
 }
 
 // Bounded barrier over `nblocks` blocks of a cooperatively launched kernel (all blocks co-resident).
-// Thread 0 of each block arrives on `count` with an acquire-release atomic (its release covers the
-// writes of the whole block, ordered before it by the preceding __syncthreads); the last arrival
-// resets the counter and advances `gen` with a release; the others poll `gen` with acquire loads.
-// A problem of one block needs only __syncthreads. `err` receives GP_ERR_TIMEOUT when a wait gives
-// up (about 2^24 polls), in which case every waiting block returns false.
+// One word per barrier, zero-initialised. At every barrier thread 0 of each block adds to it with one
+// acquire-release atomic (its release covers the writes of the whole block, ordered before it by the
+// preceding __syncthreads): block rank 0 adds 2^31 - (nblocks - 1), every other block adds 1. The
+// additions of one barrier sum to exactly 2^31, and the low 31 bits start at zero, so bit 31 flips when,
+// and only when, the last block has arrived; each block polls the word with acquire loads until bit 31
+// differs from the value its own addition returned. A block that moves on to the next barrier adds
+// again, but bit 31 cannot flip back before every block has arrived there too. A problem of one block
+// needs only __syncthreads. `err` receives GP_ERR_TIMEOUT when a wait gives up (about 2^24 polls), in
+// which case every waiting block returns false.
 constexpr unsigned kBarrierStride = 32;
 inline unsigned barrier_words(unsigned) { return kBarrierStride; }
 
 struct GridBarrier {
   unsigned int *count;  // barrier_words(nblocks) words, zero-initialised
-  unsigned int *gen;
   int *err;
   unsigned int nblocks;
   unsigned int rank;    // this block's index among the nblocks
@@ -264,20 +267,15 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     s_ok = 1;
-    const unsigned my = ld_acquire_u32(b.gen);
+    const unsigned inc = b.rank == 0 ? 0x80000000u - (b.nblocks - 1) : 1u;
     unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(b.count) : "memory");
-    if (old == b.nblocks - 1) {
-      *b.count = 0;
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" : : "l"(b.gen) : "memory");
-    } else {
-      long long polls = 0;
-      while (ld_acquire_u32(b.gen) == my) {
-        if (++polls > (1ll << 24) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
-          atomicExch(b.err, GP_ERR_TIMEOUT);
-          s_ok = 0;
-          break;
-        }
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
+    long long polls = 0;
+    while (((ld_acquire_u32(b.count) ^ old) & 0x80000000u) == 0) {
+      if (++polls > (1ll << 24) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
+        atomicExch(b.err, GP_ERR_TIMEOUT);
+        s_ok = 0;
+        break;
       }
     }
   }

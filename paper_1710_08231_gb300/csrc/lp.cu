@@ -42,13 +42,16 @@ constexpr int kHubChunk = 1024; // CSR entries per hub work item (pre-aggregated
 constexpr int64_t kHubBatchSlots = int64_t(1) << 22;  // hub table slots per batch (tables stay in L2)
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
+// A problem gets at most one block per kVertsPerBlock vertices: small problems are bound by the
+// dependent latency of each phase, so more warps (fewer vertices per warp) shorten every sub-round.
+constexpr int64_t kVertsPerBlock = 64;
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
 constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
 static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
 
-struct SubCounters {
+struct __align__(8) SubCounters {
   unsigned int bin_count[8];
   unsigned int n_movers;
   unsigned int n_contested;
@@ -59,6 +62,8 @@ struct SubCounters {
   unsigned long long max_gain, max_q;
 };
 
+static_assert(sizeof(SubCounters) % 4 == 0 && sizeof(SubCounters) / 4 <= 256, "counters are read word by word");
+
 struct LpCounters {
   SubCounters sc[3];                  // by sub-round index mod 3 (current, next, previous)
   unsigned long long moves_round[2];  // by round parity
@@ -68,7 +73,6 @@ struct LpCounters {
                                    // hub prefix (block 0's view)
   unsigned long long contest_small, contest_packed, contest_large;
   unsigned long long contest_large_items, hub_entries, hub_slots;
-  unsigned int bar_count, bar_gen;
   int err;
   int pad;
 };
@@ -215,13 +219,28 @@ __device__ __forceinline__ Best make_cand(const LpProblem &P, int v, int L, int 
   return b;
 }
 
-// Records the proposal of the active vertex in slot idx (target -1: no proposal).
+// The same with the candidate's label weight lwL = lw[L] already loaded.
+__device__ __forceinline__ Best make_cand_lw(const LpProblem &P, int v, int L, int L0, long long conn, long long qs,
+                                             long long c0, long long cv, long long lwL) {
+  if (L < 0 || L == L0 || conn <= c0) return no_best();  // the own label wins ties
+  if (lwL + cv > P.U) return no_best();                 // not eligible
+  Best b;
+  b.L = L;
+  b.conn = conn;
+  b.qs = qs;
+  b.h = mix64(mix64(P.smix ^ (uint64_t)(uint32_t)v) ^ (uint64_t)(L - P.lbase));
+  return b;
+}
+
+// Records the proposal of the active vertex in slot idx (target -1: no proposal). Score sums are
+// stored only when scores are given (LQ).
+template <bool LQ>
 __device__ __forceinline__ void write_slot(const LpProblem &P, int64_t idx, int v, const Best &b, long long c0) {
   P.mv_t[idx] = b.L;
   if (b.L >= 0) {
     P.mv_v[idx] = v;
     P.mv_gain[idx] = b.conn - c0;
-    P.mv_q[idx] = b.qs;
+    if (LQ) P.mv_q[idx] = b.qs;
     P.mv_adm[idx] = 0;
     P.mv_of_v[v] = (int32_t)idx;
   }
@@ -245,7 +264,8 @@ struct Smem {
   unsigned hist[256];
   unsigned long long base[256];
   unsigned wcnt[kWarps][256];
-  unsigned long long moves;
+  unsigned long long moves;   // admitted moves of the block in the current admission phase
+  unsigned long long movers;  // proposals of the block over the whole call (statistics)
   long long carry;
   int carry_t;
 };
@@ -261,6 +281,10 @@ __device__ __forceinline__ Best block_best_of(Best b, Smem &sm) {
     if (better(sm.best[w], r)) r = sm.best[w];
   __syncthreads();
   return r;
+}
+
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned x) {
+  return __reduce_add_sync(kFull, x);
 }
 
 __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
@@ -280,16 +304,16 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
 // next sub-round, neighbours marked active for the next round. Movers of degree above kBigDeg are
 // listed in P.big instead (counter C.n_big); every block marks their neighbours after the phase.
 // Returns the warp's admitted count.
-__device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters &C, uint8_t *act_next, bool adm,
-                                                 int64_t idx, int v, int T) {
+// This form takes the mover's current label L0 and its row (rb, deg) already loaded.
+__device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCounters &C, uint8_t *act_next, bool adm,
+                                                     int64_t idx, int v, int T, int L0, int64_t rb, int64_t deg) {
   const int lane = threadIdx.x & 31;
-  int64_t rb = 0, deg = 0;
   if (adm) {
-    const int L0 = P.labels[P.vbase + v];
     P.labels[P.vbase + v] = T;
     P.mv_from[idx] = L0;
-    rb = P.g.row_begin(v);
-    deg = P.g.row_begin(v + 1) - rb;
+  } else {
+    rb = 0;
+    deg = 0;
   }
   const unsigned am = __ballot_sync(kFull, adm);
   if (!am) return 0;
@@ -335,6 +359,18 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters
   return (unsigned)__popc(am);
 }
 
+__device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters &C, uint8_t *act_next, bool adm,
+                                                 int64_t idx, int v, int T) {
+  int L0 = 0;
+  int64_t rb = 0, deg = 0;
+  if (adm) {
+    L0 = P.labels[P.vbase + v];
+    rb = P.g.row_begin(v);
+    deg = P.g.row_begin(v + 1) - rb;
+  }
+  return apply_movers_pre(P, C, act_next, adm, idx, v, T, L0, rb, deg);
+}
+
 // Neighbours of the high-degree movers: every block takes marking items (kBigChunk entries of one
 // mover's row) in turn.
 __device__ void mark_big(const LpProblem &P, unsigned nitems, int r, int lb, int nb) {
@@ -367,15 +403,19 @@ __device__ void settle_moves(const LpProblem &P, const SubCounters &Vp, int lb, 
         if (k >= start[x]) b = x;
       i = P.bin_base[b] + (k - start[b]);
     }
-    const int T = k < na ? P.mv_t[i] : -1;
-    const bool adm = T >= 0 && P.mv_adm[i];
-    if (T >= 0) P.demand[T] = 0;
-    long long c = 0;
-    int L0 = -1;
-    if (adm) {
-      c = P.g.vweight(P.mv_v[i]);
+    // the slot's fields are loaded together (those of a slot without a proposal are not used)
+    int T = -1, vv = 0, L0 = -1;
+    uint8_t a = 0;
+    if (k < na) {
+      T = P.mv_t[i];
+      a = P.mv_adm[i];
+      vv = P.mv_v[i];
       L0 = P.mv_from[i];
     }
+    const bool adm = T >= 0 && a;
+    if (T >= 0) P.demand[T] = 0;
+    const long long c = adm ? P.g.vweight(vv) : 0;
+    if (!adm) L0 = -1;
     warp_add_by_key(P.lw, adm, T, c);
     warp_add_by_key(P.lw, adm, L0, -c);
   }
@@ -384,6 +424,8 @@ __device__ void settle_moves(const LpProblem &P, const SubCounters &Vp, int lb, 
 // ------------------------------------------------------------------------------------ phases
 // Classify the active vertices of sub-round (r, s) into degree bins. Each block takes a contiguous
 // chunk of vertices, counts them per bin, reserves space with one atomic per bin and then fills it.
+// Visits and scanned entries per bin (statistics) add up in the block's shared memory over the whole
+// call and reach the counters once, at its end.
 __device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const uint8_t *act, int r, int s,
                                           uint64_t rmix, int64_t *deg) {
   if (!((r == 0 || act[P.vbase + v]) && (int)(mix64(rmix ^ (uint64_t)v) >> 63) == s)) return -1;
@@ -395,13 +437,7 @@ __device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const u
 __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCounters *Vp, int r, int s, uint64_t rmix,
                                int lb, int nb, Smem &sm) {
   __shared__ unsigned s_cnt[8], s_base[8];
-  if (Vp) settle_moves(P, *Vp, lb, nb);
-  if (threadIdx.x < 8) {
-    sm.vis[threadIdx.x] = 0;
-    sm.edg[threadIdx.x] = 0;
-    s_cnt[threadIdx.x] = 0;
-  }
-  __syncthreads();
+  if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
   const uint8_t *act = P.act[r & 1];
   uint8_t *act_next = P.act[(r + 1) & 1];
   const int64_t n = P.g.n;
@@ -437,6 +473,9 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
         flag &= ~(1u << it);
       }
     }
+    // the previous sub-round's moves settle while the loads above are in flight
+    if (Vp) settle_moves(P, *Vp, lb, nb);
+    __syncthreads();
     unsigned codes = 0xffffffffu;
 #pragma unroll
     for (int it = 0; it < kCls; it++) {
@@ -471,13 +510,10 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
       pos = __shfl_sync(kFull, pos, leader);
       if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
     }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      if (sm.vis[threadIdx.x]) atomicAdd(&P.ctr->bin_visits[threadIdx.x], sm.vis[threadIdx.x]);
-      if (sm.edg[threadIdx.x]) atomicAdd(&P.ctr->bin_edges[threadIdx.x], sm.edg[threadIdx.x]);
-    }
     return;
   }
+  if (Vp) settle_moves(P, *Vp, lb, nb);
+  __syncthreads();
   // pass 1: counts
   for (int64_t v0 = lo; v0 < hi; v0 += kThreads) {
     const int64_t v = v0 + threadIdx.x;
@@ -514,11 +550,6 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
     pos = __shfl_sync(kFull, pos, leader);
     if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
   }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    if (sm.vis[threadIdx.x]) atomicAdd(&P.ctr->bin_visits[threadIdx.x], sm.vis[threadIdx.x]);
-    if (sm.edg[threadIdx.x]) atomicAdd(&P.ctr->bin_edges[threadIdx.x], sm.edg[threadIdx.x]);
-  }
 }
 
 // Groups of G lanes (G = 4, 8, 16 or 32 for bins 0-3), one vertex per group, d <= G. The four bins
@@ -534,6 +565,31 @@ __device__ __forceinline__ Best group_best_rt(Best b, int W) {
     if (better(x, b)) b = x;
   }
   return b;
+}
+
+// Unit edge weights without scores: connections are counts (at most 32 in a lane group), so a
+// candidate's rank (conn, then h) is the single 64-bit key conn << 58 | h >> 6, where h = H(seed, v, L)
+// = mix64(hv ^ (L - lbase)) with hv = mix64(smix ^ v). Equal keys (equal counts and equal top 58 bits
+// of h) fall back to the full order (h desc, then L asc) with h recomputed for both labels. Key 0
+// means no candidate (a candidate has conn >= 1). Returns the group's winning label (-1: none) and
+// its key in *Kout.
+__device__ __forceinline__ int group_best_unit(unsigned long long K, int L, int W, uint64_t hv, int64_t lbase,
+                                               unsigned long long *Kout) {
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const unsigned long long K2 = __shfl_xor_sync(kFull, K, o, W);
+    const int L2 = __shfl_xor_sync(kFull, L, o, W);
+    bool take = K2 > K;
+    if (K2 == K && K2 != 0 && L2 != L) {
+      const uint64_t h2 = mix64(hv ^ (uint64_t)(L2 - lbase)), h1 = mix64(hv ^ (uint64_t)(L - lbase));
+      take = h2 > h1 || (h2 == h1 && L2 < L);
+    }
+    if (take) {
+      K = K2;
+      L = L2;
+    }
+  }
+  *Kout = K;
+  return L;
 }
 
 template <int EW, bool LQ>
@@ -560,7 +616,7 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
     const unsigned sub = (unsigned)lane / (unsigned)G;
     const unsigned base = (j - pre[bin]) * gpw * U;
     int v[U], Lu[U], L0[U], qq[U];
-    long long w[U];
+    long long w[U], cv[U];
     int64_t beg[U], d[U];
     bool valid[U];
 #pragma unroll
@@ -574,10 +630,12 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
       beg[u] = 0;
       d[u] = 0;
       L0[u] = -2;
+      cv[u] = 0;
       if (valid[u]) {
         beg[u] = P.g.row_begin(v[u]);
         d[u] = P.g.row_begin(v[u] + 1) - beg[u];
         L0[u] = P.labels[P.vbase + v[u]];
+        cv[u] = P.g.vweight(v[u]);
       }
     }
     int nbr[U];
@@ -593,34 +651,59 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
     }
 #pragma unroll
     for (int u = 0; u < U; u++) Lu[u] = nbr[u] >= 0 ? P.labels[nbr[u]] : -1;
+    // connections of every vertex first, then the label weights of all their candidates in one
+    // round of loads, then the choices and the stores
+    long long c0[U], conn[U], qs[U], lwL[U];
+    bool cand[U];
+    const unsigned gmask = G == 32 ? kFull : ((1u << G) - 1u) << (sub * (unsigned)G);
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const bool has = gl < d[u];
-      long long c0 = (has && Lu[u] == L0[u]) ? w[u] : 0;
-      for (int o = G / 2; o > 0; o >>= 1) c0 += __shfl_xor_sync(kFull, c0, o, G);
       const unsigned long long key = ((unsigned long long)sub << 32) | (unsigned)Lu[u];
       const unsigned peers = __match_any_sync(kFull, key);
-      long long conn;
       if constexpr (EW == 0) {
-        conn = __popc(peers);
+        conn[u] = __popc(peers);
       } else {
         if (!__any_sync(kFull, w[u] >= (1ll << 26))) {
-          conn = (long long)__reduce_add_sync(peers, (unsigned)w[u]);
+          conn[u] = (long long)__reduce_add_sync(peers, (unsigned)w[u]);
         } else {
-          conn = 0;
-          for (unsigned m = peers; m; m &= m - 1) conn += __shfl_sync(peers, w[u], __ffs(m) - 1);
+          conn[u] = 0;
+          for (unsigned m = peers; m; m &= m - 1) conn[u] += __shfl_sync(peers, w[u], __ffs(m) - 1);
         }
       }
-      long long qs = 0;
-      if constexpr (LQ) qs = (long long)__reduce_add_sync(peers, (unsigned)qq[u]);
-      const bool first = lane == __ffs(peers) - 1;
-      const long long cv = valid[u] ? P.g.vweight(v[u]) : 0;
+      qs[u] = 0;
+      if constexpr (LQ) qs[u] = (long long)__reduce_add_sync(peers, (unsigned)qq[u]);
+      // the own-label connection is the connection of the group's lanes that carry the own label
+      const unsigned own = __ballot_sync(kFull, has && Lu[u] == L0[u]) & gmask;
+      if constexpr (EW == 0) {
+        c0[u] = __popc(own);
+      } else {
+        const long long cown = __shfl_sync(kFull, conn[u], own ? __ffs(own) - 1 : lane);
+        c0[u] = own ? cown : 0;
+      }
+      cand[u] = has && lane == __ffs(peers) - 1 && Lu[u] != L0[u] && conn[u] > c0[u];
+      lwL[u] = cand[u] ? P.lw[Lu[u]] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
       Best b = no_best();
-      if (has && first) b = make_cand(P, v[u], Lu[u], L0[u], conn, qs, c0, cv);
-      b = group_best_rt<LQ>(b, G);
+      if constexpr (EW == 0 && !LQ) {
+        const uint64_t hv = mix64(P.smix ^ (uint64_t)(uint32_t)v[u]);
+        unsigned long long K = 0;
+        int L = -1;
+        if (cand[u] && lwL[u] + cv[u] <= P.U) {  // eligible
+          K = ((unsigned long long)conn[u] << 58) | (mix64(hv ^ (uint64_t)(Lu[u] - P.lbase)) >> 6);
+          L = Lu[u];
+        }
+        b.L = group_best_unit(K, L, G, hv, P.lbase, &K);
+        b.conn = (long long)(K >> 58);
+      } else {
+        if (cand[u]) b = make_cand_lw(P, v[u], Lu[u], L0[u], conn[u], qs[u], c0[u], cv[u], lwL[u]);
+        b = group_best_rt<LQ>(b, G);
+      }
       const bool mover = valid[u] && gl == 0 && b.L >= 0;
-      if (valid[u] && gl == 0) write_slot(P, P.bin_base[bin] + base + u * gpw + sub, v[u], b, c0);
-      warp_add_by_key(P.demand, mover, b.L, cv);
+      if (valid[u] && gl == 0) write_slot<LQ>(P, P.bin_base[bin] + base + u * gpw + sub, v[u], b, c0[u]);
+      warp_add_by_key(P.demand, mover, b.L, cv[u]);
     }
   }
 }
@@ -692,7 +775,7 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
       }
       b = group_best<LQ, 32>(b);
       if (lane == 0) {
-        write_slot(P, P.bin_base[4] + i, v, b, 0);
+        write_slot<LQ>(P, P.bin_base[4] + i, v, b, 0);
         if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
       }
     }
@@ -732,7 +815,7 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
     __syncwarp();
     b = group_best<LQ, 32>(b);
     if (lane == 0) {
-      write_slot(P, P.bin_base[4] + i, v, b, c0);
+      write_slot<LQ>(P, P.bin_base[4] + i, v, b, c0);
       if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
     }
   }
@@ -769,7 +852,7 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
       }
       b = block_best_of<LQ>(b, sm);
       if (threadIdx.x == 0) {
-        write_slot(P, P.bin_base[5] + i, v, b, 0);
+        write_slot<LQ>(P, P.bin_base[5] + i, v, b, 0);
         if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
       }
     }
@@ -808,7 +891,7 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
     }
     b = block_best_of<LQ>(b, sm);
     if (threadIdx.x == 0) {
-      write_slot(P, P.bin_base[5] + i, v, b, c0);
+      write_slot<LQ>(P, P.bin_base[5] + i, v, b, c0);
       if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv);
     }
   }
@@ -1016,7 +1099,7 @@ __device__ void hub_choose_final(const LpProblem &P, unsigned h0, unsigned h1, i
     for (unsigned it = P.hub_scx[i]; it < P.hub_scx[i + 1]; it++)
       if (better(part[it - s_lo], b)) b = part[it - s_lo];
     const int v = P.bin[6][i];
-    write_slot(P, P.bin_base[6] + i, v, b, P.hub_c0[i]);
+    write_slot<true>(P, P.bin_base[6] + i, v, b, P.hub_c0[i]);
     if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)P.g.vweight(v));
   }
 }
@@ -1053,7 +1136,7 @@ __device__ void hub_direct_final(const LpProblem &P, unsigned cnt, int lb, int n
     for (unsigned c = P.hub_prefix[i]; c < P.hub_prefix[i + 1]; c++)
       if (better(part[c], b)) b = part[c];
     const int v = P.bin[6][i];
-    write_slot(P, P.bin_base[6] + i, v, b, 0);
+    write_slot<true>(P, P.bin_base[6] + i, v, b, 0);
     if (b.L >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)P.g.vweight(v));
   }
 }
@@ -1095,14 +1178,21 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounter
     bool contested = false, adm = false;
     int64_t i = 0;
     int T = -1, v = 0;
+    int L0 = 0;
+    int64_t rb = 0, deg = 0;
     if (k < na) {
+      // target and vertex first, then the target's weights and the vertex's label and row together
       i = M.slot(k);
       T = P.mv_t[i];
+      v = P.mv_v[i];
       if (T >= 0) {
         movers++;
-        if (P.lw[T] + P.demand[T] <= P.U) {
+        const long long lwT = P.lw[T], dT = P.demand[T];
+        L0 = P.labels[P.vbase + v];
+        rb = P.g.row_begin(v);
+        deg = P.g.row_begin(v + 1) - rb;
+        if (lwT + dT <= P.U) {
           adm = true;
-          v = P.mv_v[i];
           P.mv_adm[i] = 1;
         } else {
           contested = true;
@@ -1111,13 +1201,22 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounter
         }
       }
     }
-    moved += apply_movers(P, C, act_next, adm, i, v, T);
+    moved += apply_movers_pre(P, C, act_next, adm, i, v, T, L0, rb, deg);
     const unsigned pos = warp_append(&C.n_contested, contested);
     if (contested) P.ct[pos] = (unsigned)i;
   }
-  movers = (unsigned)block_sum_of((long long)movers, sm);
-  if (threadIdx.x == 0 && movers) atomicAdd(&P.ctr->movers, (unsigned long long)movers);
-  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&P.ctr->moves_round[r & 1], (unsigned long long)moved);
+  // movers (statistics) add up in shared memory over the call; the round's move count gets one
+  // atomic per block
+  movers = warp_sum_u32(movers);
+  if ((threadIdx.x & 31) == 0) {
+    if (movers) atomicAdd(&sm.movers, (unsigned long long)movers);
+    if (moved) atomicAdd(&sm.moves, (unsigned long long)moved);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.moves) {
+    atomicAdd(&P.ctr->moves_round[r & 1], sm.moves);
+    sm.moves = 0;
+  }
   for (int o = 16; o > 0; o >>= 1) {
     mg = max(mg, __shfl_xor_sync(kFull, mg, o));
     mq = max(mq, __shfl_xor_sync(kFull, mq, o));
@@ -1128,14 +1227,17 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounter
   }
 }
 
-// Contested order: target asc, gain desc, score sum desc, id asc.
+// Contested order: target asc, gain desc, score sum desc (with scores), id asc.
+template <bool LQ>
 __device__ __forceinline__ bool mover_less(const LpProblem &P, unsigned x, unsigned y) {
   const int tx = P.mv_t[x], ty = P.mv_t[y];
   if (tx != ty) return tx < ty;
   const long long gx = P.mv_gain[x], gy = P.mv_gain[y];
   if (gx != gy) return gx > gy;
-  const long long qx = P.mv_q[x], qy = P.mv_q[y];
-  if (qx != qy) return qx > qy;
+  if (LQ) {
+    const long long qx = P.mv_q[x], qy = P.mv_q[y];
+    if (qx != qy) return qx > qy;
+  }
   return P.mv_v[x] < P.mv_v[y];
 }
 
@@ -1278,7 +1380,7 @@ __device__ void contest_small(const LpProblem &P, const SubCounters &C, SubCount
         bool swap;
         if (x == 0xffffffffu) swap = (y != 0xffffffffu) == up;
         else if (y == 0xffffffffu) swap = !up;
-        else swap = mover_less(P, y, x) == up;
+        else swap = mover_less<LQ>(P, y, x) == up;
         if (swap) {
           key[i] = y;
           key[l] = x;
@@ -1504,7 +1606,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   __syncthreads();
   const int lb = (int)blockIdx.x - P.block_begin, nb = P.block_count;
   LpCounters *ctr = P.ctr;
-  const GridBarrier bar{P.bar, &ctr->bar_gen, &ctr->err, (unsigned)nb, (unsigned)lb};
+  const GridBarrier bar{P.bar, &ctr->err, (unsigned)nb, (unsigned)lb};
   // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there) in
   // shared memory and writes the totals once at the end
   __shared__ unsigned long long pacc[8];
@@ -1520,21 +1622,20 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   };
   // block-local copies of the sub-round counters (thread 0 reads them once after a barrier)
   __shared__ SubCounters sV, sVp;
+  // (one 32-bit word per thread, all loads in flight together)
   auto load_view = [&](const SubCounters &src) {
-    if (threadIdx.x == 0) {
-      const volatile SubCounters &vs = src;
-      for (int b = 0; b < 8; b++) sV.bin_count[b] = vs.bin_count[b];
-      sV.n_movers = vs.n_movers;
-      sV.n_contested = vs.n_contested;
-      sV.hub_chunks = vs.hub_chunks;
-      sV.n_big = vs.n_big;
-      sV.hub_batches = vs.hub_batches;
-      sV.max_gain = vs.max_gain;
-      sV.max_q = vs.max_q;
-    }
+    if (threadIdx.x < sizeof(SubCounters) / 4)
+      reinterpret_cast<unsigned *>(&sV)[threadIdx.x] =
+          reinterpret_cast<const volatile unsigned *>(&src)[threadIdx.x];
     __syncthreads();
   };
+  if (threadIdx.x < 8) {
+    sm.vis[threadIdx.x] = 0;
+    sm.edg[threadIdx.x] = 0;
+  }
   if (threadIdx.x == 0) {
+    sm.moves = 0;
+    sm.movers = 0;
     for (int b = 0; b < 8; b++) sV.bin_count[b] = 0;
     sV.n_movers = sV.n_contested = sV.hub_chunks = sV.n_big = sV.hub_batches = 0;
     sV.max_gain = sV.max_q = 0;
@@ -1644,6 +1745,12 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   }
   // label weights of the last sub-round's moves (every block has passed its final barrier)
   if (t_last >= 0) settle_moves(P, sV, lb, nb);
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    if (sm.vis[threadIdx.x]) atomicAdd(&ctr->bin_visits[threadIdx.x], sm.vis[threadIdx.x]);
+    if (sm.edg[threadIdx.x]) atomicAdd(&ctr->bin_edges[threadIdx.x], sm.edg[threadIdx.x]);
+  }
+  if (threadIdx.x == 0 && sm.movers) atomicAdd(&ctr->movers, sm.movers);
   tick(5);
   if (lb == 0 && threadIdx.x == 0)
     for (int k = 0; k < 8; k++) ctr->phase_ns[k] = pacc[k];
@@ -1744,8 +1851,8 @@ int coop_capacity(int ew, bool lq, int *out) {
 
 template <int EW, bool LQ>
 int launch_lp(const LpProblem *probs_dev, const int *blk_start_dev, const int *blk_list_dev, int grid, cudaStream_t s) {
-  void *args[] = {(void *)&probs_dev, (void *)&blk_start_dev, (void *)&blk_list_dev};
   count_launch();
+  void *args[] = {(void *)&probs_dev, (void *)&blk_start_dev, (void *)&blk_list_dev};
   GP_CUDA(cudaLaunchCooperativeKernel((void *)k_lp<EW, LQ>, grid, kThreads, args, kDynSmem, s));
   return GP_OK;
 }
@@ -1936,7 +2043,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   for (int j = 0; j < njobs; j++) {
     // (the large contest stages 32 bytes per block of a problem in the dynamic shared memory)
     useful[j] = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(cap_blocks, (int64_t)(kDynSmem / 32)),
-                                                       (jobs[j].g.n + 255) / 256));
+                                                       (jobs[j].g.n + kVertsPerBlock - 1) / kVertsPerBlock));
     sum_useful += useful[j];
   }
   std::vector<int> nblk(njobs, 1), home(njobs, -1);
