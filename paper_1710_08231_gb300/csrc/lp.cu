@@ -23,6 +23,7 @@
 //     target fit, no order is needed; otherwise the contested proposals are sorted (one CTA in shared
 //     memory up to 4096, else a cooperative LSD radix sort) and admitted by a segmented prefix sum.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -52,7 +53,7 @@ static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dyn
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
 
 struct __align__(8) SubCounters {
-  unsigned int bin_count[8];
+  unsigned int bin_count[8];  // (the running counts live in LpProblem::binres; views copy them here)
   unsigned int n_movers;
   unsigned int n_contested;
   unsigned int hub_chunks;
@@ -123,6 +124,10 @@ struct LpProblem {
   unsigned int *hist;        // block_count * 256
   unsigned long long *hoff;  // block_count * 256 + 256
   unsigned int *bar;         // barrier_words(block_count)
+  // bin reservation counters by sub-round index mod 3: bin b of set k at binres[k * 256 + b * 32], one
+  // 128-byte line per counter so that the blocks' reservations on different bins do not queue on one
+  // line
+  unsigned int *binres;
   LpCounters *ctr;
 };
 
@@ -344,17 +349,26 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   }
   const int64_t excl = incl - deg;
   const int64_t total = __shfl_sync(kFull, incl, 31);
-  for (int64_t t0 = 0; t0 < total; t0 += 32) {
-    const int64_t t = t0 + lane;
-    // owner: the largest lane j with excl_j <= t
-    int j = 0;
+  // four entries per lane per step: all adjacency loads are issued before any mark is stored
+  constexpr int kMarkUnroll = 4;
+  for (int64_t t0 = 0; t0 < total; t0 += 32 * kMarkUnroll) {
+    int32_t a[kMarkUnroll];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int64_t ex = __shfl_sync(kFull, excl, j + step);
-      if (j + step < 32 && ex <= t) j += step;
+    for (int x = 0; x < kMarkUnroll; x++) {
+      const int64_t t = t0 + x * 32 + lane;
+      // owner: the largest lane j with excl_j <= t
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t ex = __shfl_sync(kFull, excl, j + step);
+        if (j + step < 32 && ex <= t) j += step;
+      }
+      const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
+      a[x] = t < total ? __ldg(P.g.adj + rbj + (t - exj)) : -1;
     }
-    const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
-    if (t < total) act_next[__ldg(P.g.adj + rbj + (t - exj))] = 1;
+#pragma unroll
+    for (int x = 0; x < kMarkUnroll; x++)
+      if (a[x] >= 0) act_next[a[x]] = 1;
   }
   return (unsigned)__popc(am);
 }
@@ -437,6 +451,7 @@ __device__ __forceinline__ int active_bin(const LpProblem &P, int64_t v, const u
 __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCounters *Vp, int r, int s, uint64_t rmix,
                                int lb, int nb, Smem &sm) {
   __shared__ unsigned s_cnt[8], s_base[8];
+  const unsigned bres = (unsigned)((2 * r + s) % 3) * 256;
   if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
   const uint8_t *act = P.act[r & 1];
   uint8_t *act_next = P.act[(r + 1) & 1];
@@ -484,15 +499,18 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
       if (flag >> it & 1) b = dd[it] == 0 ? kBinZero : bin_of(dd[it], P.deg_warp, P.deg_cta);
       if (b >= 0) codes = (codes & ~(15u << (4 * it))) | ((unsigned)b << (4 * it));
       const unsigned peers = __match_any_sync(kFull, b);
+      // entries of the lanes in the same bin summed in the warp (at most 2^31 in all): one shared
+      // atomic per bin and warp
+      const unsigned esum = __reduce_add_sync(peers, (unsigned)dd[it]);
       if (b >= 0 && lane == __ffs(peers) - 1) {
         atomicAdd(&sm.vis[b], (unsigned long long)__popc(peers));
         if (b < kBins) atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+        if (esum) atomicAdd(&sm.edg[b], (unsigned long long)esum);
       }
-      if (b >= 0 && dd[it]) atomicAdd(&sm.edg[b], (unsigned long long)dd[it]);
     }
     __syncthreads();
     if (threadIdx.x < kBins) {
-      s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&C.bin_count[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+      s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&P.binres[bres + threadIdx.x * 32], s_cnt[threadIdx.x]) : 0;
       s_cnt[threadIdx.x] = 0;
     }
     __syncthreads();
@@ -524,15 +542,16 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
       b = active_bin(P, v, act, r, s, rmix, &d);
     }
     const unsigned peers = __match_any_sync(kFull, b);
+    const unsigned esum = __reduce_add_sync(peers, (unsigned)d);
     if (b >= 0 && lane == __ffs(peers) - 1) {
       atomicAdd(&sm.vis[b], (unsigned long long)__popc(peers));
       if (b < kBins) atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
+      if (esum) atomicAdd(&sm.edg[b], (unsigned long long)esum);
     }
-    if (b >= 0 && d) atomicAdd(&sm.edg[b], (unsigned long long)d);
   }
   __syncthreads();
   if (threadIdx.x < kBins) {
-    s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&C.bin_count[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+    s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&P.binres[bres + threadIdx.x * 32], s_cnt[threadIdx.x]) : 0;
     s_cnt[threadIdx.x] = 0;
   }
   __syncthreads();
@@ -1622,9 +1641,12 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   };
   // block-local copies of the sub-round counters (thread 0 reads them once after a barrier)
   __shared__ SubCounters sV, sVp;
-  // (one 32-bit word per thread, all loads in flight together)
-  auto load_view = [&](const SubCounters &src) {
-    if (threadIdx.x < sizeof(SubCounters) / 4)
+  // (one 32-bit word per thread, all loads in flight together; the bin counts come from binres)
+  static_assert(offsetof(SubCounters, bin_count) == 0, "bin counts lead the counters");
+  auto load_view = [&](const SubCounters &src, int t) {
+    if (threadIdx.x < 8)
+      sV.bin_count[threadIdx.x] = reinterpret_cast<const volatile unsigned *>(P.binres)[(t % 3) * 256 + threadIdx.x * 32];
+    else if (threadIdx.x < sizeof(SubCounters) / 4)
       reinterpret_cast<unsigned *>(&sV)[threadIdx.x] =
           reinterpret_cast<const volatile unsigned *>(&src)[threadIdx.x];
     __syncthreads();
@@ -1650,7 +1672,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       SubCounters &Cn = ctr->sc[(t + 1) % 3];
       if (lb == 0) {
         // counter set t+1 was last used by sub-round t-2, which every block has finished
-        if (threadIdx.x < 8) Cn.bin_count[threadIdx.x] = 0;
+        if (threadIdx.x < 8) P.binres[((t + 1) % 3) * 256 + threadIdx.x * 32] = 0;
         if (threadIdx.x == 0) {
           Cn.n_movers = 0;
           Cn.n_contested = 0;
@@ -1665,7 +1687,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       __syncthreads();
       phase_classify(P, C, t > 0 ? &sVp : nullptr, r, s, rmix, lb, nb, sm);
       if (!grid_sync(bar)) return false;
-      load_view(C);
+      load_view(C, t);
       tick(0);
       t_last = t;
       unsigned active = 0;
@@ -1683,7 +1705,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
         if (!grid_sync(bar)) return false;
         tick(1);
         if (P.has_hubs && sV.bin_count[6] && direct) {
-          load_view(C);  // hub chunks
+          load_view(C, t);  // hub chunks
           hub_direct_part<EW, LQ>(P, sV.bin_count[6], sV.hub_chunks, lb, nb, sm);
           if (!grid_sync(bar)) return false;
           tick(2);
@@ -1691,7 +1713,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           if (!grid_sync(bar)) return false;
           tick(6);
         } else if (P.has_hubs && sV.bin_count[6]) {
-          load_view(C);  // hub batches
+          load_view(C, t);  // hub batches
           const unsigned nbat = sV.hub_batches;
           for (unsigned bt = 0; bt < nbat; bt++) {
             const unsigned h0 = P.hub_bstart[bt], h1 = P.hub_bstart[bt + 1];
@@ -1709,7 +1731,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
         if (lb == 0 && threadIdx.x == 0 && s == 0) ctr->moves_round[(r + 1) & 1] = 0;
         phase_admit<LQ>(P, C, sV, r, lb, nb, sm);
         if (!grid_sync(bar)) return false;
-        load_view(C);  // contested count and key ranges
+        load_view(C, t);  // contested count and key ranges
         tick(3);
         const unsigned nc = sV.n_contested;
         if (nc > 0) {
@@ -1719,7 +1741,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
             if (!contest_large<LQ>(P, sV, &C, nc, r, lb, nb, bar, sm, dsm)) return false;
           }
           if (!grid_sync(bar)) return false;
-          load_view(C);  // high-degree movers listed by the contest
+          load_view(C, t);  // high-degree movers listed by the contest
           tick(4);
         }
         if (sV.n_big > 0) {
@@ -2125,6 +2147,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   unsigned *bar_all;
   GP_TRY(ws.zeros(&ctr_all, (size_t)njobs));
   GP_TRY(ws.zeros(&bar_all, (size_t)njobs * kBarrierStride));
+  unsigned *binres_all;
+  GP_TRY(ws.zeros(&binres_all, (size_t)njobs * 3 * 256));
   for (int j = 0; j < njobs; j++) {
     const LpJob &jb = jobs[j];
     LpProblem &P = hp[j];
@@ -2173,6 +2197,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.hist, (size_t)nblk[j] * 256 + 16));
     GP_TRY(ws.get(&P.hoff, (size_t)nblk[j] * 256 + 256 + 16));
     P.ctr = ctr_all + j;
+    P.binres = binres_all + (size_t)j * 3 * 256;
     P.bar = bar_all + (size_t)j * kBarrierStride;
     const unsigned nhub = hcls[9 * j + 6];
     if (nhub) {
