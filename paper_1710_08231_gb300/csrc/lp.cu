@@ -678,8 +678,7 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const bool has = gl < d[u];
-      const unsigned long long key = ((unsigned long long)sub << 32) | (unsigned)Lu[u];
-      const unsigned peers = __match_any_sync(kFull, key);
+      const unsigned peers = __match_any_sync(kFull, (unsigned)Lu[u]) & gmask;
       if constexpr (EW == 0) {
         conn[u] = __popc(peers);
       } else {
@@ -707,15 +706,25 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
     for (int u = 0; u < U; u++) {
       Best b = no_best();
       if constexpr (EW == 0 && !LQ) {
+        // first the 32-bit key conn << 26 | h >> 38 (maximum over the group with one shuffle per
+        // level); a unique maximum is the exact winner. Equal keys in some group (equal counts and
+        // equal top 26 bits of h) send the whole warp through the exact 64-bit comparison.
         const uint64_t hv = mix64(P.smix ^ (uint64_t)(uint32_t)v[u]);
-        unsigned long long K = 0;
-        int L = -1;
-        if (cand[u] && lwL[u] + cv[u] <= P.U) {  // eligible
-          K = ((unsigned long long)conn[u] << 58) | (mix64(hv ^ (uint64_t)(Lu[u] - P.lbase)) >> 6);
-          L = Lu[u];
+        const bool elig = cand[u] && lwL[u] + cv[u] <= P.U;
+        const uint64_t h = elig ? mix64(hv ^ (uint64_t)(Lu[u] - P.lbase)) : 0;
+        const unsigned K = elig ? ((unsigned)conn[u] << 26) | (unsigned)(h >> 38) : 0u;
+        unsigned Km = K;
+        for (int o = G / 2; o > 0; o >>= 1) Km = max(Km, __shfl_xor_sync(kFull, Km, o, G));
+        const unsigned top = __ballot_sync(kFull, Km != 0 && K == Km) & gmask;
+        if (__any_sync(kFull, __popc(top) > 1)) {
+          unsigned long long K64 = elig ? ((unsigned long long)conn[u] << 58) | (h >> 6) : 0ull;
+          b.L = group_best_unit(K64, elig ? Lu[u] : -1, G, hv, P.lbase, &K64);
+          b.conn = (long long)(K64 >> 58);
+        } else {
+          const int Lw = __shfl_sync(kFull, Lu[u], top ? __ffs(top) - 1 : lane);
+          b.L = top ? Lw : -1;
+          b.conn = (long long)(Km >> 26);
         }
-        b.L = group_best_unit(K, L, G, hv, P.lbase, &K);
-        b.conn = (long long)(K >> 58);
       } else {
         if (cand[u]) b = make_cand_lw(P, v[u], Lu[u], L0[u], conn[u], qs[u], c0[u], cv[u], lwL[u]);
         b = group_best_rt<LQ>(b, G);
