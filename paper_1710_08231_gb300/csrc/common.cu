@@ -53,6 +53,41 @@ static size_t g_cache_bytes = 0;
 constexpr size_t kCacheMaxBlock = size_t(64) << 20;
 constexpr size_t kCacheMaxTotal = size_t(1) << 30;
 
+// The calling thread's pinned staging buffer for Readback (grown on demand, kept until the thread
+// exits).
+namespace {
+struct PinnedStage {
+  unsigned char *p = nullptr;
+  size_t cap = 0;
+  ~PinnedStage() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local PinnedStage t_stage;
+}  // namespace
+
+int Readback::run(cudaStream_t s) {
+  if (items.empty()) return GP_OK;
+  if (t_stage.cap < total) {
+    if (t_stage.p) cudaFreeHost(t_stage.p);
+    t_stage.p = nullptr;
+    t_stage.cap = 0;
+    const size_t cap = std::max<size_t>(total, 64 * 1024);
+    void *h = nullptr;
+    GP_CUDA(cudaMallocHost(&h, cap));
+    t_stage.p = static_cast<unsigned char *>(h);
+    t_stage.cap = cap;
+  }
+  for (const Item &it : items)
+    if (it.bytes) GP_CUDA(cudaMemcpyAsync(t_stage.p + it.off, it.dev, it.bytes, cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  for (const Item &it : items)
+    if (it.bytes) std::memcpy(it.host, t_stage.p + it.off, it.bytes);
+  items.clear();
+  total = 0;
+  return GP_OK;
+}
+
 void free_cached() {
   std::lock_guard<std::mutex> lk(g_cache_mu);
   for (const CachedBlock &b : g_cache) raw_free(b.p, b.bytes, b.s);

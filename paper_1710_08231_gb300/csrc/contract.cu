@@ -15,6 +15,7 @@
 #include <climits>
 
 #include "contract.cuh"
+#include "lp.cuh"
 #include "sort.cuh"
 
 namespace gp {
@@ -96,8 +97,10 @@ __global__ void k_max_i64(const int64_t *x, int64_t n, unsigned long long *out) 
   if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
-__global__ void k_row_classify(int64_t nc, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2, int32_t *l3,
-                               int32_t *l4, unsigned *counts) {
+// nc_dev: the number of coarse vertices (device; the grid is sized for an upper bound)
+__global__ void k_row_classify(const int64_t *nc_dev, const int64_t *dsum, int32_t *l0, int32_t *l1, int32_t *l2,
+                               int32_t *l3, int32_t *l4, unsigned *counts) {
+  const int64_t nc = *nc_dev;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nc; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = base + threadIdx.x;
     int b = -1;
@@ -596,7 +599,7 @@ int alloc_graph(OwnedGraph *g, int64_t n, int64_t m, cudaStream_t s) {
 }
 
 int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGraph *out, int32_t *f2c_user,
-                   cudaStream_t s) {
+                   cudaStream_t s, const LpConfig *cfg, LpClassInfo *cls) {
   Workspace ws(s);
   const int nsm = num_sms();
   const int64_t n = g.n;
@@ -620,51 +623,57 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   (::gp::count_launch(), k_mark_used<<<grid_n(n), 256, 0, s>>>(labels, n, nl, used, bad));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_u32(used, newid, nl, hdr, ws));
-  int64_t hh[4];
-  int hbad = 0;
-  GP_CUDA(cudaMemcpyAsync(hh, hdr, sizeof(hh), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
-  if (hbad) {
-    set_error("contract: a label is outside [0, n)");
-    return GP_ERR_INVALID_ARG;
-  }
-  const int64_t nc = hh[0];
+  // The coarse vertex count nc = hdr[0] stays on the device until the read back after step 4: the
+  // arrays indexed by coarse vertex are sized for the bound min(n, nl) (zero beyond nc, so the scans
+  // over the bound equal the scans over nc) and the row classification reads nc on the device.
+  const int64_t ncb = std::max<int64_t>(1, std::min<int64_t>(n, nl));
   // 2. fine -> coarse map, member counts, coarse vertex weights, degree sums
   int32_t *f2c = f2c_user;
   if (!f2c) GP_TRY(ws.get(&f2c, (size_t)n));
   int64_t *cnt, *dsum, *mstart, *tstart, *cw;
-  GP_TRY(ws.zeros(&cnt, (size_t)nc + 1));
-  GP_TRY(ws.zeros(&dsum, (size_t)nc + 1));
-  GP_TRY(ws.zeros(&cw, (size_t)nc));
-  GP_TRY(ws.get(&mstart, (size_t)nc + 1));
-  GP_TRY(ws.get(&tstart, (size_t)nc + 1));
+  GP_TRY(ws.zeros(&cnt, (size_t)ncb + 1));
+  GP_TRY(ws.zeros(&dsum, (size_t)ncb + 1));
+  GP_TRY(ws.zeros(&cw, (size_t)ncb));
+  GP_TRY(ws.get(&mstart, (size_t)ncb + 1));
+  GP_TRY(ws.get(&tstart, (size_t)ncb + 1));
   (::gp::count_launch(), k_f2c<<<grid_n(n), 256, 0, s>>>(g, labels, nl, newid, f2c, cnt, cw, dsum, bad));
   GP_LAUNCH_CHECK();
-  GP_TRY(scan_excl_i64(cnt, mstart, nc, mstart + nc, ws));
-  GP_TRY(scan_excl_i64(dsum, tstart, nc, tstart + nc, ws));
+  GP_TRY(scan_excl_i64(cnt, mstart, ncb, mstart + ncb, ws));
+  GP_TRY(scan_excl_i64(dsum, tstart, ncb, tstart + ncb, ws));
   // 3. members bucketed by coarse id
   unsigned *fill;
   int32_t *members;
-  GP_TRY(ws.zeros(&fill, (size_t)nc));
+  GP_TRY(ws.zeros(&fill, (size_t)ncb));
   GP_TRY(ws.get(&members, (size_t)n));
   (::gp::count_launch(), k_members<<<grid_n(n), 256, 0, s>>>(n, f2c, mstart, fill, members));
   // 4. rows binned by pair count
   int32_t *lists[5];
   unsigned *counts_dev;
-  for (int b = 0; b < 5; b++) GP_TRY(ws.get(&lists[b], (size_t)nc));
+  for (int b = 0; b < 5; b++) GP_TRY(ws.get(&lists[b], (size_t)ncb));
   GP_TRY(ws.zeros(&counts_dev, 5));
-  (::gp::count_launch(), k_row_classify<<<grid_n(nc), 256, 0, s>>>(nc, dsum, lists[0], lists[1], lists[2], lists[3],
-                                                                    lists[4], counts_dev));
+  (::gp::count_launch(), k_row_classify<<<grid_n(ncb), 256, 0, s>>>(hdr, dsum, lists[0], lists[1], lists[2],
+                                                                     lists[3], lists[4], counts_dev));
   GP_LAUNCH_CHECK();
   unsigned long long *maxvw_dev;
   GP_TRY(ws.zeros(&maxvw_dev, 1));
-  (::gp::count_launch(), k_max_i64<<<grid_n(nc), 256, 0, s>>>(cw, nc, maxvw_dev));
+  (::gp::count_launch(), k_max_i64<<<grid_n(ncb), 256, 0, s>>>(cw, ncb, maxvw_dev));
   unsigned counts[5];
   unsigned long long maxvw = 0;
-  GP_CUDA(cudaMemcpyAsync(counts, counts_dev, sizeof(counts), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaMemcpyAsync(&maxvw, maxvw_dev, sizeof(maxvw), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  int64_t hh[4];
+  int hbad = 0;
+  {
+    Readback rb;
+    rb.add(hh, hdr, sizeof(hh));
+    rb.add(&hbad, bad, sizeof(int));
+    rb.add(counts, counts_dev, sizeof(counts));
+    rb.add(&maxvw, maxvw_dev, sizeof(maxvw));
+    GP_TRY(rb.run(s));
+  }
+  if (hbad) {
+    set_error("contract: a label is outside [0, n)");
+    return GP_ERR_INVALID_ARG;
+  }
+  const int64_t nc = hh[0];
   RowArgs a;
   a.g = g;
   a.f2c = f2c;
@@ -732,8 +741,25 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   int64_t *off_tmp;
   GP_TRY(ws.get(&off_tmp, (size_t)nc + 1));
   GP_TRY(scan_excl_i64(a.rowcnt, off_tmp, nc, off_tmp + nc, ws));
-  GP_CUDA(cudaMemcpyAsync(&mc, off_tmp + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  // the next level's LP degree classes need only the coarse offsets: computed here and read back
+  // with the coarse entry count
+  unsigned long long *cls_dev = nullptr;
+  unsigned long long cls_words[kLpClassWords];
+  if (cfg && cls) {
+    GP_TRY(ws.get(&cls_dev, (size_t)kLpClassWords));
+    DGraph cg;
+    cg.n = nc;
+    cg.off = off_tmp;
+    cg.off64 = 1;
+    GP_TRY(lp_classes_launch(cg, *cfg, cls_dev, ws));
+  }
+  {
+    Readback rb;
+    rb.add(&mc, off_tmp + nc, sizeof(int64_t));
+    if (cls_dev) rb.add(cls_words, cls_dev, sizeof(cls_words));
+    GP_TRY(rb.run(s));
+  }
+  if (cls_dev) lp_classes_from(cls_words, *cfg, cls);
   GP_TRY(alloc_graph(out, nc, mc, s));
   out->max_vw = (int64_t)maxvw;
   GP_CUDA(cudaMemcpyAsync(out->off, off_tmp, sizeof(int64_t) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));

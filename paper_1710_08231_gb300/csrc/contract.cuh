@@ -41,9 +41,13 @@ struct OwnedGraph {
 
 int alloc_graph(OwnedGraph *g, int64_t n, int64_t m, cudaStream_t s);
 
+struct LpConfig;
+struct LpClassInfo;
+
 // labels[n] in [0, nl). Writes the coarse graph into *out (allocated here) and f2c[n] (device,
-// caller-allocated, may be NULL).
+// caller-allocated, may be NULL). With cfg and cls (may be NULL) it also fills *cls with the coarse
+// graph's LP degree classes under cfg, read back together with the coarse sizes.
 int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGraph *out, int32_t *f2c,
-                   cudaStream_t s);
+                   cudaStream_t s, const LpConfig *cfg = nullptr, LpClassInfo *cls = nullptr);
 
 }  // namespace gp

@@ -45,6 +45,24 @@ void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 void free_cached();  // returns the blocks the library keeps for reuse to the allocator
 
+// Several device ranges read to host memory with one synchronisation of the stream: the copies go
+// through the calling thread's pinned staging buffer (so they are queued without blocking) and are
+// scattered to their host destinations after the single cudaStreamSynchronize.
+struct Readback {
+  struct Item {
+    void *host;
+    const void *dev;
+    size_t bytes, off;
+  };
+  std::vector<Item> items;
+  size_t total = 0;
+  void add(void *host, const void *dev, size_t bytes) {
+    items.push_back({host, dev, bytes, total});
+    total += (bytes + 15) & ~size_t(15);
+  }
+  int run(cudaStream_t s);
+};
+
 // Scoped set of temporary allocations, released in stream order when the scope ends.
 class Workspace {
  public:

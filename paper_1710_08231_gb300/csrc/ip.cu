@@ -55,6 +55,8 @@ struct IpArgs {
   int32_t *mv_t;
   long long *mv_g;
   uint8_t *flag;
+  int64_t smem_ns;           // > 0: the bisection keeps part, gk, dist and both BFS queues of every try
+                             // in dynamic shared memory (every graph of the launch has ns <= smem_ns)
   long long *gws;            // k-sized scratch arrays
   unsigned long long *gminh;
   int *gstart;
@@ -93,7 +95,12 @@ __device__ void set_bfs(const DGraph &g, int64_t vbase, int32_t *part, int32_t *
   }
 }
 
+// Per-vertex state of a bisection in shared memory: 5 arrays of ns int32 (part, gk, dist, qa, qb).
+constexpr int64_t kIpSmemMaxNs = 8192;
+constexpr size_t ip_smem_bytes(int64_t ns) { return (size_t)ns * 5 * sizeof(int32_t); }
+
 __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
+  extern __shared__ __align__(16) unsigned char ip_dsm[];
   __shared__ BlockSortSmem sm;
   __shared__ int s_any, s_maxd;
   const IpGraph &G = a.graphs[a.block_graph[blockIdx.x]];
@@ -102,8 +109,19 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
   const int n = (int)g.n, k = G.k;
   const size_t ns = (size_t)G.ns;
   const size_t so = (size_t)G.scr_off + (size_t)t * ns, ko = (size_t)G.kscr_off + (size_t)t * k;
-  int32_t *part = G.parts + (size_t)t * n, *gk = a.gk + so, *dist = a.dist + so;
+  int32_t *const part_out = G.parts + (size_t)t * n;
+  int32_t *part = part_out, *gk = a.gk + so, *dist = a.dist + so;
   int32_t *qa = a.qa + so, *qb = a.qb + so;
+  if (a.smem_ns > 0) {
+    // small coarsest graphs: the BFS state lives in shared memory (the partition is copied out at
+    // the end)
+    int32_t *sp = reinterpret_cast<int32_t *>(ip_dsm);
+    part = sp;
+    gk = sp + ns;
+    dist = sp + 2 * ns;
+    qa = sp + 3 * ns;
+    qb = sp + 4 * ns;
+  }
   unsigned long long *ka = a.ka + so, *kb = a.kb + so;
   int32_t *va = a.va + so, *vb = a.vb + so;
   long long *gws = a.gws + ko;
@@ -208,6 +226,10 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
         },
         sm);
     __syncthreads();
+  }
+  if (a.smem_ns > 0) {
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) part_out[v] = part[v];
   }
 }
 
@@ -377,11 +399,28 @@ __global__ void k_vw_stats(DGraph g, unsigned long long *mx, unsigned long long 
   }
 }
 
-__global__ void k_deg_flags(DGraph g, uint32_t *keep, int64_t *deg0) {
+// Keep flags (degree > 0) and degrees; with `acc`, also acc[0] = max c(v) over the kept vertices and
+// acc[1] = sum of c(v) over all vertices.
+__global__ void k_deg_flags(DGraph g, uint32_t *keep, int64_t *deg0, unsigned long long *acc) {
+  unsigned long long m = 0, sum = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
     keep[v] = d > 0 ? 1u : 0u;
     deg0[v] = d;
+    if (acc) {
+      const unsigned long long c = (unsigned long long)g.vweight(v);
+      if (d > 0) m = max(m, c);
+      sum += c;
+    }
+  }
+  if (!acc) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(kFull, m, o));
+    sum += __shfl_xor_sync(kFull, sum, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(&acc[0], m);
+    if (sum) atomicAdd(&acc[1], sum);
   }
 }
 
@@ -481,7 +520,8 @@ int grid_for_n(int64_t n) {
 
 }  // namespace
 
-int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s) {
+int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s,
+                            int *err_dev) {
   if (njobs <= 0) return GP_OK;
   Workspace ws(s);
   std::vector<IpGraph> hg(njobs);
@@ -545,10 +585,23 @@ int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_
   a.block_graph = bg_dev;
   a.block_try = bt_dev;
   const int grid = (int)bgraph.size();
-  (::gp::count_launch(), k_bisect<<<grid, kIpThreads, 0, s>>>(a));
+  int64_t max_ns = 0;
+  for (const IpGraph &G : hg) max_ns = std::max<int64_t>(max_ns, G.ns);
+  a.smem_ns = max_ns <= kIpSmemMaxNs ? max_ns : 0;
+  const size_t dsm = a.smem_ns > 0 ? ip_smem_bytes(a.smem_ns) : 0;
+  static bool attr_set = false;
+  if (!attr_set) {
+    GP_CUDA(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ip_smem_bytes(kIpSmemMaxNs)));
+    attr_set = true;
+  }
+  (::gp::count_launch(), k_bisect<<<grid, kIpThreads, dsm, s>>>(a));
   GP_LAUNCH_CHECK();
   (::gp::count_launch(), k_repair<<<grid, kIpThreads, 0, s>>>(a));
   GP_LAUNCH_CHECK();
+  if (err_dev) {
+    GP_CUDA(cudaMemcpyAsync(err_dev, a.err, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return GP_OK;
+  }
   int err = 0;
   GP_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
@@ -560,7 +613,7 @@ int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_
 }
 
 int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries, int repair_rounds,
-                      int32_t *parts, cudaStream_t s) {
+                      int32_t *parts, cudaStream_t s, int *err_dev) {
   IpJob j;
   j.g = g;
   j.vbase = 0;
@@ -569,7 +622,7 @@ int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int l
   j.seed = seed;
   j.level = level;
   j.parts = parts;
-  return initial_partition_multi(&j, 1, tries, repair_rounds, s);
+  return initial_partition_multi(&j, 1, tries, repair_rounds, s, err_dev);
 }
 
 int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev, cudaStream_t s) {
@@ -611,11 +664,14 @@ int vertex_weight_stats(const DGraph &g, int64_t *maxc, int64_t *total, cudaStre
   return GP_OK;
 }
 
-int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s) {
+int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s, int64_t *W_out,
+                   int64_t *maxc_kept_out) {
   out->g0 = g;
   out->n0 = g.n;
   out->n_iso = 0;
   out->rank = nullptr;
+  if (W_out) *W_out = 0;
+  if (maxc_kept_out) *maxc_kept_out = 0;
   if (g.n == 0) return GP_OK;
   uint32_t *keep;
   int64_t *deg, *total;
@@ -623,13 +679,19 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
   GP_TRY(ws.get(&keep, (size_t)g.n));
   GP_TRY(ws.get(&deg, (size_t)g.n));
   GP_TRY(ws.get(&rank, (size_t)g.n));
-  GP_TRY(ws.get(&total, 1));
-  (::gp::count_launch(), k_deg_flags<<<grid_for_n(g.n), 256, 0, s>>>(g, keep, deg));
+  // total[0] = kept vertices, total[1] = max kept weight, total[2] = total weight (one read back)
+  GP_TRY(ws.zeros(&total, 3));
+  const bool stats = W_out || maxc_kept_out;
+  (::gp::count_launch(), k_deg_flags<<<grid_for_n(g.n), 256, 0, s>>>(
+                             g, keep, deg, stats ? reinterpret_cast<unsigned long long *>(total + 1) : nullptr));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_u32(keep, rank, g.n, total, ws));
-  int64_t n0 = 0;
-  GP_CUDA(cudaMemcpyAsync(&n0, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int64_t h[3] = {0, 0, 0};
+  GP_CUDA(cudaMemcpyAsync(h, total, sizeof(h), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
+  const int64_t n0 = h[0];
+  if (maxc_kept_out) *maxc_kept_out = h[1];
+  if (W_out) *W_out = h[2];
   if (n0 == g.n) return GP_OK;
   out->n0 = n0;
   out->n_iso = g.n - n0;

@@ -8,8 +8,9 @@ namespace gp {
 
 // Recursive bisection of `tries` independent tries (try t uses s_try = H(seed, level, 4 + t)),
 // followed by balance repair. parts: tries * n int32 (device) receives the k-way partitions.
+// err_dev (device int, may be NULL): see initial_partition_multi.
 int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int level, int tries,
-                      int repair_rounds, int32_t *parts, cudaStream_t s);
+                      int repair_rounds, int32_t *parts, cudaStream_t s, int *err_dev = nullptr);
 
 // The same for several graphs of a disjoint union in one launch (one CTA per graph and try).
 struct IpJob {
@@ -21,7 +22,10 @@ struct IpJob {
   int level = 0;
   int32_t *parts = nullptr;  // tries * g.n
 };
-int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s);
+// err_dev (device int, may be NULL): when given, the repair's error flag is copied there instead of
+// being read back here (the caller reads it later, with other results), so the call does not wait.
+int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s,
+                            int *err_dev = nullptr);
 
 // cut (each undirected edge once) of part on g; also block weights into bw[k] when bw != NULL.
 int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev,
@@ -39,7 +43,10 @@ struct Stripped {
   int32_t *rank = nullptr;  // n entries (device), NULL when n_iso == 0
   DGraph g0;
 };
-int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s);
+// With W_out / maxc_kept_out (host, may be NULL) it also returns the total vertex weight and the
+// largest weight of a vertex with neighbours, from the same read back.
+int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s, int64_t *W_out = nullptr,
+                   int64_t *maxc_kept_out = nullptr);
 
 // part_full[v] = part0[rank[v]] for kept vertices; degree-0 vertices in ascending id order go
 // to the block of minimum weight (ties: smaller id) given bw (block weights of the kept vertices).

@@ -1971,6 +1971,37 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
 
 size_t lp_counters_bytes() { return sizeof(LpCounters); }
 
+int lp_classes_launch(const DGraph &g, const LpConfig &cfg, unsigned long long *words_dev, Workspace &ws) {
+  cudaStream_t s = ws.stream();
+  GP_CUDA(cudaMemsetAsync(words_dev, 0, sizeof(unsigned long long) * kLpClassWords, s));
+  if (g.n <= 0) return GP_OK;
+  DGraph *gs_dev;
+  int64_t *pre_dev;
+  GP_TRY(ws.get(&gs_dev, 1));
+  GP_TRY(ws.get(&pre_dev, 2));
+  const int64_t pre[2] = {0, g.n};
+  GP_CUDA(cudaMemcpyAsync(gs_dev, &g, sizeof(DGraph), cudaMemcpyHostToDevice, s));
+  GP_CUDA(cudaMemcpyAsync(pre_dev, pre, sizeof(pre), cudaMemcpyHostToDevice, s));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, num_sms() * 8));
+  // words: [0, 5) the 9 unsigned class counts, [5] entries, [6, 8) hub statistics
+  (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, 1, cfg.deg_warp, cfg.deg_cta,
+                                                                 reinterpret_cast<unsigned *>(words_dev),
+                                                                 words_dev + 5, words_dev + 6));
+  GP_LAUNCH_CHECK();
+  return GP_OK;
+}
+
+void lp_classes_from(const unsigned long long *words, const LpConfig &cfg, LpClassInfo *ci) {
+  const unsigned *cls = reinterpret_cast<const unsigned *>(words);
+  ci->valid = true;
+  ci->deg_warp = cfg.deg_warp;
+  ci->deg_cta = cfg.deg_cta;
+  for (int b = 0; b < 9; b++) ci->cls[b] = cls[b];
+  ci->entries = words[5];
+  ci->hub_max_cap = words[6];
+  ci->hub_cap_sum = words[7];
+}
+
 int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves) {
   if (edges) *edges = 0;
   if (moves) *moves = 0;
@@ -2049,10 +2080,11 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
                                                                        classes, entries, hubstat));
       GP_LAUNCH_CHECK();
     }
-    GP_CUDA(cudaMemcpyAsync(hcls.data(), classes, sizeof(unsigned) * hcls.size(), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(hent.data(), entries, sizeof(unsigned long long) * njobs, cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(hhub.data(), hubstat, sizeof(unsigned long long) * hhub.size(), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaStreamSynchronize(s));
+    Readback rb;
+    rb.add(hcls.data(), classes, sizeof(unsigned) * hcls.size());
+    rb.add(hent.data(), entries, sizeof(unsigned long long) * njobs);
+    rb.add(hhub.data(), hubstat, sizeof(unsigned long long) * hhub.size());
+    GP_TRY(rb.run(s));
     for (int j = 0; j < njobs; j++) {
       LpClassInfo *ci = jobs[j].classes;
       if (!ci) continue;

@@ -23,6 +23,13 @@ struct LpClassInfo {
   unsigned long long entries = 0, hub_max_cap = 0, hub_cap_sum = 0;
 };
 
+// Degree classes of one graph computed without a read back: lp_classes_launch writes kLpClassWords
+// words into words_dev (device, caller-owned) on the workspace's stream; after the caller has read
+// them to the host, lp_classes_from fills the LpClassInfo.
+constexpr int kLpClassWords = 8;
+int lp_classes_launch(const DGraph &g, const LpConfig &cfg, unsigned long long *words_dev, Workspace &ws);
+void lp_classes_from(const unsigned long long *words, const LpConfig &cfg, LpClassInfo *ci);
+
 // Counters of several LP calls kept on the device and read back once (lp_collect) instead of after
 // every call. `dev` holds `capacity` counter blocks (lp_counters_bytes() each, from the caller).
 struct LpDeferred {

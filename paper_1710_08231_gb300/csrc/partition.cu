@@ -188,13 +188,13 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
   const LpConfig cfg = schedule_for(&p);
   const DGraph g = make_dgraph(gin);
   Workspace ws(s);
-  int64_t W = 0;
-  GP_TRY(vertex_weight_stats(g, nullptr, &W, s));
+  // degree-0 vertices are set aside; the same read back gives the total weight and the largest weight
+  // of a kept vertex (the level-0 graph's max c(v))
+  int64_t W = 0, maxc0 = 0;
+  Stripped st;
+  GP_TRY(strip_isolated(g, &st, ws, s, &W, &maxc0));
   const int64_t lmax = lmax_of(W, k, eps);
   res->lmax = lmax;
-  // degree-0 vertices are set aside
-  Stripped st;
-  GP_TRY(strip_isolated(g, &st, ws, s));
   res->n_isolated = st.n_iso;
   Hierarchy H;
   H.s = s;
@@ -224,9 +224,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     while (G.back().n > T && (int64_t)f2c.size() < p.max_levels) {
       const int l = (int)f2c.size();
       const DGraph &gl = G.back();
-      int64_t maxc = 0;
-      if (l == 0) GP_TRY(vertex_weight_stats(gl, &maxc, nullptr, s));
-      else maxc = H.levels.back().g.max_vw;  // reported by the contraction that built this level
+      // (level 0: from the strip's read back; later levels: reported by the contraction)
+      const int64_t maxc = l == 0 ? maxc0 : H.levels.back().g.max_vw;
       const int64_t U = std::max<int64_t>(maxc, lmax / p.cluster_div);
       (::gp::count_launch(), k_iota<<<grid_n(gl.n), 256, 0, s>>>(labels, gl.n));
       (::gp::count_launch(), k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw));
@@ -242,7 +241,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
         return GP_ERR_OOM;
       }
       H.levels.push_back(lev);
-      GP_TRY(contract_graph(gl, labels, gl.n, &H.levels.back().g, H.levels.back().f2c, s));
+      GP_TRY(contract_graph(gl, labels, gl.n, &H.levels.back().g, H.levels.back().f2c, s, &cfg, &level_cls[l + 1]));
       const int64_t n_before = gl.n;
       G.push_back(H.levels.back().g.view());
       f2c.push_back(H.levels.back().f2c);
@@ -259,7 +258,9 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     int64_t *bw;
     GP_TRY(ws.get(&parts, (size_t)tries * (size_t)gc.n));
     GP_TRY(ws.get(&bw, (size_t)k));
-    GP_TRY(initial_partition(gc, k, lmax, seed, levels, tries, (int)p.repair_rounds, parts, s));
+    int *ip_err;  // read back with the tries' cuts
+    GP_TRY(ws.zeros(&ip_err, 1));
+    GP_TRY(initial_partition(gc, k, lmax, seed, levels, tries, (int)p.repair_rounds, parts, s, ip_err));
     int best = -1;
     int64_t best_cut = 0, best_imb = 0;
     // the tries' LP refinements run as independent problems of one launch
@@ -278,6 +279,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       jobs[t].U = lmax;
       jobs[t].rounds = (int)p.rounds_refine;
       jobs[t].seed = hash3(s_try, (uint64_t)levels, 3);
+      // degree classes of the coarsest graph from the contraction that built it (if any)
+      jobs[t].classes = level_cls[levels].valid ? &level_cls[levels] : nullptr;
     }
     if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg, &lpdef));
     // cuts of all tries in one pass; their block weights are the label weights the refinement kept
@@ -290,9 +293,16 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
         (::gp::count_launch(), k_tries_cut<<<grid_n(gc.n), 256, 0, s>>>(gc, parts, tries, cut2));
         GP_LAUNCH_CHECK();
       }
-      GP_CUDA(cudaMemcpyAsync(hcut2.data(), cut2, sizeof(unsigned long long) * tries, cudaMemcpyDeviceToHost, s));
-      GP_CUDA(cudaMemcpyAsync(hbws.data(), bws, sizeof(int64_t) * (size_t)tries * k, cudaMemcpyDeviceToHost, s));
-      GP_CUDA(cudaStreamSynchronize(s));
+      int herr = 0;
+      Readback rb;
+      rb.add(hcut2.data(), cut2, sizeof(unsigned long long) * tries);
+      rb.add(hbws.data(), bws, sizeof(int64_t) * (size_t)tries * k);
+      rb.add(&herr, ip_err, sizeof(int));
+      GP_TRY(rb.run(s));
+      if (herr) {
+        set_error("initial partitioning: gain range too wide for the repair sort keys");
+        return herr;
+      }
     }
     for (int t = 0; t < tries; t++) {
       const int64_t cut = (int64_t)(hcut2[t] / 2);
