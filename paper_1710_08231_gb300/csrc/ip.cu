@@ -625,15 +625,22 @@ int initial_partition(const DGraph &g, int k, int64_t lmax, uint64_t seed, int l
   return initial_partition_multi(&j, 1, tries, repair_rounds, s, err_dev);
 }
 
-int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev, cudaStream_t s) {
-  Workspace ws(s);
-  unsigned long long *acc;
-  GP_TRY(ws.zeros(&acc, 1));
+int eval_cut_launch(const DGraph &g, const int32_t *part, int64_t k, unsigned long long *acc_dev, int64_t *bw_dev,
+                    cudaStream_t s) {
+  GP_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(unsigned long long), s));
   if (g.n > 0) {
-    (::gp::count_launch(), k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc));
+    (::gp::count_launch(), k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc_dev));
     GP_LAUNCH_CHECK();
   }
   if (bw_dev) GP_TRY(block_weights(g, part, k, bw_dev, nullptr, s));
+  return GP_OK;
+}
+
+int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev, cudaStream_t s) {
+  Workspace ws(s);
+  unsigned long long *acc;
+  GP_TRY(ws.get(&acc, 1));
+  GP_TRY(eval_cut_launch(g, part, k, acc, bw_dev, s));
   unsigned long long h = 0;
   GP_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   GP_CUDA(cudaStreamSynchronize(s));
@@ -665,7 +672,7 @@ int vertex_weight_stats(const DGraph &g, int64_t *maxc, int64_t *total, cudaStre
 }
 
 int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s, int64_t *W_out,
-                   int64_t *maxc_kept_out) {
+                   int64_t *maxc_kept_out, const LpConfig *cfg, LpClassInfo *cls) {
   out->g0 = g;
   out->n0 = g.n;
   out->n_iso = 0;
@@ -686,12 +693,22 @@ int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s
                              g, keep, deg, stats ? reinterpret_cast<unsigned long long *>(total + 1) : nullptr));
   GP_LAUNCH_CHECK();
   GP_TRY(scan_excl_u32(keep, rank, g.n, total, ws));
+  // the LP degree classes of g, valid for the level-0 graph when no vertex is stripped
+  unsigned long long *cls_dev = nullptr;
+  unsigned long long cls_words[kLpClassWords];
+  if (cfg && cls) {
+    GP_TRY(ws.get(&cls_dev, (size_t)kLpClassWords));
+    GP_TRY(lp_classes_launch(g, *cfg, cls_dev, ws));
+  }
   int64_t h[3] = {0, 0, 0};
-  GP_CUDA(cudaMemcpyAsync(h, total, sizeof(h), cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  Readback rb;
+  rb.add(h, total, sizeof(h));
+  if (cls_dev) rb.add(cls_words, cls_dev, sizeof(cls_words));
+  GP_TRY(rb.run(s));
   const int64_t n0 = h[0];
   if (maxc_kept_out) *maxc_kept_out = h[1];
   if (W_out) *W_out = h[2];
+  if (cls_dev && n0 == g.n) lp_classes_from(cls_words, *cfg, cls);
   if (n0 == g.n) return GP_OK;
   out->n0 = n0;
   out->n_iso = g.n - n0;

@@ -27,6 +27,10 @@ struct IpJob {
 int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_rounds, cudaStream_t s,
                             int *err_dev = nullptr);
 
+// The kernels of eval_cut without the read back: *acc_dev (device) receives twice the cut.
+int eval_cut_launch(const DGraph &g, const int32_t *part, int64_t k, unsigned long long *acc_dev, int64_t *bw_dev,
+                    cudaStream_t s);
+
 // cut (each undirected edge once) of part on g; also block weights into bw[k] when bw != NULL.
 int eval_cut(const DGraph &g, const int32_t *part, int64_t k, int64_t *cut_host, int64_t *bw_dev,
              cudaStream_t s);
@@ -44,9 +48,10 @@ struct Stripped {
   DGraph g0;
 };
 // With W_out / maxc_kept_out (host, may be NULL) it also returns the total vertex weight and the
-// largest weight of a vertex with neighbours, from the same read back.
+// largest weight of a vertex with neighbours, from the same read back; with cfg and cls it fills *cls
+// with g's LP degree classes when no vertex is stripped (then g is the level-0 graph).
 int strip_isolated(const DGraph &g, Stripped *out, Workspace &ws, cudaStream_t s, int64_t *W_out = nullptr,
-                   int64_t *maxc_kept_out = nullptr);
+                   int64_t *maxc_kept_out = nullptr, const LpConfig *cfg = nullptr, LpClassInfo *cls = nullptr);
 
 // part_full[v] = part0[rank[v]] for kept vertices; degree-0 vertices in ascending id order go
 // to the block of minimum weight (ties: smaller id) given bw (block weights of the kept vertices).

@@ -2002,13 +2002,15 @@ void lp_classes_from(const unsigned long long *words, const LpConfig &cfg, LpCla
   ci->hub_cap_sum = words[7];
 }
 
-int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves) {
+int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves, Readback *extra) {
   if (edges) *edges = 0;
   if (moves) *moves = 0;
-  if (def.count == 0) return GP_OK;
+  Readback local;
+  Readback &rb = extra ? *extra : local;
   std::vector<LpCounters> hc(def.count);
-  GP_CUDA(cudaMemcpyAsync(hc.data(), def.dev, sizeof(LpCounters) * def.count, cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  if (def.count) rb.add(hc.data(), def.dev, sizeof(LpCounters) * def.count);
+  GP_TRY(rb.run(s));
+  if (def.count == 0) return GP_OK;
   const int st = account_counters(hc.data(), def.count, def.visit_bytes.data(), def.entry_bytes.data(), nullptr, edges,
                                   moves);
   def.count = 0;

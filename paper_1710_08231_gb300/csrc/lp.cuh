@@ -38,9 +38,10 @@ struct LpDeferred {
   std::vector<int64_t> visit_bytes, entry_bytes;  // algorithmic bytes per visit and per entry, by job
 };
 size_t lp_counters_bytes();
-// Reads every deferred counter block back (one synchronisation), checks the device error flags and
-// returns the summed LP edges and admitted moves; adds the LP profile entries when profiling.
-int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves);
+// Reads every deferred counter block back (one synchronisation, shared with the caller's pending
+// reads in `extra` when given), checks the device error flags and returns the summed LP edges and
+// admitted moves; adds the LP profile entries when profiling.
+int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves, Readback *extra = nullptr);
 
 // One LP run for run_lp_multi. With vbase/lbase != 0 the job is one graph of a disjoint union:
 // g is its view (g.n local vertices, offsets and vertex weights shifted to its first vertex, adjacency

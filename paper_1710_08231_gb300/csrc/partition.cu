@@ -192,7 +192,8 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
   // of a kept vertex (the level-0 graph's max c(v))
   int64_t W = 0, maxc0 = 0;
   Stripped st;
-  GP_TRY(strip_isolated(g, &st, ws, s, &W, &maxc0));
+  std::vector<LpClassInfo> level_cls((size_t)p.max_levels + 1);
+  GP_TRY(strip_isolated(g, &st, ws, s, &W, &maxc0, &cfg, &level_cls[0]));
   const int64_t lmax = lmax_of(W, k, eps);
   res->lmax = lmax;
   res->n_isolated = st.n_iso;
@@ -211,7 +212,6 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     GP_TRY(ws.get(&buf, lp_counters_bytes() * (size_t)lpdef.capacity));
     lpdef.dev = buf;
   }
-  std::vector<LpClassInfo> level_cls((size_t)p.max_levels + 1);
   const double t_coarse0 = now_ms();
   if (st.n0 > 0) {
     const int64_t T = std::max<int64_t>(p.coarse_min, p.coarse_per_k * (int64_t)k);
@@ -347,15 +347,20 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
   GP_TRY(place_isolated(g, st, cur, k, part_out, s));
   int64_t *bw_final;
   GP_TRY(ws.get(&bw_final, (size_t)k));
-  int64_t cut = 0;
-  GP_TRY(eval_cut(g, part_out, k, &cut, bw_final, s));
+  // cut, block weights and the LP counters of the whole partition in one read back
+  unsigned long long *cut_acc;
+  GP_TRY(ws.get(&cut_acc, 1));
+  GP_TRY(eval_cut_launch(g, part_out, k, cut_acc, bw_final, s));
+  unsigned long long cut2 = 0;
   std::vector<int64_t> hbw(k);
-  GP_CUDA(cudaMemcpyAsync(hbw.data(), bw_final, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, s));
-  GP_CUDA(cudaStreamSynchronize(s));
+  Readback rb;
+  rb.add(&cut2, cut_acc, sizeof(cut2));
+  rb.add(hbw.data(), bw_final, sizeof(int64_t) * k);
+  GP_TRY(lp_collect(lpdef, s, &lp_edges, &lp_moves, &rb));
+  const int64_t cut = (int64_t)(cut2 / 2);
   res->cut = cut;
   res->max_block_weight = *std::max_element(hbw.begin(), hbw.end());
   res->imbalanced = res->max_block_weight > lmax ? 1 : 0;
-  GP_TRY(lp_collect(lpdef, s, &lp_edges, &lp_moves));
   res->lp_edges = lp_edges;
   res->lp_moves = lp_moves;
   if (learned) res->learned_cut = cut;
