@@ -266,9 +266,7 @@ struct Smem {
   long long tmp[32];
   long long tot;
   unsigned long long vis[8], edg[8];
-  unsigned hist[256];
-  unsigned long long base[256];
-  unsigned wcnt[kWarps][256];
+  unsigned wflag[kWarps];
   unsigned long long moves;   // admitted moves of the block in the current admission phase
   unsigned long long movers;  // proposals of the block over the whole call (statistics)
   long long carry;
@@ -1312,14 +1310,14 @@ __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi
     }
     if (lane == 31) {
       sm.sum[wid] = x;
-      sm.wcnt[wid][0] = (unsigned)f;
+      sm.wflag[wid] = (unsigned)f;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       long long run = sm.carry;
       for (int w = 0; w < kWarps; w++) {
         const long long s = sm.sum[w];
-        const int fl = (int)sm.wcnt[w][0];
+        const int fl = (int)sm.wflag[w];
         sm.sum[w] = run;  // carry into warp w
         run = fl ? s : run + s;
       }
@@ -1455,6 +1453,13 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCount
   unsigned *src = P.ct, *dst = P.ct2;
   unsigned long long *ks = P.ck, *kd = P.ck2;
   const int wid = threadIdx.x >> 5;
+  // radix workspace in the dynamic shared memory (the choice tables are idle during the contest):
+  // digit counts, per-digit output bases and per-warp digit counts
+  unsigned *const s_hist = reinterpret_cast<unsigned *>(dsm);
+  unsigned long long *const s_base = reinterpret_cast<unsigned long long *>(dsm + 256 * sizeof(unsigned));
+  unsigned (*const s_wcnt)[256] =
+      reinterpret_cast<unsigned (*)[256]>(dsm + 256 * (sizeof(unsigned) + sizeof(unsigned long long)));
+  static_assert(256 * (4 + 8) + kWarps * 256 * 4 <= (int)kDynSmem, "radix workspace fits the dynamic smem");
   if (packed) {
     for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) {
       const unsigned idx = src[p];
@@ -1475,12 +1480,12 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCount
       return packed ? (int)((ks[p] >> shift) & 255)
                     : (int)((field_key(P, src[p], field, maxg, maxq) >> shift) & 255);
     };
-    for (int t = threadIdx.x; t < 256; t += kThreads) sm.hist[t] = 0;
+    for (int t = threadIdx.x; t < 256; t += kThreads) s_hist[t] = 0;
     __syncthreads();
-    for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) atomicAdd(&sm.hist[digit(p)], 1u);
+    for (unsigned p = lo + threadIdx.x; p < hi; p += kThreads) atomicAdd(&s_hist[digit(p)], 1u);
     __syncthreads();
     // digit-major counts: hist[d * nb + block]
-    for (int t = threadIdx.x; t < 256; t += kThreads) P.hist[(size_t)t * nb + lb] = sm.hist[t];
+    for (int t = threadIdx.x; t < 256; t += kThreads) P.hist[(size_t)t * nb + lb] = s_hist[t];
     if (!grid_sync(bar)) return false;
     // one warp per digit scans the per-block counts (coalesced, 32 blocks per step)
     {
@@ -1509,7 +1514,7 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCount
       const long long tot = t < 256 ? (long long)P.hoff[(size_t)nb * 256 + t] : 0;
       const long long own = t < 256 ? (long long)P.hoff[(size_t)lb * 256 + t] : 0;
       const long long ex = block_excl_scan64(tot, sm.tmp, (long long *)nullptr);
-      if (t < 256) sm.base[t] = (unsigned long long)(ex + own);
+      if (t < 256) s_base[t] = (unsigned long long)(ex + own);
     }
     __syncthreads();
     for (unsigned t0 = lo; t0 < hi; t0 += kThreads) {
@@ -1518,24 +1523,24 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCount
       const unsigned x = valid ? src[p] : 0;
       const unsigned long long kx = (valid && packed) ? ks[p] : 0;
       const int dg = valid ? digit(p) : 256;
-      for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) sm.wcnt[k >> 8][k & 255] = 0;
+      for (int k = threadIdx.x; k < kWarps * 256; k += kThreads) s_wcnt[k >> 8][k & 255] = 0;
       __syncthreads();
       const unsigned peers = __match_any_sync(kFull, dg);
       const int rank = __popc(peers & lanemask_lt());
-      if (valid && rank == 0) sm.wcnt[wid][dg] = __popc(peers);
+      if (valid && rank == 0) s_wcnt[wid][dg] = __popc(peers);
       __syncthreads();
       if (valid) {
         unsigned pre = 0;
-        for (int w = 0; w < wid; w++) pre += sm.wcnt[w][dg];
-        const unsigned long long pos = sm.base[dg] + pre + rank;
+        for (int w = 0; w < wid; w++) pre += s_wcnt[w][dg];
+        const unsigned long long pos = s_base[dg] + pre + rank;
         dst[pos] = x;
         if (packed) kd[pos] = kx;
       }
       __syncthreads();
       if (threadIdx.x < 256) {
         unsigned s2 = 0;
-        for (int w = 0; w < kWarps; w++) s2 += sm.wcnt[w][threadIdx.x];
-        sm.base[threadIdx.x] += s2;
+        for (int w = 0; w < kWarps; w++) s2 += s_wcnt[w][threadIdx.x];
+        s_base[threadIdx.x] += s2;
       }
       __syncthreads();
     }
