@@ -96,6 +96,9 @@ struct LpProblem {
   const int32_t *q;
   uint8_t *act[2];
   int32_t *bin[kBins];
+  // lane-group bins 0-3 (d <= 32): beside each vertex its row, (row_begin << 6) | d, so that the
+  // choice loads the row and the vertex's own data in one step
+  unsigned long long *binx[4];
   int64_t bin_base[kBins];  // proposal slot of bin position i is bin_base[b] + i
   int32_t *mv_v, *mv_t;
   int32_t *mv_from;  // label an admitted mover left (its weight is moved in the next sub-round)
@@ -524,7 +527,12 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
       unsigned pos = 0;
       if (put && lane == leader) pos = atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
       pos = __shfl_sync(kFull, pos, leader);
-      if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
+      if (put) {
+        const unsigned at = s_base[b] + pos + __popc(peers & lanemask_lt());
+        P.bin[b][at] = (int32_t)v;
+        // (the row begin was loaded above; this load hits L1)
+        if (b < 4) P.binx[b][at] = ((unsigned long long)P.g.row_begin(v) << 6) | (unsigned long long)dd[it];
+      }
     }
     return;
   }
@@ -565,7 +573,11 @@ __device__ void phase_classify(const LpProblem &P, SubCounters &C, const SubCoun
     unsigned pos = 0;
     if (put && lane == leader) pos = atomicAdd(&s_cnt[b], (unsigned)__popc(peers));
     pos = __shfl_sync(kFull, pos, leader);
-    if (put) P.bin[b][s_base[b] + pos + __popc(peers & lanemask_lt())] = (int32_t)v;
+    if (put) {
+      const unsigned at = s_base[b] + pos + __popc(peers & lanemask_lt());
+      P.bin[b][at] = (int32_t)v;
+      if (b < 4) P.binx[b][at] = ((unsigned long long)P.g.row_begin(v) << 6) | (unsigned long long)d;
+    }
   }
 }
 
@@ -629,6 +641,7 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
     const unsigned gpw = 32u >> (2 + bin);
     const unsigned cnt = V.bin_count[bin];
     const int32_t *list = P.bin[bin];
+    const unsigned long long *listx = P.binx[bin];
     const int gl = lane & (G - 1);
     const unsigned sub = (unsigned)lane / (unsigned)G;
     const unsigned base = (j - pre[bin]) * gpw * U;
@@ -636,21 +649,26 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
     long long w[U], cv[U];
     int64_t beg[U], d[U];
     bool valid[U];
+    // the vertex and its row together, then its label and weight together with the adjacency
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const unsigned i = base + u * gpw + sub;
       valid[u] = i < cnt;
-      v[u] = valid[u] ? list[i] : 0;
-    }
-    #pragma unroll
-    for (int u = 0; u < U; u++) {
+      v[u] = 0;
       beg[u] = 0;
       d[u] = 0;
+      if (valid[u]) {
+        v[u] = list[i];
+        const unsigned long long x = listx[i];
+        beg[u] = (int64_t)(x >> 6);
+        d[u] = (int64_t)(x & 63);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
       L0[u] = -2;
       cv[u] = 0;
       if (valid[u]) {
-        beg[u] = P.g.row_begin(v[u]);
-        d[u] = P.g.row_begin(v[u] + 1) - beg[u];
         L0[u] = P.labels[P.vbase + v[u]];
         cv[u] = P.g.vweight(v[u]);
       }
@@ -2220,6 +2238,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     int64_t slots_total = 0;
     for (int b = 0; b < kBins; b++) {
       GP_TRY(ws.get(&P.bin[b], (size_t)std::max<unsigned>(hcls[9 * j + b], 1)));
+      if (b < 4) GP_TRY(ws.get(&P.binx[b], (size_t)std::max<unsigned>(hcls[9 * j + b], 1)));
       P.bin_base[b] = slots_total;
       slots_total += hcls[9 * j + b];
     }
