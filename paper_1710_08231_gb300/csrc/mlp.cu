@@ -56,51 +56,75 @@ __global__ void k_wdeg(DGraph g, float *wdeg) {
   }
 }
 
-// One warp per vertex v; each lane owns one entry (v,u) of a 32-entry step. The shared-neighbour
-// count of every entry is computed by the whole warp: lanes take the first 64 neighbours of u and
-// binary-search them in v's first 64 neighbours (kept in shared memory).
+// One half-warp (16 lanes) per vertex v; each lane owns one entry (v,u) of a 16-entry step. The
+// shared-neighbour count of an entry: its lane takes the first 64 neighbours of u and looks each up
+// in a set of v's first 64 neighbours (an open-addressing table of 128 slots in shared memory for the
+// half-warp, slot mix32(x) mod 128, linear probing).
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_features(DGraph g, int level, const float *wdeg, float *fout, unsigned *bout) {
-  __shared__ int nv_s[8][64];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int *nv = nv_s[wid];
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+__global__ void __launch_bounds__(256, 6) k_features(DGraph g, int level, const float *wdeg, float *fout, unsigned *bout) {
+  constexpr int kH = 16;     // lanes per vertex
+  constexpr int kTab = 128;  // set slots (at most 64 keys)
+  __shared__ int tab_s[8][2][kTab];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane / kH, hl = lane % kH;
+  const unsigned hmask = 0xFFFFu << (kH * half);
+  int *tab = tab_s[wid][half];
+  const int64_t gh = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kH;
+  const int64_t nh = ((int64_t)gridDim.x * blockDim.x) / kH;
   const float flevel = (float)level / 16.0f;
-  for (int64_t v = gw; v < g.n; v += nw) {
+  for (int64_t v = gh; v < g.n; v += nh) {
     const int64_t beg = g.row_begin(v), end = g.row_begin(v + 1);
     const int64_t dv = end - beg;
     if (dv == 0) continue;
     const int lenv = (int)gp_min64(dv, 64);
-    __syncwarp();
-    if (lane < lenv) nv[lane] = g.adj[beg + lane];
-    if (lane + 32 < lenv) nv[lane + 32] = g.adj[beg + lane + 32];
-    __syncwarp();
+    __syncwarp(hmask);
+    for (int t = hl; t < kTab; t += kH) tab[t] = -1;
+    __syncwarp(hmask);
+    for (int t = hl; t < lenv; t += kH) {
+      const int x = g.adj[beg + t];
+      unsigned sl = mix32((unsigned)x) & (kTab - 1);
+      while (atomicCAS(&tab[sl], -1, x) != -1) sl = (sl + 1) & (kTab - 1);  // ids in a row are distinct
+    }
+    __syncwarp(hmask);
     const float cv = (float)g.vweight(v);
     const float wv = wdeg[v];
-    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+    for (int64_t e0 = beg; e0 < end; e0 += kH) {
       // lane j takes entry e0 + j: it walks the first (up to) 64 neighbours of u and looks each up in
-      // the first 64 neighbours of v (sorted, in shared memory)
-      const int64_t e = e0 + lane;
+      // the set of v's first 64 neighbours
+      const int64_t e = e0 + hl;
       const bool has = e < end;
       const int u = has ? g.adj[e] : 0;
       const int64_t bu = has ? g.row_begin(u) : 0;
-      const int lenu = has ? (int)gp_min64(g.row_begin(u + 1) - bu, 64) : 0;
+      const int64_t eu = has ? g.row_begin(u + 1) : 0;
+      const int lenu = (int)gp_min64(eu - bu, 64);
+      // u's weight, its weighted degree and the entry's weight are loaded before the search
+      const float cu = has ? (float)g.vweight(u) : 0.0f;
+      const float wu = has ? wdeg[u] : 0.0f;
+      const float w = has ? (float)g.eweight(e) : 0.0f;
       int mine = 0;
-      for (int kk = 0; kk < lenu; kk++) {
-        const int x = g.adj[bu + kk];
-        int lo = 0, hi = lenv;
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (nv[mid] < x) lo = mid + 1;
-          else hi = mid;
+      // eight of u's neighbours are loaded before any is searched (independent loads in flight)
+      constexpr int kBatch = 8;
+      for (int k0 = 0; k0 < lenu; k0 += kBatch) {
+        int xs[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; q++) xs[q] = k0 + q < lenu ? __ldg(g.adj + bu + k0 + q) : 0;
+#pragma unroll
+        for (int q = 0; q < kBatch; q++) {
+          if (k0 + q >= lenu) break;
+          const int x = xs[q];
+          unsigned sl = mix32((unsigned)x) & (kTab - 1);
+          while (true) {
+            const int k = tab[sl];
+            if (k == x) {
+              mine++;
+              break;
+            }
+            if (k == -1) break;
+            sl = (sl + 1) & (kTab - 1);
+          }
         }
-        mine += (lo < lenv && nv[lo] == x) ? 1 : 0;
       }
       if (!has) continue;
-      const float du = (float)(g.row_begin(u + 1) - g.row_begin(u));
-      const float cu = (float)g.vweight(u);
-      const float w = (float)g.eweight(e);
+      const float du = (float)(eu - bu);
       const float dvf = (float)dv;
       float f[kIn];
       f[0] = log2f(1.0f + fminf(dvf, du));
@@ -109,7 +133,7 @@ __global__ void __launch_bounds__(256) k_features(DGraph g, int level, const flo
       f[3] = log2f(1.0f + fminf(cv, cu));
       f[4] = log2f(1.0f + fmaxf(cv, cu));
       f[5] = (float)mine / 64.0f;
-      f[6] = w / fmaxf(wv, wdeg[u]);
+      f[6] = w / fmaxf(wv, wu);
       f[7] = flevel;
       if (BF16) {
 #pragma unroll
@@ -320,8 +344,8 @@ int features(const DGraph &g, int level, float *fout, unsigned *bout, cudaStream
   (::gp::count_launch(), k_wdeg<<<grid_for(g.n * 32, 256, nsm * 8), 256, 0, s>>>(g, wdeg));
   {
     ProfScope ps("mlp_features", s);
-    if (bout) (::gp::count_launch(), k_features<true><<<grid_for(g.n * 32, 256, nsm * 8), 256, 0, s>>>(g, level, wdeg, nullptr, bout));
-    else (::gp::count_launch(), k_features<false><<<grid_for(g.n * 32, 256, nsm * 8), 256, 0, s>>>(g, level, wdeg, fout, nullptr));
+    if (bout) (::gp::count_launch(), k_features<true><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, nullptr, bout));
+    else (::gp::count_launch(), k_features<false><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, fout, nullptr));
   }
   GP_LAUNCH_CHECK();
   return GP_OK;
