@@ -13,6 +13,7 @@
 // so the coarse CSR is canonical and independent of scheduling.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "contract.cuh"
 #include "lp.cuh"
@@ -215,12 +216,20 @@ __device__ __forceinline__ unsigned row_slot(int cu) { return mix32((unsigned)cu
 // members at a time, 64 entries per step (all lanes busy whatever the members' degrees, adjacency
 // read contiguously); equal coarse neighbours of one step are combined in the warp before they touch
 // the table.
+// Table values: 32-bit counts with unit edge weights (a coarse entry counts at most the fine entries,
+// fewer than 2^32), else 64-bit sums.
+template <int EW>
+using RowVal = typename std::conditional<EW == 0, unsigned, unsigned long long>::type;
+template <int EW>
+constexpr int row_slot_bytes() { return 4 + (int)sizeof(RowVal<EW>); }
+
 template <int EW, int S>
 __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
+  using V = RowVal<EW>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwb = blockDim.x >> 5;
-  long long *vals = reinterpret_cast<long long *>(smem) + wid * S;
-  int *keys = reinterpret_cast<int *>(smem + nwb * S * 8) + wid * S;
+  V *vals = reinterpret_cast<V *>(smem) + wid * S;
+  int *keys = reinterpret_cast<int *>(smem + (size_t)nwb * S * sizeof(V)) + wid * S;
   for (int t = lane; t < S; t += 32) {
     keys[t] = -1;
     vals[t] = 0;
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
           while (true) {
             const int k = atomicCAS(&keys[sl], -1, cu[h]);
             if (k == -1 || k == cu[h]) {
-              atomicAdd(reinterpret_cast<unsigned long long *>(&vals[sl]), (unsigned long long)sum);
+              atomicAdd(&vals[sl], (V)sum);
               break;
             }
             sl = (sl + 1) & mask;
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
     int u = 0;
     for (int c0 = 0; c0 < cap; c0 += 32) {
       const int k = keys[c0 + lane];
-      const long long val = vals[c0 + lane];
+      const V val = vals[c0 + lane];
       const unsigned hm = __ballot_sync(kFull, k >= 0);
       __syncwarp();
       if (k >= 0) {
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
           if ((x > y) == up && x != y) {
             keys[lo] = y;
             keys[hi] = x;
-            const long long vx = vals[lo];
+            const V vx = vals[lo];
             vals[lo] = vals[hi];
             vals[hi] = vx;
           }
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kRowThreads) k_row_whash(RowArgs a) {
     const int64_t dst = a.tstart[cv];
     for (int t = lane; t < u; t += 32) {
       a.okey[dst + t] = keys[t];
-      a.oval[dst + t] = vals[t];
+      a.oval[dst + t] = (int64_t)vals[t];
     }
     if (lane == 0) a.rowcnt[cv] = u;
     __syncwarp();
@@ -552,18 +561,18 @@ int build_rows(RowArgs a, const unsigned *counts_dev, const unsigned counts[5], 
     RowArgs b = a;
     b.list = lists[3];
     b.count = counts_dev + 3;
-    const int sm = (kRowThreads / 32) * kWarpSlots * 12;
+    const int sm = (kRowThreads / 32) * kWarpSlots * row_slot_bytes<EW>();
     set_smem(k_row_whash<EW, kWarpSlots>, sm);
-    (::gp::count_launch(), k_row_whash<EW, kWarpSlots><<<grid_for(counts[3], 8, nsm * 4), kRowThreads, sm, s>>>(b));
+    (::gp::count_launch(), k_row_whash<EW, kWarpSlots><<<grid_for(counts[3], 8, nsm * (EW == 0 ? 6 : 4)), kRowThreads, sm, s>>>(b));
   }
   if (counts[4]) {
     RowArgs b = a;
     b.list = lists[4];
     b.count = counts_dev + 4;
     constexpr int kBigSlots = 2 * kRowWarpBig;
-    const int sm = 4 * kBigSlots * 12;  // 4 warps per CTA
+    const int sm = 4 * kBigSlots * row_slot_bytes<EW>();  // 4 warps per CTA
     set_smem(k_row_whash<EW, kBigSlots>, sm);
-    (::gp::count_launch(), k_row_whash<EW, kBigSlots><<<grid_for(counts[4], 4, nsm * 2), 128, sm, s>>>(b));
+    (::gp::count_launch(), k_row_whash<EW, kBigSlots><<<grid_for(counts[4], 4, nsm * (EW == 0 ? 3 : 2)), 128, sm, s>>>(b));
   }
   if (counts[1]) {
     RowArgs b = a;
