@@ -1081,22 +1081,43 @@ __device__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, 
       }
     }
     c0 = block_sum_of(c0, sm);  // also completes the shared table
-    for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
-      const int L = skeys[t];
-      if (L < 0) continue;
-      uint64_t sg = hub_slot(L, cap);
-      while (true) {
-        const int k = atomicCAS(&P.hub_keys[tb + sg], -1, L);
-        if (k == -1 || k == L) {
-          atomicAdd(&P.hub_vals[tb + sg], svals[t]);
-          if (LQ) atomicAdd(&P.hub_qv[tb + sg], sq[t]);
-          break;
-        }
-        sg = sg + 1 == cap ? 0 : sg + 1;
+    // flush into the hub's table: each thread claims the slots of four of its labels at once (the
+    // claims are in flight together), then retries the ones that met another label
+    static_assert(kCtaCap % (4 * kThreads) == 0, "the flush takes four table slots per thread per step");
+    for (int t0 = threadIdx.x; t0 < kCtaCap; t0 += 4 * kThreads) {
+      int Ls[4];
+      uint64_t sg[4];
+      bool pend[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        Ls[q] = skeys[t0 + q * kThreads];
+        pend[q] = Ls[q] >= 0;
+        sg[q] = pend[q] ? hub_slot(Ls[q], cap) : 0;
       }
-      skeys[t] = -1;
-      svals[t] = 0;
-      if (LQ) sq[t] = 0;
+      while (pend[0] || pend[1] || pend[2] || pend[3]) {
+        int ks[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) ks[q] = pend[q] ? atomicCAS(&P.hub_keys[tb + sg[q]], -1, Ls[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (!pend[q]) continue;
+          if (ks[q] == -1 || ks[q] == Ls[q]) {
+            const int t = t0 + q * kThreads;
+            atomicAdd(&P.hub_vals[tb + sg[q]], svals[t]);
+            if (LQ) atomicAdd(&P.hub_qv[tb + sg[q]], sq[t]);
+            pend[q] = false;
+          } else {
+            sg[q] = sg[q] + 1 == cap ? 0 : sg[q] + 1;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int t = t0 + q * kThreads;
+        skeys[t] = -1;
+        svals[t] = 0;
+        if (LQ) sq[t] = 0;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
