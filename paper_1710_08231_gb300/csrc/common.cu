@@ -202,8 +202,9 @@ __global__ void k_scan_tops(int64_t *block_tot, int64_t nb, int64_t *total_dev) 
   if (threadIdx.x == 0 && total_dev) *total_dev = carry;
 }
 
+// block_off NULL: a single tile (one block), whose total goes to *total_dev (may be NULL).
 template <class In, class Out>
-__global__ void k_scan_final(const In *in, Out *out, int64_t n, const int64_t *block_off) {
+__global__ void k_scan_final(const In *in, Out *out, int64_t n, const int64_t *block_off, int64_t *total_dev) {
   __shared__ int64_t tmp[32];
   __shared__ int64_t tot;
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -214,7 +215,8 @@ __global__ void k_scan_final(const In *in, Out *out, int64_t n, const int64_t *b
     vals[k] = i < n ? in[i] : (In)0;
     s += (int64_t)vals[k];
   }
-  int64_t run = block_excl_scan64(s, tmp, &tot) + block_off[blockIdx.x];
+  int64_t run = block_excl_scan64(s, tmp, &tot) + (block_off ? block_off[blockIdx.x] : 0);
+  if (!block_off && total_dev && threadIdx.x == 0) *total_dev = tot;
   for (int k = 0; k < kScanItems; k++) {
     const int64_t i = base + (int64_t)threadIdx.x * kScanItems + k;
     if (i < n) out[i] = (Out)run;
@@ -230,11 +232,17 @@ int scan_impl(const In *in, Out *out, int64_t n, int64_t *total_dev, Workspace &
     return GP_OK;
   }
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    // one tile: one launch
+    (::gp::count_launch(), k_scan_final<In, Out><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total_dev));
+    GP_LAUNCH_CHECK();
+    return GP_OK;
+  }
   int64_t *bt;
   GP_TRY(ws.get(&bt, (size_t)nb));
   (::gp::count_launch(), k_scan_reduce<In><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, bt));
   (::gp::count_launch(), k_scan_tops<<<1, 1024, 0, s>>>(bt, nb, total_dev));
-  (::gp::count_launch(), k_scan_final<In, Out><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bt));
+  (::gp::count_launch(), k_scan_final<In, Out><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, bt, nullptr));
   GP_LAUNCH_CHECK();
   return GP_OK;
 }

@@ -1845,8 +1845,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, cons
 // ------------------------------------------------------------------------------------ host helpers
 // Degree classes and CSR entries of every job of a launch: counts[9 j + bin] vertices per bin and
 // counts64[j] entries. Vertex x of the concatenation belongs to the job j with pre[j] <= x < pre[j+1].
+// With at most kClsSmemJobs jobs the counts add up in shared memory first (one global atomic per
+// block and counter instead of one per warp: the counters of a job share a cache line).
+constexpr int kClsSmemJobs = 16;
+
 __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs, int deg_warp, int deg_cta,
                                  unsigned *counts, unsigned long long *entries, unsigned long long *hubstat) {
+  __shared__ unsigned s_counts[9 * kClsSmemJobs];
+  __shared__ unsigned long long s_entries[kClsSmemJobs], s_hub[2 * kClsSmemJobs];
+  const bool local = njobs <= kClsSmemJobs;
+  if (local) {
+    for (int t = threadIdx.x; t < 9 * kClsSmemJobs; t += blockDim.x) s_counts[t] = 0;
+    for (int t = threadIdx.x; t < kClsSmemJobs; t += blockDim.x) s_entries[t] = 0;
+    for (int t = threadIdx.x; t < 2 * kClsSmemJobs; t += blockDim.x) s_hub[t] = 0;
+    __syncthreads();
+  }
+  unsigned *cnt_out = local ? s_counts : counts;
+  unsigned long long *ent_out = local ? s_entries : entries, *hub_out = local ? s_hub : hubstat;
   const int64_t total = pre[njobs];
   const int lane = threadIdx.x & 31;
   for (int64_t x0 = blockIdx.x * (int64_t)blockDim.x; x0 < total; x0 += (int64_t)gridDim.x * blockDim.x) {
@@ -1868,15 +1883,27 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
     }
     // one atomic per distinct (job, bin) and per distinct job in the warp
     const unsigned pk = __match_any_sync(kFull, (j << 3) | (bin & 7));
-    if (bin >= 0 && lane == __ffs(pk) - 1) atomicAdd(&counts[9 * j + bin], (unsigned)__popc(pk));
+    if (bin >= 0 && lane == __ffs(pk) - 1) atomicAdd(&cnt_out[9 * j + bin], (unsigned)__popc(pk));
     const unsigned pj = __match_any_sync(kFull, j);
-    unsigned long long dsum = 0;
-    for (unsigned m = pj; m; m &= m - 1) dsum += (unsigned long long)__shfl_sync(pj, d, __ffs(m) - 1);
-    if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&entries[j], dsum);
+    // (at most 32 degrees of one graph: below 2^32, as a graph has at most 2^31 entries)
+    const unsigned long long dsum = __reduce_add_sync(pj, (unsigned)d);
+    if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&ent_out[j], dsum);
     if (bin == 6) {  // hub: table slots hub_cap(d); per job the largest table and their sum
       const unsigned long long cap = (unsigned long long)hub_cap(d);
-      atomicMax(&hubstat[2 * j], cap);
-      atomicAdd(&hubstat[2 * j + 1], cap);
+      atomicMax(&hub_out[2 * j], cap);
+      atomicAdd(&hub_out[2 * j + 1], cap);
+    }
+  }
+  if (local) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 9 * njobs; t += blockDim.x)
+      if (s_counts[t]) atomicAdd(&counts[t], s_counts[t]);
+    for (int t = threadIdx.x; t < njobs; t += blockDim.x)
+      if (s_entries[t]) atomicAdd(&entries[t], s_entries[t]);
+    for (int t = threadIdx.x; t < 2 * njobs; t += blockDim.x) {
+      if (!s_hub[t]) continue;
+      if (t & 1) atomicAdd(&hubstat[t], s_hub[t]);
+      else atomicMax(&hubstat[t], s_hub[t]);
     }
   }
 }
