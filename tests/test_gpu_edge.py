@@ -138,3 +138,32 @@ def test_empty_and_single_vertex(gp):
     one = gg.Graph(1, np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32))
     part, res = gp.partition(gp.DeviceGraph.from_host(one), 1, 0.03, 1)
     assert part.cpu().numpy().tolist() == [0] and res.cut == 0 and res.n_isolated == 1
+
+
+def test_choice_key_tie_takes_the_exact_order(gp):
+    """With unit weights the lane-group choice first ranks candidates by the 32-bit key
+    (count, top 26 bits of H(seed, v, L)) and falls back to the full order (H, then L) when two
+    candidates of one vertex have equal keys. Vertex v here has exactly two neighbours whose labels
+    collide in those 26 bits; its choice, and the whole clustering, must still be the oracle's."""
+    seed = 4242
+    smix = O.mix64(seed)
+    rmix0 = O.mix64(smix ^ 0)  # round 0
+    # v is active in sub-round 0 of round 0, when every neighbour still carries its own label
+    v = next(x for x in range(1, 4096) if (O.mix64(rmix0 ^ x) >> 63) == 0)
+    hv = O.mix64(smix ^ v)
+    seen, pair = {}, None
+    for L in range(v + 1, v + (1 << 17)):
+        key = O.mix64(hv ^ L) >> 38
+        if key in seen:
+            pair = (seen[key], L)
+            break
+        seen[key] = L
+    assert pair is not None
+    l1, l2 = pair
+    assert O.mix64(hv ^ l1) != O.mix64(hv ^ l2)  # equal keys, different full hashes
+    g = from_edges(l2 + 1, [(v, l1), (v, l2)], name="key_tie")
+    dg = gp.DeviceGraph.from_host(g)
+    lab, st = gp.lp_cluster(dg, 8, 4, seed)
+    lab_o, _, st_o = O.lp_cluster(g, 8, 4, seed)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    _stats_eq(st, st_o)
