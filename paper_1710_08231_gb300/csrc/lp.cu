@@ -721,6 +721,12 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
 #pragma unroll
     for (int u = 0; u < U; u++) {
       Best b = no_best();
+      if (!__any_sync(kFull, cand[u])) {
+        // no lane of the warp has a candidate (every vertex keeps its label, the common case once
+        // clusters or blocks settle): only the empty proposals are recorded
+        if (valid[u] && gl == 0) P.mv_t[P.bin_base[bin] + base + u * gpw + sub] = -1;
+        continue;
+      }
       if constexpr (EW == 0 && !LQ) {
         // first the 32-bit key conn << 26 | h >> 38 (maximum over the group with one shuffle per
         // level); a unique maximum is the exact winner. Equal keys in some group (equal counts and
