@@ -840,13 +840,20 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
     const unsigned mask = (unsigned)cap - 1;
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
+    bool other = false;  // some neighbour carries another label
     for (int64_t e0 = beg; e0 < end; e0 += 32) {
       const int64_t e = e0 + lane;
       const bool in = e < end;
       const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
       const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
       if (in && L == L0) c0 += w;
+      other |= in && L != L0;
       warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
+    }
+    if (!__any_sync(kFull, other)) {
+      // every neighbour carries the own label: no candidate, the table is still empty
+      if (lane == 0) P.mv_t[P.bin_base[4] + i] = -1;
+      continue;
     }
     c0 = warp_sum64(c0);
     __syncwarp();
