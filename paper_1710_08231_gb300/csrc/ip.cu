@@ -589,11 +589,8 @@ int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_
   for (const IpGraph &G : hg) max_ns = std::max<int64_t>(max_ns, G.ns);
   a.smem_ns = max_ns <= kIpSmemMaxNs ? max_ns : 0;
   const size_t dsm = a.smem_ns > 0 ? ip_smem_bytes(a.smem_ns) : 0;
-  static bool attr_set = false;
-  if (!attr_set) {
+  if (dsm > 0)  // (per call: the attribute belongs to the current device)
     GP_CUDA(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ip_smem_bytes(kIpSmemMaxNs)));
-    attr_set = true;
-  }
   (::gp::count_launch(), k_bisect<<<grid, kIpThreads, dsm, s>>>(a));
   GP_LAUNCH_CHECK();
   (::gp::count_launch(), k_repair<<<grid, kIpThreads, 0, s>>>(a));

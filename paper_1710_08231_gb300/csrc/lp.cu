@@ -309,7 +309,8 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
 // vertex v to target T was admitted): new label, the left label recorded for the weight update of the
 // next sub-round, neighbours marked active for the next round. Movers of degree above kBigDeg are
 // listed in P.big instead (counter C.n_big); every block marks their neighbours after the phase.
-// Returns the warp's admitted count.
+// act_next NULL (the last round: no round reads the marks) skips the marking. Returns the warp's
+// admitted count.
 // This form takes the mover's current label L0 and its row (rb, deg) already loaded.
 __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCounters &C, uint8_t *act_next, bool adm,
                                                      int64_t idx, int v, int T, int L0, int64_t rb, int64_t deg) {
@@ -323,6 +324,7 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   }
   const unsigned am = __ballot_sync(kFull, adm);
   if (!am) return 0;
+  if (!act_next) return (unsigned)__popc(am);
   const bool big = adm && deg > kBigDeg;
   if (__any_sync(kFull, big)) {
     // one marking item per kBigChunk entries; the warp reserves all of its items with one atomic
@@ -1250,7 +1252,7 @@ __device__ void phase_admit(const LpProblem &P, SubCounters &C, const SubCounter
   const unsigned na = M.total();
   unsigned long long mg = 0, mq = 0;
   unsigned movers = 0, moved = 0;
-  uint8_t *act_next = P.act[(r + 1) & 1];
+  uint8_t *act_next = r + 1 < P.rounds ? P.act[(r + 1) & 1] : nullptr;  // (no marks in the last round)
   for (unsigned base = (unsigned)lb * kThreads; base < na; base += (unsigned)nb * kThreads) {
     const unsigned k = base + threadIdx.x;
     bool contested = false, adm = false;
@@ -1325,7 +1327,7 @@ __device__ __forceinline__ bool mover_less(const LpProblem &P, unsigned x, unsig
 template <class At>
 __device__ void admit_sorted(const LpProblem &P, At at, unsigned lo, unsigned hi, long long carry_in,
                              int carry_target, int r, SubCounters *Cg, Smem &sm) {
-  uint8_t *act_next = P.act[(r + 1) & 1];
+  uint8_t *act_next = r + 1 < P.rounds ? P.act[(r + 1) & 1] : nullptr;  // (no marks in the last round)
   unsigned moved = 0;
   if (threadIdx.x == 0) {
     sm.carry = carry_in;
