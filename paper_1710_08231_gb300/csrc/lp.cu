@@ -755,7 +755,8 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
       }
       const bool mover = valid[u] && gl == 0 && b.L >= 0;
       if (valid[u] && gl == 0) write_slot<LQ>(P, P.bin_base[bin] + base + u * gpw + sub, v[u], b, c0[u]);
-      warp_add_by_key(P.demand, mover, b.L, cv[u]);
+      // (at most one mover per group: equal targets within a warp are rare, so no aggregation)
+      if (mover) atomicAdd(reinterpret_cast<unsigned long long *>(&P.demand[b.L]), (unsigned long long)cv[u]);
     }
   }
 }
