@@ -324,10 +324,12 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     int32_t *bufA, *bufB;
     GP_TRY(ws.get(&bufA, (size_t)st.n0));
     GP_TRY(ws.get(&bufB, (size_t)st.n0));
+    // projection keeps every block's weight (a coarse vertex weighs what its members weigh), so the
+    // block weights an LP refinement ends with are those the next finer level starts with
+    GP_CUDA(cudaMemcpyAsync(bw, bws + (size_t)best * k, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToDevice, s));
     for (int l = levels - 1; l >= 0; l--) {
       int32_t *fine = (cur == bufA) ? bufB : bufA;
       GP_TRY(project(cur, f2c[l], G[l].n, fine, s));
-      GP_TRY(block_weights(G[l], fine, k, bw, nullptr, s));
       GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), nullptr, s, cfg,
                     false, &level_cls[l], &lpdef));
       cur = fine;
