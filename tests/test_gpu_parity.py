@@ -77,6 +77,26 @@ def test_lp_cluster_learned_scores_match_oracle(gp, name):
     _stats_eq(st, st_o)
 
 
+@pytest.mark.parametrize("name", ["rgg15", "rmat13"])
+@pytest.mark.parametrize("bits", [15, 20])
+def test_lp_cluster_score_ranges_match_oracle(gp, name, bits):
+    """Scores up to 2^15 (the scorer's range) take the packed-key choice with unit weights; wider
+    scores take the general reduction. Both must equal the oracle."""
+    import torch
+    g = GRAPHS[name]
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    key = np.minimum(src, g.adj).astype(np.int64) * g.n + np.maximum(src, g.adj)
+    mask = (1 << bits) - 1
+    q = (np.vectorize(lambda x: O.mix64(int(x) ^ 0x5A5A) & mask, otypes=[np.int64])(key)).astype(np.int32)
+    if bits == 15:
+        q[::7] = 1 << 15  # the top of the scorer's range
+    dg = gp.DeviceGraph.from_host(g)
+    lab, st = gp.lp_cluster(dg, 60, 10, 17, q=torch.from_numpy(q).cuda())
+    lab_o, _, st_o = O.lp_cluster(g, 60, 10, 17, q=q)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    _stats_eq(st, st_o)
+
+
 @pytest.mark.parametrize("name", ["grid256", "rgg15", "rmat13", "rmat12w", "rgg_vw"])
 @pytest.mark.parametrize("k", [2, 16])
 def test_lp_refine_matches_oracle(gp, name, k):
