@@ -2279,6 +2279,14 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   GP_TRY(ws.zeros(&bar_all, (size_t)njobs * kBarrierStride));
   unsigned *binres_all;
   GP_TRY(ws.zeros(&binres_all, (size_t)njobs * 3 * 256));
+  // every job's demand array in one zeroed allocation (one memset for the launch, not one per job)
+  int64_t *demand_all;
+  {
+    size_t total = 0;
+    for (int j = 0; j < njobs; j++) total += (size_t)std::max<int64_t>(jobs[j].nl, 1);
+    GP_TRY(ws.zeros(&demand_all, total));
+  }
+  size_t demand_off = 0;
   for (int j = 0; j < njobs; j++) {
     const LpJob &jb = jobs[j];
     LpProblem &P = hp[j];
@@ -2313,8 +2321,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.mv_q, n));
     GP_TRY(ws.get(&P.mv_adm, n));
     GP_TRY(ws.get(&P.mv_of_v, n));
-    GP_TRY(ws.zeros(&P.demand, (size_t)std::max<int64_t>(jb.nl, 1)));
-    P.demand -= jb.lbase;  // indexed by global label
+    P.demand = demand_all + demand_off - jb.lbase;  // indexed by global label
+    demand_off += (size_t)std::max<int64_t>(jb.nl, 1);
     GP_TRY(ws.get(&P.ct, n));
     GP_TRY(ws.get(&P.ct2, n));
     GP_TRY(ws.get(&P.ck, n));
