@@ -12,7 +12,8 @@
 //     the schedule;
 //   * one cooperative launch runs every round of an LP call. The blocks of a "problem" (one LP run;
 //     several independent runs can share a launch) meet at bounded barriers between the phases of a
-//     sub-round: classify -> aggregate+choose -> admission -> apply;
+//     sub-round: classify -> aggregate+choose -> admission with apply (-> contest when a target's
+//     proposals do not all fit);
 //   * active vertices are binned by degree: groups of 4/8/16/32 lanes (labels aggregated with
 //     __match_any_sync), one warp with a shared-memory hash table, one CTA with a shared-memory hash
 //     table, or several CTAs with a global-memory hash table for hubs;
@@ -1708,7 +1709,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       tmark = now;
     }
   };
-  // block-local copies of the sub-round counters (thread 0 reads them once after a barrier)
+  // block-local copies of the sub-round counters (read once after a barrier)
   __shared__ SubCounters sV, sVp;
   // (one 32-bit word per thread, all loads in flight together; the bin counts come from binres)
   static_assert(offsetof(SubCounters, bin_count) == 0, "bin counts lead the counters");
@@ -2186,7 +2187,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       ci->hub_cap_sum = hhub[2 * (size_t)j + 1];
     }
   }
-  // Blocks: a job gets at most one block per 256 vertices. When all jobs fit the co-resident
+  // Blocks: a job gets at most one block per kVertsPerBlock vertices. When all jobs fit the co-resident
   // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
   // + a fixed per-problem latency term): jobs above twice the mean block load get several blocks,
   // the rest run one block each, packed onto the remaining blocks longest first.
