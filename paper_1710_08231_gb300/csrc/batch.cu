@@ -609,18 +609,22 @@ int partition_batch_device(const gp_batch_item *items, int count, const gp_param
   GP_LAUNCH_CHECK();
   const double t_r0 = now_ms_b();
   // ---- uncoarsening: project everything, refine the graphs whose own level this is
+  // Block weights per graph: the best try's, then each refinement's final label weights. Projection
+  // keeps every block's weight, so they are never recomputed on the way up.
   int64_t *d_bwoff, *lbw;
   GP_TRY(to_device(ws, bwoff, &d_bwoff, s));
-  GP_TRY(ws.get(&lbw, (size_t)std::max<int64_t>(bwoff[count], 1)));
+  {
+    std::vector<int64_t> h((size_t)std::max<int64_t>(bwoff[count], 1), 0);
+    for (int i = 0; i < count; i++)
+      for (int b = 0; b < items[i].k; b++)
+        h[bwoff[i] + b] = htbw[(size_t)bwoff[i] * tries + (size_t)best[i] * items[i].k + b];
+    GP_TRY(to_device(ws, h, &lbw, s));
+  }
   for (int l = L - 1; l >= 0; l--) {
     const DGraph &gl = G[l];
     const std::vector<int64_t> &vbl = VB[l];
     GP_TRY(project(cur, f2c[l], gl.n, nxt, s));
     std::swap(cur, nxt);
-    GP_CUDA(cudaMemcpyAsync(d_vbl, vbl.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
-    GP_CUDA(cudaMemsetAsync(lbw, 0, sizeof(int64_t) * (size_t)bwoff[count], s));
-    (::gp::count_launch(), k_union_eval<<<gridn(gl.n), 256, 0, s>>>(gl, d_vbl, count, cur, d_bwoff, lbw, nullptr));
-    GP_LAUNCH_CHECK();
     std::vector<LpJob> uj;
     std::vector<gp_lp_stats> ustats(count);
     std::vector<int> ug;
@@ -652,10 +656,7 @@ int partition_batch_device(const gp_batch_item *items, int count, const gp_param
   int32_t *fullp;
   GP_TRY(ws.get(&fullp, (size_t)std::max<int64_t>(N, 1)));
   if (st.n_iso > 0) {
-    // block weights of the kept vertices per graph
-    GP_CUDA(cudaMemcpyAsync(d_vbl, vb0.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
-    GP_CUDA(cudaMemsetAsync(lbw, 0, sizeof(int64_t) * (size_t)bwoff[count], s));
-    if (st.n0 > 0) (::gp::count_launch(), k_union_eval<<<gridn(st.n0), 256, 0, s>>>(st.g0, d_vbl, count, cur, d_bwoff, lbw, nullptr));
+    // (lbw holds the block weights of the kept vertices per graph)
     int *d_k;
     GP_TRY(to_device(ws, kint, &d_k, s));
     if (!any_vw)
