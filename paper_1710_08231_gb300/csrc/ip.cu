@@ -57,6 +57,7 @@ struct IpArgs {
   uint8_t *flag;
   int64_t smem_ns;           // > 0: the bisection keeps part, gk, dist and both BFS queues of every try
                              // in dynamic shared memory (every graph of the launch has ns <= smem_ns)
+  int smem_sort;             // with smem_ns: the sort's key and value arrays are in shared memory too
   long long *gws;            // k-sized scratch arrays
   unsigned long long *gminh;
   int *gstart;
@@ -95,11 +96,16 @@ __device__ void set_bfs(const DGraph &g, int64_t vbase, int32_t *part, int32_t *
   }
 }
 
-// Per-vertex state of a bisection in shared memory: 5 arrays of ns int32 (part, gk, dist, qa, qb).
+// Per-vertex state of a bisection in shared memory: 5 arrays of ns int32 (part, gk, dist, qa, qb), and
+// for ns <= kIpSmemSortNs also the sort's keys and values (2 x ns uint64 + 2 x ns int32) after them.
 constexpr int64_t kIpSmemMaxNs = 8192;
-constexpr size_t ip_smem_bytes(int64_t ns) { return (size_t)ns * 5 * sizeof(int32_t); }
+constexpr int64_t kIpSmemSortNs = 4096;
+constexpr size_t ip_state_bytes(int64_t ns) { return ((size_t)ns * 5 * sizeof(int32_t) + 15) & ~size_t(15); }
+constexpr size_t ip_smem_bytes(int64_t ns, bool sort) {
+  return ip_state_bytes(ns) + (sort ? (size_t)ns * (2 * sizeof(unsigned long long) + 2 * sizeof(int32_t)) : 0);
+}
 
-__global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
+__global__ void __launch_bounds__(kIpThreads, 2) k_bisect(IpArgs a) {
   extern __shared__ __align__(16) unsigned char ip_dsm[];
   __shared__ BlockSortSmem sm;
   __shared__ int s_any, s_maxd;
@@ -124,6 +130,13 @@ __global__ void __launch_bounds__(kIpThreads) k_bisect(IpArgs a) {
   }
   unsigned long long *ka = a.ka + so, *kb = a.kb + so;
   int32_t *va = a.va + so, *vb = a.vb + so;
+  if (a.smem_sort) {
+    unsigned char *sb = ip_dsm + ip_state_bytes((int64_t)ns);
+    ka = reinterpret_cast<unsigned long long *>(sb);
+    kb = ka + ns;
+    va = reinterpret_cast<int32_t *>(kb + ns);
+    vb = va + ns;
+  }
   long long *gws = a.gws + ko;
   unsigned long long *gminh = a.gminh + ko, *gfar = a.gfar + ko;
   int *gstart = a.gstart + ko;
@@ -617,9 +630,12 @@ int initial_partition_multi(const IpJob *jobs, int njobs, int tries, int repair_
   int64_t max_ns = 0;
   for (const IpGraph &G : hg) max_ns = std::max<int64_t>(max_ns, G.ns);
   a.smem_ns = max_ns <= kIpSmemMaxNs ? max_ns : 0;
-  const size_t dsm = a.smem_ns > 0 ? ip_smem_bytes(a.smem_ns) : 0;
-  if (dsm > 0)  // (per call: the attribute belongs to the current device)
-    GP_CUDA(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ip_smem_bytes(kIpSmemMaxNs)));
+  a.smem_sort = max_ns <= kIpSmemSortNs ? 1 : 0;
+  const size_t dsm = a.smem_ns > 0 ? ip_smem_bytes(a.smem_ns, a.smem_sort != 0) : 0;
+  if (dsm > 0) {  // (per call: the attribute belongs to the current device)
+    const size_t cap = std::max(ip_smem_bytes(kIpSmemMaxNs, false), ip_smem_bytes(kIpSmemSortNs, true));
+    GP_CUDA(cudaFuncSetAttribute(k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  }
   (::gp::count_launch(), k_bisect<<<grid, kIpThreads, dsm, s>>>(a));
   GP_LAUNCH_CHECK();
   (::gp::count_launch(), k_repair<<<grid, kIpThreads, 0, s>>>(a));
