@@ -370,46 +370,17 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
   }
 }
 
-// Each warp takes 32 consecutive vertices and walks the concatenation of their rows 32 entries at a
-// time (contiguous adjacency reads); an entry's vertex is the largest lane whose row starts at or
-// before it.
 __global__ void k_cut(DGraph g, const int32_t *part, unsigned long long *acc) {
   __shared__ long long sh[32];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   long long s = 0;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = w0 * 32; base < g.n; base += nw * 32) {
-    const int64_t v = base + lane;
-    int64_t rb = 0, deg = 0;
-    int pv = -1;
-    if (v < g.n) {
-      rb = g.row_begin(v);
-      deg = g.row_begin(v + 1) - rb;
-      pv = part[v];
-    }
-    int64_t incl = deg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const int64_t excl = incl - deg;
-    const int64_t total = __shfl_sync(kFull, incl, 31);
-    for (int64_t t0 = 0; t0 < total; t0 += 32) {
-      const int64_t t = t0 + lane;
-      int j = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int64_t ex = __shfl_sync(kFull, excl, j + step);
-        if (j + step < 32 && ex <= t) j += step;
-      }
-      const int64_t x = __shfl_sync(kFull, rb, j) + (t - __shfl_sync(kFull, excl, j));
-      const int pj = __shfl_sync(kFull, pv, j);
-      if (t < total && part[g.adj[x]] != pj) s += g.eweight(x);
-    }
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int pv = part[v];
+    const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
+    for (int64_t j = b; j < e; j++)
+      if (part[g.adj[j]] != pv) s += g.eweight(j);
   }
   s = warp_sum64(s);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) sh[wid] = s;
   __syncthreads();
   if (wid == 0) {
