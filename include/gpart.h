@@ -95,6 +95,11 @@ typedef struct gp_params {
   int32_t deg_cta;
   int32_t reserved;
   const void *mlp;        /* device pointer to a gp_mlp (learned modes), else NULL */
+  /* LP tile sizes (0 = default; never change results): hub table slots per batch of the multi-CTA
+   * hub path (default 4M, clamped to [4096, 2^28]) and the fewest vertices per CTA of one LP problem
+   * (default 64, clamped to [16, 4096]) */
+  int64_t hub_batch_slots;
+  int64_t verts_per_block;
 } gp_params;
 
 enum { GP_MODE_PLAIN = 0, GP_MODE_LEARNED = 1, GP_MODE_BEST_OF = 2 };
@@ -193,6 +198,8 @@ int gp_lp_cluster(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
  *   Temporary buffers come from one fixed 16 MiB device array inside the library, which every
  *   process that loads the library holds on each GPU it uses until exit. Graphs with
  *   n > 32768 vertices or m_dir > 131072 CSR entries are rejected with GP_ERR_UNSUPPORTED.
+ *   The call makes no pinned host allocation either (cudaMallocHost): its few read-backs of counters
+ *   go straight into ordinary host memory. gp_pinned_stage_allocs() lets a caller check this.
  *   The first call on a device looks the array's device address up (with that device current); make
  *   that first call before any stream capture.
  *   All calls share the array and it keeps the last call's contents (every call clears what must
@@ -208,6 +215,12 @@ int gp_lp_cluster_noalloc(const gp_graph *g, int64_t U, int32_t rounds, uint64_t
  * [deg_warp, 1024]. The schedule never changes results. gp_partition uses params.deg_warp/deg_cta
  * when non-zero, else this schedule. */
 int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta);
+
+/* LP tile sizes of gp_lp_cluster and gp_lp_refine (process-wide), as gp_params.hub_batch_slots and
+ * gp_params.verts_per_block; 0 restores a default. Tile sizes never change results: a small
+ * hub_batch_slots splits the hubs of one sub-round into many batches (each with its own table pass),
+ * which the tests use to compare the multi-batch hub path with the oracle on small graphs. */
+int gp_lp_set_tiles(int64_t hub_batch_slots, int64_t verts_per_block);
 
 /* LP refinement of a k-way partition (Section III-C, Section IV-C): the same rounds with labels
  * = blocks 0..k-1 and U = lmax.
@@ -297,6 +310,13 @@ int gp_partition_batch(const gp_batch_item *items, int32_t count, const gp_param
 int gp_autotune_schedule(const gp_graph *g, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
                          gp_stream stream);
 
+/* Schedule and tile-size autotuner: as gp_autotune_schedule, then, with the best degree bins, times
+ * three LP rounds under candidate tile sizes (verts_per_block in {32, 64, 128, 256}; when g has
+ * vertices of degree > deg_cta, hub_batch_slots in {1M, 4M, 16M}) and writes the fastest into
+ * params->deg_warp, deg_cta, verts_per_block and hub_batch_slots (other fields are left as they are).
+ * params: host struct (required), typically from gp_default_params. */
+int gp_autotune(const gp_graph *g, gp_params *params, double *ms_out, gp_stream stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Profiling: when enabled, the library records CUDA events on the caller's stream around each
  * launch of its named hot kernels (the LP aggregate+choose kernels of every degree bin, the
@@ -312,6 +332,14 @@ typedef struct gp_profile_entry {
   int64_t bytes;
 } gp_profile_entry;
 int gp_profile_enable(int on);
+/* Limit of every bounded device-side wait (the grid barriers of the LP kernel), in nanoseconds of the
+ * GPU's global timer; 0 restores the default of 20 s. A wait that runs out makes the call return
+ * GP_ERR_TIMEOUT after every CTA of the kernel has returned (the CUDA context stays usable). The limit is
+ * process-wide and read when a call launches its kernels. */
+int gp_set_wait_limit(uint64_t ns);
+/* Number of pinned host staging buffers (cudaMallocHost) the library has allocated for its device-to-
+ * host read-backs since load. gp_lp_cluster_noalloc never adds to it. */
+int64_t gp_pinned_stage_allocs(void);
 /* Number of kernel launches the library has issued since load (or since the last reset != 0). */
 int64_t gp_launch_count(int reset);
 /* Copies up to max_entries entries into out and returns how many were written; reset != 0 clears

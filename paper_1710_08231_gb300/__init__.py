@@ -42,7 +42,7 @@ class GpParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64), ("coarse_min", I64),
                 ("coarse_per_k", I64), ("stall_pct", I64), ("max_levels", I64), ("ip_tries", I64),
                 ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("reserved", I32),
-                ("mlp", VP)]
+                ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64)]
 
 
 class GpResult(ctypes.Structure):
@@ -139,6 +139,14 @@ def lib():
         L.gp_lp_set_schedule.argtypes = [ctypes.c_int, ctypes.c_int]
         L.gp_autotune_schedule.restype = ctypes.c_int
         L.gp_autotune_schedule.argtypes = [ctypes.POINTER(GpGraph), VP, VP, VP, VP]
+        L.gp_autotune.restype = ctypes.c_int
+        L.gp_autotune.argtypes = [ctypes.POINTER(GpGraph), ctypes.POINTER(GpParams), VP, VP]
+        L.gp_lp_set_tiles.restype = ctypes.c_int
+        L.gp_lp_set_tiles.argtypes = [I64, I64]
+        L.gp_set_wait_limit.restype = ctypes.c_int
+        L.gp_set_wait_limit.argtypes = [U64]
+        L.gp_pinned_stage_allocs.restype = I64
+        L.gp_pinned_stage_allocs.argtypes = []
         L.gp_free_cached.restype = None
         L.gp_free_cached.argtypes = []
         L.gp_launch_count.restype = I64
@@ -424,6 +432,21 @@ def lp_set_schedule(deg_warp: int = 0, deg_cta: int = 0):
     _check(lib().gp_lp_set_schedule(deg_warp, deg_cta), "gp_lp_set_schedule")
 
 
+def lp_set_tiles(hub_batch_slots: int = 0, verts_per_block: int = 0):
+    """LP tile sizes for gp_lp_cluster/gp_lp_refine (0 = defaults); results never depend on them."""
+    _check(lib().gp_lp_set_tiles(hub_batch_slots, verts_per_block), "gp_lp_set_tiles")
+
+
+def set_wait_limit(ns: int = 0):
+    """Limit of every bounded device wait in nanoseconds (0 = the default of 20 s)."""
+    _check(lib().gp_set_wait_limit(ns), "gp_set_wait_limit")
+
+
+def pinned_stage_allocs() -> int:
+    """Pinned host staging buffers the library has allocated since load."""
+    return int(lib().gp_pinned_stage_allocs())
+
+
 def launch_count(reset: bool = False) -> int:
     """Kernel launches issued by the library (optionally resetting the counter)."""
     return int(lib().gp_launch_count(1 if reset else 0))
@@ -533,6 +556,15 @@ def partition_batch(graphs, ks, eps, seeds, params: Optional[GpParams] = None, s
            "gp_partition_batch")
     tries = params.ip_tries if params else 4
     return [parts[i][: graphs[i].n] for i in range(n)], [_result(res[i], tries) for i in range(n)]
+
+
+def autotune(dg: DeviceGraph, params: Optional[GpParams] = None, stream=None):
+    """Degree bins and tile sizes picked by timing LP rounds of dg; returns (params, ms)."""
+    p = params if params is not None else default_params()
+    ms = ctypes.c_double(0)
+    _check(lib().gp_autotune(ctypes.byref(dg.desc), ctypes.byref(p), ctypes.byref(ms), _stream(stream)),
+           "gp_autotune")
+    return p, float(ms.value)
 
 
 def autotune_schedule(dg: DeviceGraph, stream=None):

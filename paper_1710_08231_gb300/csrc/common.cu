@@ -66,8 +66,22 @@ struct PinnedStage {
 thread_local PinnedStage t_stage;
 }  // namespace
 
+static std::atomic<long long> g_stage_allocs{0};
+long long pinned_stage_allocs() { return g_stage_allocs.load(); }
+static thread_local ScratchArena *t_arena = nullptr;
+
 int Readback::run(cudaStream_t s) {
   if (items.empty()) return GP_OK;
+  if (t_arena) {
+    // A caller that allocates nothing gets no pinned host stage either: the copies go straight to
+    // the (pageable) host destinations, still with a single synchronisation at the end.
+    for (const Item &it : items)
+      if (it.bytes) GP_CUDA(cudaMemcpyAsync(it.host, it.dev, it.bytes, cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    items.clear();
+    total = 0;
+    return GP_OK;
+  }
   if (t_stage.cap < total) {
     if (t_stage.p) cudaFreeHost(t_stage.p);
     t_stage.p = nullptr;
@@ -75,6 +89,7 @@ int Readback::run(cudaStream_t s) {
     const size_t cap = std::max<size_t>(total, 64 * 1024);
     void *h = nullptr;
     GP_CUDA(cudaMallocHost(&h, cap));
+    g_stage_allocs.fetch_add(1);
     t_stage.p = static_cast<unsigned char *>(h);
     t_stage.cap = cap;
   }
@@ -104,7 +119,6 @@ void set_allocator(gp_alloc_fn a, gp_free_fn f, void *ctx) {
 
 // While a thread has an arena installed, its temporary allocations are carved from that fixed
 // device buffer (bump allocation, released all at once by the caller) instead of an allocator.
-static thread_local ScratchArena *t_arena = nullptr;
 void set_thread_arena(ScratchArena *a) { t_arena = a; }
 bool arena_active() { return t_arena != nullptr; }
 
@@ -143,6 +157,11 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
   }
   raw_free(p, bytes, s);
 }
+
+// ------------------------------------------------------------------------------------------ waits
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+unsigned long long wait_limit_ns() { return g_wait_ns.load(); }
+void set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : kDefaultWaitNs); }
 
 // ------------------------------------------------------------------------------------------ device
 int device_id() {

@@ -44,6 +44,7 @@ bool arena_active();
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
 void free_cached();  // returns the blocks the library keeps for reuse to the allocator
+long long pinned_stage_allocs();  // pinned host staging allocations made by Readback so far
 
 // Several device ranges read to host memory with one synchronisation of the stream: the copies go
 // through the calling thread's pinned staging buffer (so they are queued without blocking) and are
@@ -258,22 +259,36 @@ __device__ __forceinline__ T block_excl_scan64(T x, T *tmp, T *total) {
 // and only when, the last block has arrived; each block polls the word with acquire loads until bit 31
 // differs from the value its own addition returned. A block that moves on to the next barrier adds
 // again, but bit 31 cannot flip back before every block has arrived there too. A problem of one block
-// needs only __syncthreads. `err` receives GP_ERR_TIMEOUT when a wait gives up (about 2^24 polls), in
-// which case every waiting block returns false.
+// needs only __syncthreads.
+// The wait is bounded in time: a block that has polled for more than `wait_ns` nanoseconds of the
+// global timer (or that sees another block's timeout) stores GP_ERR_TIMEOUT in `err` and returns false,
+// and so does every other waiting block once it sees the flag, so the kernel ends with every block
+// returned and the host reads the status.
 constexpr unsigned kBarrierStride = 32;
 inline unsigned barrier_words(unsigned) { return kBarrierStride; }
+constexpr unsigned long long kDefaultWaitNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+// Process-wide limit of every bounded device wait (host setting, copied into each launch's arguments).
+unsigned long long wait_limit_ns();
+void set_wait_limit_ns(unsigned long long ns);  // 0 restores kDefaultWaitNs
 
 struct GridBarrier {
   unsigned int *count;  // barrier_words(nblocks) words, zero-initialised
   int *err;
   unsigned int nblocks;
   unsigned int rank;    // this block's index among the nblocks
+  unsigned long long wait_ns;
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
@@ -288,9 +303,9 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
     const unsigned inc = b.rank == 0 ? 0x80000000u - (b.nblocks - 1) : 1u;
     unsigned old;
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
-    long long polls = 0;
+    const unsigned long long t0 = global_ns();
     while (((ld_acquire_u32(b.count) ^ old) & 0x80000000u) == 0) {
-      if (++polls > (1ll << 24) || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
+      if (global_ns() - t0 > b.wait_ns || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
         atomicExch(b.err, GP_ERR_TIMEOUT);
         s_ok = 0;
         break;

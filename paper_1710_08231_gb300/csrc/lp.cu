@@ -41,12 +41,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpCap = 256;   // table slots per warp (d <= 128)
 constexpr int kCtaCap = 2048;   // table slots per CTA (d <= 1024)
 constexpr int kHubChunk = 1024; // CSR entries per hub work item (pre-aggregated in a 2048-slot table)
-constexpr int64_t kHubBatchSlots = int64_t(1) << 22;  // hub table slots per batch (tables stay in L2)
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
-// A problem gets at most one block per kVertsPerBlock vertices: small problems are bound by the
-// dependent latency of each phase, so more warps (fewer vertices per warp) shorten every sub-round.
-constexpr int64_t kVertsPerBlock = 64;
+// Hub table slots per batch and the fewest vertices per block come from LpConfig (tile sizes picked by
+// gp_autotune): a problem gets at most one block per verts_per_block vertices, since small problems are
+// bound by the dependent latency of each phase and more warps (fewer vertices per warp) shorten every
+// sub-round.
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
 constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
@@ -86,6 +86,8 @@ struct LpProblem {
   DGraph g;  // g.n local vertices; offsets/vertex weights indexed by local id, adjacency by global entry
   int64_t vbase, lbase;
   int64_t nl, U;
+  int64_t hub_batch_slots;     // hub table slots per batch (tile size of the hub path)
+  unsigned long long wait_ns;  // limit of every barrier wait
   uint64_t smix;  // mix64(seed)
   int rounds;
   int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
@@ -961,8 +963,8 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
 
 // Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (kHubChunk
 // entries), table slots (hub_cap(d) each) and choice items (kSlotChunk slots); cut into batches of
-// about kHubBatchSlots slots (a hub starts a new batch when its slot prefix crosses a multiple of
-// kHubBatchSlots); table base of each hub inside its batch.
+// about P.hub_batch_slots slots (a hub starts a new batch when its slot prefix crosses a multiple of
+// that size); table base of each hub inside its batch.
 __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm) {
   const unsigned cnt = V.bin_count[6];
   __shared__ long long s_cap, s_ch, s_sc, s_nbat, s_prev_bid;
@@ -993,7 +995,7 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     const long long ch_t = sm.tot;
     const long long scx = s_sc + block_excl_scan64(sc, sm.tmp, &sm.tot);
     const long long sc_t = sm.tot;
-    const long long bid = capx / kHubBatchSlots;
+    const long long bid = capx / P.hub_batch_slots;
     t_bid[threadIdx.x] = bid;
     __syncthreads();
     const long long prev = threadIdx.x > 0 ? t_bid[threadIdx.x - 1] : s_prev_bid;
@@ -1695,7 +1697,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   __syncthreads();
   const int lb = (int)blockIdx.x - P.block_begin, nb = P.block_count;
   LpCounters *ctr = P.ctr;
-  const GridBarrier bar{P.bar, &ctr->err, (unsigned)nb, (unsigned)lb};
+  const GridBarrier bar{P.bar, &ctr->err, (unsigned)nb, (unsigned)lb, P.wait_ns};
   // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there) in
   // shared memory and writes the totals once at the end
   __shared__ unsigned long long pacc[8];
@@ -1986,6 +1988,10 @@ LpConfig lp_config_from(const gp_params *p) {
   }
   c.deg_warp = std::max(32, std::min(c.deg_warp, kWarpCap / 2));
   c.deg_cta = std::max(c.deg_warp, std::min(c.deg_cta, kCtaCap / 2));
+  if (p && p->hub_batch_slots > 0) c.hub_batch_slots = p->hub_batch_slots;
+  if (p && p->verts_per_block > 0) c.verts_per_block = p->verts_per_block;
+  c.hub_batch_slots = std::max<int64_t>(kMinHubBatchSlots, std::min<int64_t>(c.hub_batch_slots, kMaxHubBatchSlots));
+  c.verts_per_block = std::max<int64_t>(kMinVertsPerBlock, std::min<int64_t>(c.verts_per_block, kMaxVertsPerBlock));
   return c;
 }
 
@@ -2187,7 +2193,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       ci->hub_cap_sum = hhub[2 * (size_t)j + 1];
     }
   }
-  // Blocks: a job gets at most one block per kVertsPerBlock vertices. When all jobs fit the co-resident
+  // Blocks: a job gets at most one block per cfg.verts_per_block vertices. When all jobs fit the co-resident
   // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
   // + a fixed per-problem latency term): jobs above twice the mean block load get several blocks,
   // the rest run one block each, packed onto the remaining blocks longest first.
@@ -2196,7 +2202,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   for (int j = 0; j < njobs; j++) {
     // (the large contest stages 32 bytes per block of a problem in the dynamic shared memory)
     useful[j] = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(cap_blocks, (int64_t)(kDynSmem / 32)),
-                                                       (jobs[j].g.n + kVertsPerBlock - 1) / kVertsPerBlock));
+                                                       (jobs[j].g.n + cfg.verts_per_block - 1) / cfg.verts_per_block));
     sum_useful += useful[j];
   }
   std::vector<int> nblk(njobs, 1), home(njobs, -1);
@@ -2297,6 +2303,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.lbase = jb.lbase;
     P.nl = jb.nl;
     P.U = jb.U;
+    P.hub_batch_slots = cfg.hub_batch_slots;
+    P.wait_ns = wait_limit_ns();
     P.smix = mix64(jb.seed);
     P.rounds = jb.g.n > 0 ? jb.rounds : 0;
     P.singletons = jb.singletons ? 1 : 0;
@@ -2343,7 +2351,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     if (nhub) {
       // tables of one batch of hubs (reused batch after batch), partial choices, per-hub arrays
       const int64_t max_cap = (int64_t)hhub[2 * j], cap_sum = (int64_t)hhub[2 * j + 1];
-      const int64_t slots = std::min<int64_t>(kHubBatchSlots, cap_sum) + max_cap;
+      const int64_t slots = std::min<int64_t>(cfg.hub_batch_slots, cap_sum) + max_cap;
       // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub; the
       // round-0 direct path keeps one item per chunk of every hub row
       const int64_t items = std::max<int64_t>(slots / kSlotChunk, (int64_t)(hent[j] / kHubChunk)) + (int64_t)nhub + 16;

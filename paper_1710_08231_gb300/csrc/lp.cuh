@@ -11,7 +11,13 @@ struct LpConfig {
   int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 128)
   int deg_cta = 1024;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 1024)
                         // d > deg_cta: several CTAs per vertex, global-memory hash
+  // tile sizes: hub table slots per batch (the hub tables of one batch are reused by the next) and the
+  // fewest vertices per block of a problem
+  int64_t hub_batch_slots = int64_t(1) << 22;
+  int64_t verts_per_block = 64;
 };
+constexpr int64_t kMinHubBatchSlots = 4096, kMaxHubBatchSlots = int64_t(1) << 28;
+constexpr int64_t kMinVertsPerBlock = 16, kMaxVertsPerBlock = 4096;
 
 // Degree classes of a graph under one schedule (vertices per bin, CSR entries, largest hub table and
 // the sum of hub tables). run_lp_multi fills it when `valid` is false and a later call on the same

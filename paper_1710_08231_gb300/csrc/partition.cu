@@ -98,6 +98,8 @@ LpConfig schedule_for(const gp_params *p) {
   gp_params q = g_schedule;
   if (p && p->deg_warp > 0) q.deg_warp = p->deg_warp;
   if (p && p->deg_cta > 0) q.deg_cta = p->deg_cta;
+  if (p && p->hub_batch_slots > 0) q.hub_batch_slots = p->hub_batch_slots;
+  if (p && p->verts_per_block > 0) q.verts_per_block = p->verts_per_block;
   return lp_config_from(&q);
 }
 
@@ -611,21 +613,31 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta) {
   return GP_OK;
 }
 
+int gp_lp_set_tiles(int64_t hub_batch_slots, int64_t verts_per_block) {
+  if (hub_batch_slots < 0 || verts_per_block < 0) {
+    set_error("gp_lp_set_tiles: tile sizes must be >= 0");
+    return GP_ERR_INVALID_ARG;
+  }
+  g_schedule.hub_batch_slots = hub_batch_slots;
+  g_schedule.verts_per_block = verts_per_block;
+  return GP_OK;
+}
+
+int gp_set_wait_limit(uint64_t ns) {
+  gp::set_wait_limit_ns(ns);
+  return GP_OK;
+}
+
+int64_t gp_pinned_stage_allocs(void) { return gp::pinned_stage_allocs(); }
+
 int64_t gp_launch_count(int reset) { return gp::launch_count(reset); }
 
 void gp_free_cached(void) { gp::free_cached(); }
 
-int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
-                         gp_stream stream) {
-  GP_TRY(check_graph_desc(gd));
-  if (!deg_warp_out || !deg_cta_out) {
-    set_error("gp_autotune_schedule: outputs are required");
-    return GP_ERR_INVALID_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  const DGraph g = make_dgraph(gd);
-  static const int cand[][2] = {{32, 256}, {64, 256}, {64, 512}, {128, 512}, {128, 1024}, {32, 1024}};
-  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+// Times three LP rounds of g from singletons under each candidate configuration (the first sweep
+// warms up) and returns the index of the fastest; *best_ms receives its time.
+static int time_candidates(const DGraph &g, const std::vector<gp_params> &cand, int *best, double *best_ms,
+                           cudaStream_t s) {
   Workspace ws(s);
   int32_t *labels;
   int64_t *lw;
@@ -637,41 +649,109 @@ int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg
   cudaEvent_t a, b;
   GP_CUDA(cudaEventCreate(&a));
   GP_CUDA(cudaEventCreate(&b));
-  double best_ms = -1;
-  int best = 0;
-  for (int rep = 0; rep < 2; rep++) {  // the first sweep warms up
-    for (int c = 0; c < nc; c++) {
-      gp_params pr;
-      gp_default_params(&pr);
-      pr.deg_warp = cand[c][0];
-      pr.deg_cta = cand[c][1];
-      const LpConfig cfg = lp_config_from(&pr);
+  *best_ms = -1;
+  *best = 0;
+  for (int rep = 0; rep < 2; rep++) {
+    for (size_t c = 0; c < cand.size(); c++) {
+      const LpConfig cfg = lp_config_from(&cand[c]);
       if (g.n > 0) {
         (::gp::count_launch(), k_iota<<<grid_n(g.n), 256, 0, s>>>(labels, g.n));
         (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
       }
-      GP_CUDA(cudaEventRecord(a, s));
-      const int st = run_lp(g, nullptr, labels, lw, g.n, U, 3, 0x5eedULL, nullptr, s, cfg, true);
-      GP_CUDA(cudaEventRecord(b, s));
+      int st = cudaEventRecord(a, s) == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+      if (st == GP_OK) st = run_lp(g, nullptr, labels, lw, g.n, U, 3, 0x5eedULL, nullptr, s, cfg, true);
+      float ms = 0;
+      if (st == GP_OK && (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+        st = GP_ERR_CUDA;
       if (st != GP_OK) {
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        if (st == GP_ERR_CUDA) set_error("autotune: CUDA event timing failed");
         return st;
       }
-      GP_CUDA(cudaEventSynchronize(b));
-      float ms = 0;
-      GP_CUDA(cudaEventElapsedTime(&ms, a, b));
-      if (rep == 1 && (best_ms < 0 || ms < best_ms)) {
-        best_ms = ms;
-        best = c;
+      if (rep == 1 && (*best_ms < 0 || ms < *best_ms)) {
+        *best_ms = ms;
+        *best = (int)c;
       }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  *deg_warp_out = cand[best][0];
-  *deg_cta_out = cand[best][1];
-  if (ms_out) *ms_out = best_ms;
+  return GP_OK;
+}
+
+int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
+                         gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if (!deg_warp_out || !deg_cta_out) {
+    set_error("gp_autotune_schedule: outputs are required");
+    return GP_ERR_INVALID_ARG;
+  }
+  static const int cand[][2] = {{32, 256}, {64, 256}, {64, 512}, {128, 512}, {128, 1024}, {32, 1024}};
+  std::vector<gp_params> cs;
+  for (const auto &c : cand) {
+    gp_params pr;
+    gp_default_params(&pr);
+    pr.deg_warp = c[0];
+    pr.deg_cta = c[1];
+    cs.push_back(pr);
+  }
+  int best = 0;
+  double ms = 0;
+  GP_TRY(time_candidates(make_dgraph(gd), cs, &best, &ms, (cudaStream_t)stream));
+  *deg_warp_out = (int32_t)cs[best].deg_warp;
+  *deg_cta_out = (int32_t)cs[best].deg_cta;
+  if (ms_out) *ms_out = ms;
+  return GP_OK;
+}
+
+int gp_autotune(const gp_graph *gd, gp_params *params, double *ms_out, gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if (!params) {
+    set_error("gp_autotune: params is required");
+    return GP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t dw = 0, dc = 0;
+  double ms = 0;
+  GP_TRY(gp_autotune_schedule(gd, &dw, &dc, &ms, stream));
+  const DGraph g = make_dgraph(gd);
+  // hubs under the chosen bins decide whether the hub batch size matters
+  gp_params base;
+  gp_default_params(&base);
+  base.deg_warp = dw;
+  base.deg_cta = dc;
+  LpClassInfo ci;
+  {
+    Workspace ws(s);
+    unsigned long long *words;
+    GP_TRY(ws.get(&words, kLpClassWords));
+    const LpConfig cfg = lp_config_from(&base);
+    GP_TRY(lp_classes_launch(g, cfg, words, ws));
+    unsigned long long hw[kLpClassWords];
+    GP_CUDA(cudaMemcpyAsync(hw, words, sizeof(hw), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    lp_classes_from(hw, cfg, &ci);
+  }
+  std::vector<gp_params> cs;
+  static const int64_t vpb[] = {32, 64, 128, 256};
+  static const int64_t hbs[] = {int64_t(1) << 20, int64_t(1) << 22, int64_t(1) << 24};
+  const bool hubs = ci.cls[6] > 0;
+  for (int64_t v : vpb)
+    for (int h = 0; h < (hubs ? 3 : 1); h++) {
+      gp_params pr = base;
+      pr.verts_per_block = v;
+      pr.hub_batch_slots = hubs ? hbs[h] : 0;
+      cs.push_back(pr);
+    }
+  int best = 0;
+  GP_TRY(time_candidates(g, cs, &best, &ms, s));
+  params->deg_warp = dw;
+  params->deg_cta = dc;
+  params->verts_per_block = cs[best].verts_per_block;
+  params->hub_batch_slots = cs[best].hub_batch_slots;
+  if (ms_out) *ms_out = ms;
   return GP_OK;
 }
 

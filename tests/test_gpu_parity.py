@@ -217,3 +217,88 @@ def test_determinism_repeated_runs(gp):
     dg = gp.DeviceGraph.from_host(g)
     outs = [gp.partition(dg, 16, 0.03, 9)[0].cpu().numpy() for _ in range(3)]
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+# ---- the multi-batch hub path: a small hub batch size splits the hubs of one sub-round into many
+# batches, each with its own table pass (the path that dominates large power-law graphs)
+HUB_CASES = [("rmat13", 32, 32, 4096), ("rmat13", 0, 0, 4096), ("rmat12w", 32, 64, 8192),
+             ("rmat14", 32, 32, 16384)]
+
+
+@pytest.mark.parametrize("name,dw,dc,slots", HUB_CASES)
+def test_lp_cluster_multi_batch_hubs_match_oracle(gp, name, dw, dc, slots):
+    g = GRAPHS[name] if name in GRAPHS else gg.rmat(14, 16, seed=8)
+    gp.lp_set_schedule(dw, dc)
+    gp.lp_set_tiles(slots, 0)
+    try:
+        dg = gp.DeviceGraph.from_host(g)
+        gp.profile_read(reset=True)
+        gp.profile_enable(True)
+        lab, st = gp.lp_cluster(dg, 200, 10, 0xBEEF)
+        gp.profile_enable(False)
+        prof = {e["name"]: e for e in gp.profile_read(reset=True)}
+        lab_o, _, st_o = O.lp_cluster(g, 200, 10, 0xBEEF)
+        assert np.array_equal(lab.cpu().numpy(), lab_o)
+        _stats_eq(st, st_o)
+        # the hub tables of a sub-round with every vertex active are several batches' worth
+        d = np.diff(g.off)
+        hubs = d[d > (dc or 1024)]
+        assert ((2 * hubs + 63) // 64 * 64).sum() > 4 * slots
+        assert prof["lp_hub_work"]["items"] > 0
+    finally:
+        gp.lp_set_schedule(0, 0)
+        gp.lp_set_tiles(0, 0)
+
+
+@pytest.mark.parametrize("name,k", [("rmat13", 16), ("rmat12w", 8)])
+def test_lp_refine_and_partition_multi_batch_hubs_match_oracle(gp, name, k):
+    import torch
+    g = GRAPHS[name]
+    c = O.vertex_weights(g)
+    lm = O.lmax(int(c.sum()), k, 0.03)
+    part = np.random.default_rng(3).integers(0, k, g.n).astype(np.int32)
+    dg = gp.DeviceGraph.from_host(g)
+    params = gp.default_params(deg_warp=32, deg_cta=32, hub_batch_slots=4096, coarse_min=300)
+    oparams = O.default_params()
+    oparams.coarse_min = 300
+    gp.lp_set_schedule(32, 32)
+    gp.lp_set_tiles(4096, 0)
+    try:
+        p, bw, st = gp.lp_refine(dg, torch.from_numpy(part).cuda(), k, lm, 25, 77)
+    finally:
+        gp.lp_set_schedule(0, 0)
+        gp.lp_set_tiles(0, 0)
+    p_o, bw_o, st_o = O.lp_refine(g, part, k, lm, 25, 77)
+    assert np.array_equal(p.cpu().numpy(), p_o) and np.array_equal(bw.cpu().numpy(), bw_o)
+    _stats_eq(st, st_o)
+    pp, res = gp.partition(dg, k, 0.03, 5, params)
+    pp_o, res_o = O.partition(g, k, 0.03, 5, oparams)
+    assert np.array_equal(pp.cpu().numpy(), pp_o) and res.cut == res_o.cut
+
+
+@pytest.mark.parametrize("vpb", [16, 32, 256, 4096])
+def test_tile_sizes_never_change_results(gp, vpb):
+    g = GRAPHS["rgg15"]
+    dg = gp.DeviceGraph.from_host(g)
+    ref, st_ref = gp.lp_cluster(dg, 50, 10, 31)
+    gp.lp_set_tiles(0, vpb)
+    try:
+        lab, st = gp.lp_cluster(dg, 50, 10, 31)
+    finally:
+        gp.lp_set_tiles(0, 0)
+    assert np.array_equal(lab.cpu().numpy(), ref.cpu().numpy()) and st == st_ref
+    part, res = gp.partition(dg, 16, 0.03, 1, gp.default_params(verts_per_block=vpb))
+    part_o, res_o = O.partition(g, 16, 0.03, 1)
+    assert np.array_equal(part.cpu().numpy(), part_o)
+
+
+def test_autotune_picks_valid_tiles_and_keeps_results(gp):
+    g = GRAPHS["rmat13"]
+    dg = gp.DeviceGraph.from_host(g)
+    params, ms = gp.autotune(dg)
+    assert ms > 0
+    assert params.verts_per_block in (32, 64, 128, 256)
+    assert params.hub_batch_slots in (0, 1 << 20, 1 << 22, 1 << 24)
+    part, res = gp.partition(dg, 16, 0.03, 1, params)
+    part_o, res_o = O.partition(g, 16, 0.03, 1)
+    assert np.array_equal(part.cpu().numpy(), part_o)

@@ -72,3 +72,28 @@ def test_noalloc_rejects_graphs_beyond_the_limit(gp):
                                         ctypes.byref(st), None)
     assert rc == gp.GP_ERR_UNSUPPORTED
     assert "32768" in gp.lib().gp_last_error().decode()
+
+
+def test_noalloc_makes_no_pinned_host_allocation_on_a_new_thread(gp):
+    """A thread's first call would have to allocate the pinned staging buffer of the library's
+    read-backs; the allocation-free call must not: its counters go straight to ordinary host memory."""
+    import threading
+    g = gg.rgg(8000, 12.0, 9)
+    dg = gp.DeviceGraph.from_host(g)
+    ref, st_ref = gp.lp_cluster(dg, 40, 10, 5)
+    ref = ref.cpu().numpy()
+    out = {}
+
+    def run():
+        import torch
+        torch.cuda.set_device(0)
+        before = gp.pinned_stage_allocs()
+        out["res"] = [_noalloc(gp, dg, 40, 10, 5) for _ in range(2)]
+        out["pinned"] = gp.pinned_stage_allocs() - before
+
+    t = threading.Thread(target=run)
+    t.start()
+    t.join()
+    assert out["pinned"] == 0
+    for lab, st in out["res"]:
+        assert np.array_equal(lab, ref) and st == st_ref
