@@ -5,15 +5,19 @@ projection + LP refinement per level, degree-0 placement, evaluation) of one syn
 is resident in HBM when the timed region starts. value = LP edges traversed per step (CSR entries
 scanned by all LP sub-rounds of the partition, counted by the library) / device time per step.
 
-Default workload: random geometric graph, 2^20 vertices, average degree 12, unit weights, k=16,
-eps=0.03, seed 1 (a stand-in for the paper's rgg instances).
+Default workload: the largest configuration, R-MAT scale 26 (67M vertices, about 2.1G CSR entries),
+edge factor 16, integer edge weights in [1,8], k=64, eps=0.03, seed 1. Other workloads: rgg20 (random
+geometric graph 2^20), grid256, rmat24, batch512.
 
-The line also carries two comparisons at the same seed: the learned edge scorer (trained untimed on
-same-family graphs with other seeds) against plain LP on the same graph, and the batch of 512 uneven
-graphs partitioned in one call against a per-graph loop (results identical by construction, checked).
+The line carries, besides value: the LP kernel's HBM roofline (all LP launches, and the level-0
+coarsening launch alone), LP-only GTEPS (LP edges over LP kernel time), an end-to-end number through
+gp_partition_host from pinned host buffers, the CPU oracle timed on all host cores on a bounded sample
+of the workload, a check of the GPU result against the oracle's stored digests of the full-size
+workload, and comparisons at the same seed: the learned edge scorer against plain LP, and the batch of
+512 uneven graphs in one call against a per-graph loop.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                       [--mode plain|learned] [--no-compare]
+                       [--mode plain|learned] [--no-compare] [--learned-seeds S]
 --workload batch512 makes the batched call itself the timed step (value: LP GTEPS of the batch).
 For N > 1 the script runs under torch.distributed.run; every rank partitions its own replica
 (replicas only: the single-graph path does not shard), so scaling is weak.
@@ -95,18 +99,17 @@ def time_steps(fn, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev), out
 
 
-def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res):
-    """Learned against plain LP on the same graph at seeds 1..10 (geometric means of the per-seed cut
+def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res, nseeds=10):
+    """Learned against plain LP on the same graph at seeds 1..nseeds (geometric means of the per-seed cut
     and time ratios), plus the timed learned run at the bench's own seed."""
     import math
     mlp, loss = train_scorer(gp, name, k)
     params = gp.default_params(mode=gp.MODE_LEARNED)
     params.mlp = mlp.data_ptr()
-    for _ in range(2):
-        gp.partition(dg, k, EPS, SEED, params)
+    gp.partition(dg, k, EPS, SEED, params)
     ms, (_, res) = time_steps(lambda: gp.partition(dg, k, EPS, SEED, params), steps, flush)
     per_seed = []
-    for sd in range(1, 11):
+    for sd in range(1, nseeds + 1):
         pm, (_, rp) = time_steps(lambda: gp.partition(dg, k, EPS, sd), 1, flush)
         lm, (_, rl) = time_steps(lambda: gp.partition(dg, k, EPS, sd, params), 1, flush)
         per_seed.append({"seed": sd, "plain_cut": rp.cut, "learned_cut": rl.cut, "plain_ms": pm, "learned_ms": lm,
@@ -116,7 +119,7 @@ def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res):
             "imbalanced": res.imbalanced, "plain_cut": plain_res.cut, "plain_ms_per_partition": plain_ms,
             "cut_ratio_learned_over_plain": res.cut / max(plain_res.cut, 1),
             "time_ratio_learned_over_plain": (ms / steps) / plain_ms, "levels": res.levels,
-            "seeds_1_10": {"geomean_cut_ratio": gm([x["learned_cut"] / max(x["plain_cut"], 1) for x in per_seed]),
+            "seeds": {"count": nseeds, "geomean_cut_ratio": gm([x["learned_cut"] / max(x["plain_cut"], 1) for x in per_seed]),
                            "geomean_time_ratio": gm([x["learned_ms"] / x["plain_ms"] for x in per_seed]),
                            "learned_better_or_equal": sum(x["learned_cut"] <= x["plain_cut"] for x in per_seed),
                            "per_seed": per_seed},
@@ -177,14 +180,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
-TRAFFIC_SUMMARY = {"rgg20": "profiles/k_lp_rgg20_dram_per_launch.md"}
+# committed ncu summaries giving DRAM bytes per k_lp launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid while the LP sources hash to the value recorded in them
+TRAFFIC_SUMMARY = {"rgg20": "profiles/k_lp_rgg20_dram_per_launch.md",
+                   "rmat26w": "profiles/k_lp_rmat_level0_dram.md"}
 LP_SOURCES = ["paper_1710_08231_gb300/csrc/lp.cu", "paper_1710_08231_gb300/csrc/lp.cuh",
               "paper_1710_08231_gb300/csrc/gp_internal.cuh"]
+LP_NAMES = ("lp_persistent", "lp_persistent_level0")
 
 
-def lp_traffic(workload: str):
-    """DRAM bytes per k_lp launch from the committed ncu summary of this workload, or None when there
-    is none or the LP sources changed since the counters were taken."""
+def lp_traffic(workload: str, key: str):
+    """DRAM bytes per k_lp launch (`key` = traffic_bytes_per_launch for the average over a partition's LP
+    launches, level0_traffic_bytes_per_launch for the level-0 coarsening launch) from the committed ncu
+    summary of this workload, or None when there is none or the LP sources changed since."""
     import hashlib
     path = os.path.join(ROOT, TRAFFIC_SUMMARY.get(workload, ""))
     if workload not in TRAFFIC_SUMMARY or not os.path.exists(path):
@@ -192,16 +200,56 @@ def lp_traffic(workload: str):
     fields = {}
     with open(path) as f:
         for line in f:
-            if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "source_sha256"):
-                k, v = line.split(":", 1)
-                fields[k] = v.strip()
+            if ":" in line:
+                k_, v_ = line.split(":", 1)
+                fields[k_.strip().strip("`*- ")] = v_.strip().strip("`* ")
     h = hashlib.sha256()
     for src in LP_SOURCES:
         with open(os.path.join(ROOT, src), "rb") as f:
             h.update(f.read())
-    if fields.get("source_sha256") != h.hexdigest() or "traffic_bytes_per_launch" not in fields:
+    if fields.get("source_sha256") != h.hexdigest() or key not in fields:
         return None
-    return float(fields["traffic_bytes_per_launch"])
+    return float(fields[key])
+
+
+def lp_roofline(prof, args, peak, peak_kind):
+    """HBM roofline of k_lp from the library's per-launch CUDA events inside the timed region and its
+    algorithmic byte counts: over every LP launch of the timed partitions, and over the level-0
+    coarsening launches alone. Returns (roofline object, LP-only GTEPS)."""
+    lp = [e for e in prof if e["name"] in LP_NAMES and e["launches"] > 0 and e["ms"] > 0]
+    if not lp:
+        return None, None
+    ms = sum(e["ms"] for e in lp)
+    by = sum(e["bytes"] for e in lp)
+    ed = sum(e["edges"] for e in lp)
+    la = sum(e["launches"] for e in lp)
+    achieved = by / (ms * 1e-3) / 1e9
+    peak_src = "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": lp_traffic(args.workload, "traffic_bytes_per_launch"),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per k_lp launch, "
+                              + TRAFFIC_SUMMARY.get(args.workload, "none"),
+            "kernel": "k_lp (all LP launches of the timed partitions)", "launches": la,
+            "ms_per_launch": ms / la, "bytes_per_launch": by / la, "peak_source": peak_src,
+            "lp_gteps": ed / (ms * 1e-3) / 1e9}
+    l0 = next((e for e in lp if e["name"] == "lp_persistent_level0"), None)
+    if l0:
+        a0 = l0["bytes"] / (l0["ms"] * 1e-3) / 1e9
+        roof["level0"] = {"kernel": "k_lp, level-0 coarsening launch", "achieved": a0, "frac": a0 / peak,
+                          "launches": l0["launches"], "ms_per_launch": l0["ms"] / l0["launches"],
+                          "bytes_per_launch": l0["bytes"] / l0["launches"],
+                          "lp_gteps": l0["edges"] / (l0["ms"] * 1e-3) / 1e9,
+                          "traffic": lp_traffic(args.workload, "level0_traffic_bytes_per_launch")}
+    roof["kernels_ms_per_step"] = {e["name"]: e["ms"] / args.steps for e in prof
+                                   if e["launches"] > 0 and not e["name"].startswith("lp_phase")}
+    roof["kernels_achieved_gbs"] = {e["name"]: {"gbs": e["bytes"] / (e["ms"] * 1e-3) / 1e9,
+                                                "frac": e["bytes"] / (e["ms"] * 1e-3) / 1e9 / peak}
+                                    for e in prof if e["launches"] > 0 and e["bytes"] > 0 and e["ms"] > 0}
+    roof["lp_phases_ms_per_step"] = {e["name"][9:]: e["ms"] / args.steps for e in prof
+                                     if e["name"].startswith("lp_phase")}
+    roof["contest_calls_per_step"] = {e["name"][11:-6]: e["items"] / args.steps for e in prof
+                                      if e["name"].startswith("lp_contest")}
+    return roof, ed / (ms * 1e-3) / 1e9
 
 
 class ClockSampler:
@@ -303,88 +351,215 @@ def sum_over_ranks(x: float, dist) -> float:
     return float(t.item())
 
 
-def run_oracle_sample(g, k: int):
-    import oracle
-    t0 = time.perf_counter()
-    part, res = oracle.partition(g, k, EPS, SEED)
-    dt = time.perf_counter() - t0
-    return res.lp_edges, dt, res
+# ---------------------------------------------------------------------------------------------- CPU oracle
+# The oracle is timed on every host core at once: one worker process per core, each with its own copy
+# of the sample graph(s), all started together; a step's rate is the LP edges of all workers over the
+# step's wall time. Samples are bounded so that a step takes a few seconds of CPU work.
+SAMPLES = {
+    "rgg20": ("one full oracle partition of the workload graph itself (RGG 2^20, k=16) per core",
+              lambda i: [(("rgg", 1 << 20, 12.0, 1), 16, SEED)]),
+    "grid256": ("one full oracle partition of the workload graph itself (grid 256x256, k=2) per core",
+                lambda i: [(("grid", 256, 256), 2, SEED)]),
+    "rmat24": ("one full oracle partition (k=16) per core of an R-MAT scale-17 graph of the same generator and "
+               "parameters (seed 101 + core index); a full scale-24 oracle partition takes about 20 minutes",
+               lambda i: [(("rmat", 17, 16, 101 + i, False), 16, SEED)]),
+    "rmat26w": ("one full oracle partition (k=64) per core of a weighted R-MAT scale-16 graph of the same generator "
+                "and parameters (seed 101 + core index); one oracle LP round of the scale-26 graph alone takes "
+                "minutes",
+                lambda i: [(("rmat", 16, 16, 101 + i, True), 64, SEED)]),
+}
 
 
-def oracle_batch_sample(specs, graphs, budget_s: float = 10.0):
-    """Oracle partitions of the batch's graphs in order until budget_s of CPU time: (edges, s, count)."""
+def _make(spec):
+    import graphgen as gg
+    if spec[0] == "rgg":
+        return gg.rgg(spec[1], spec[2], spec[3])
+    if spec[0] == "grid":
+        return gg.grid(spec[1], spec[2])
+    if spec[0] == "batch":
+        return gg.batch_graph(gg.batch_specs(512, seed=SEED)[spec[1]])
+    return gg.rmat(spec[1], spec[2], seed=spec[3], weighted=spec[4])
+
+
+def _oracle_worker(conn, items):
+    """Worker: builds its sample graphs, then runs one oracle partition of each per 'run' command."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
     import oracle
-    e, t, c = 0, 0.0, 0
-    for sp, g in zip(specs, graphs):
-        t0 = time.perf_counter()
-        _, res = oracle.partition(g, sp.k, EPS, sp.seed)
-        t += time.perf_counter() - t0
-        e += res.lp_edges
-        c += 1
-        if t >= budget_s:
+    graphs = [(_make(spec), k, sd) for spec, k, sd in items]
+    oracle.build()
+    conn.send("ready")
+    while True:
+        cmd = conn.recv()
+        if cmd != "run":
             break
-    return e, t, c
+        e, t, cut = 0, 0.0, 0
+        for g, k, sd in graphs:
+            t0 = time.perf_counter()
+            _, res = oracle.partition(g, k, EPS, sd)
+            t += time.perf_counter() - t0
+            e += res.lp_edges
+            cut += res.cut
+        conn.send((e, t, cut))
 
 
-def bench_reference(args, g, w):
-    """Reference arm: the CPU oracle as it stands, single-threaded, one full partition per step."""
+class OraclePool:
+    """One oracle worker per host core (spawned processes)."""
+
+    def __init__(self, workload: str, cores: int | None = None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        if workload == "batch512":
+            # every core takes every cores-th graph of the batch
+            import graphgen as gg
+            specs = gg.batch_specs(512, seed=SEED)
+            per = [[(("batch", j), specs[j].k, specs[j].seed) for j in range(i, 512, self.cores)][:2]
+                   for i in range(self.cores)]
+            self.desc = (f"two graphs of the batch per core (graphs i and i + {self.cores}), each fully "
+                         f"partitioned by the oracle with its own k and seed")
+        else:
+            self.desc, mk = SAMPLES[workload]
+            per = [mk(i) for i in range(self.cores)]
+        self.conns, self.procs = [], []
+        for i in range(self.cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, per[i]), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def step(self):
+        """One sample on every core: (LP edges of all cores, wall seconds, summed CPU seconds)."""
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("run")
+        got = [c.recv() for c in self.conns]
+        wall = time.perf_counter() - t0
+        return sum(g[0] for g in got), wall, sum(g[1] for g in got)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send("stop")
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def cpu_info() -> dict:
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": __import__("platform").machine()}
+
+
+def bench_reference(args, w):
+    """Reference arm: the CPU oracle as it stands, on every host core, a bounded sample per step."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
-    if w["kind"] == "batch":
-        specs, graphs = g
+    pool = OraclePool(args.workload)
+    try:
         for _ in range(args.warmup):
-            oracle_batch_sample(specs, graphs, 2.0)
-        tot_e, tot_t, cnt = 0, 0.0, 0
+            pool.step()
+        tot_e, tot_t = 0, 0.0
         for _ in range(args.steps):
-            e, dt, c = oracle_batch_sample(specs, graphs, 10.0)
-            tot_e, tot_t, cnt = tot_e + e, tot_t + dt, c
-        value = tot_e / tot_t / 1e9
-        sample = f"the batch's first {cnt} graphs in order (about 10 s of oracle time per step), single-threaded"
-        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-                "data": "synthetic", "config": {"workload": w["desc"]},
-                "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
-                "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return
-    for _ in range(args.warmup):
-        run_oracle_sample(g, w["k"])
-    tot_e, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        e, dt, res = run_oracle_sample(g, w["k"])
-        tot_e += e
-        tot_t += dt
+            e, wall, _ = pool.step()
+            tot_e += e
+            tot_t += wall
+    finally:
+        pool.close()
     value = tot_e / tot_t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": w["desc"], "n": g.n, "m_dir": g.m_dir, "k": w["k"]},
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"one full oracle partition of the workload per step (cut {res.cut})"},
+            "data": "synthetic", "config": {"workload": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": pool.cores, "kind": "oracle",
+                             "sample": pool.desc, **cpu_info()},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------- digests
+DIGESTS = os.path.join(ROOT, "tests", "golden", "fullsize_digests.json")
+
+
+def _sha(*arrays) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for a, dt in arrays:
+        h.update(np.ascontiguousarray(a, dtype=dt).tobytes())
+    return h.hexdigest()
+
+
+def digest_check(gp, workload, dg=None, part=None, res=None, parts=None):
+    """Compares the GPU's results with the oracle's stored digests of this full-size workload."""
+    if not os.path.exists(DIGESTS):
+        return None
+    with open(DIGESTS) as f:
+        gold = json.load(f).get(workload)
+    if gold is None:
+        return None
+    if workload == "rmat24":
+        ok = _sha((part.cpu().numpy(), "<i4")) == gold["part_sha256"] and res.cut == gold["cut"]
+        return {"what": "full partition (labels of every vertex, cut)", "match": bool(ok)}
+    if workload == "batch512":
+        bad = [i for i, (p_, g_) in enumerate(zip(parts, gold["graphs"]))
+               if _sha((p_.cpu().numpy(), "<i4"))[:32] != g_["part_sha256"]]
+        return {"what": "every graph's partition", "graphs": len(parts), "match": not bad, "mismatched": bad[:10]}
+    if workload == "rmat26w":
+        import torch
+        lab, st = gp.lp_cluster(dg, gold["U"], gold["rounds"], int(gold["seed_hash"]))
+        ok_lab = _sha((lab.cpu().numpy(), "<i4")) == gold["labels_sha256"]
+        ok_st = all(st[k] == gold["lp_stats"][k] for k in gold["lp_stats"])
+        cg, f2c = gp.contract(dg, lab)
+        ok_f2c = _sha((f2c.cpu().numpy(), "<i4")) == gold["f2c_sha256"]
+        h = cg.to_host()
+        cg.free()
+        ok_c = (h.n == gold["coarse_n"] and h.m_dir == gold["coarse_m_dir"] and
+                _sha((h.off, "<i8"), (h.adj, "<i4"), (h.vw, "<i8"), (h.ew, "<i8")) == gold["coarse_sha256"])
+        del lab, f2c
+        torch.cuda.empty_cache()
+        return {"what": "level-0 gp_lp_cluster (labels, counters) and gp_contract (map, coarse CSR) at full size",
+                "match": bool(ok_lab and ok_st and ok_f2c and ok_c),
+                "labels": ok_lab, "lp_stats": ok_st, "f2c": ok_f2c, "coarse_csr": ok_c}
+    return None
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rgg20", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="rmat26w", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-digest", action="store_true")
     ap.add_argument("--once", action="store_true", help="one untimed partition (for profiler launch lists)")
     ap.add_argument("--mode", default="plain", choices=["plain", "learned"])
     ap.add_argument("--no-compare", action="store_true", help="skip the learned and batched comparisons")
+    ap.add_argument("--learned-seeds", type=int, default=None,
+                    help="seeds 1..S of the learned-vs-plain comparison (default 10, 1 when a partition takes > 2 s)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     w = WORKLOADS[args.workload]
     is_batch = w["kind"] == "batch"
     if args.impl == "reference":
-        bench_reference(args, make_batch(w["count"]) if is_batch else make_graph(args.workload), w)
+        bench_reference(args, w)
         return
 
     import torch
@@ -394,14 +569,15 @@ def main():
     gp.build()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > 129 MB L2
     stream = torch.cuda.current_stream()
+    batch_parts = None
     if is_batch:
         specs, graphs = make_batch(w["count"])
         dgs = batch_items(gp, graphs)
         ks = [sp.k for sp in specs]
         seeds = [sp.seed + rank for sp in specs]
         big = max(range(len(graphs)), key=lambda i: graphs[i].n)
-        dw, dc, _ = gp.autotune_schedule(dgs[big])
-        params = gp.default_params(deg_warp=dw, deg_cta=dc)
+        params, _ = gp.autotune(dgs[big])
+        dw, dc = params.deg_warp, params.deg_cta
         g = None
         k = None
 
@@ -409,7 +585,8 @@ def main():
             pass
 
         def step():
-            _, rs = gp.partition_batch(dgs, ks, EPS, seeds, params)
+            nonlocal batch_parts
+            batch_parts, rs = gp.partition_batch(dgs, ks, EPS, seeds, params)
             r = _Sum()
             r.lp_edges = sum(x.lp_edges for x in rs)
             r.cut = sum(x.cut for x in rs)
@@ -417,9 +594,12 @@ def main():
             r.lmax = None
             r.imbalanced = sum(x.imbalanced for x in rs)
             r.levels = max(x.levels for x in rs)
+            r.level_n = None
             return r
     else:
+        t_gen = time.perf_counter()
         g = make_graph(args.workload)
+        t_gen = time.perf_counter() - t_gen
         k = w["k"]
         dg = gp.DeviceGraph.from_host(g)
         part = torch.empty(g.n, dtype=torch.int32, device="cuda")
@@ -467,29 +647,19 @@ def main():
     ms_total = max_over_ranks(ms_local, dist)
     edges_all = sum_over_ranks(float(lp_edges_step * args.steps), dist)
     value = edges_all / (ms_total * 1e-3) / 1e9
+    ms_step = ms_total / args.steps
 
-    kernels = [e for e in prof if e["launches"] > 0 and e["bytes"] > 0 and not e["name"].startswith("lp_phase")]
-    top = max(kernels, key=lambda e: e["ms"]) if kernels else None
     peak, peak_kind = peaks()
-    roofline = None
-    if top:
-        achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": lp_traffic(args.workload) if top["name"] == "lp_persistent" else None,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per k_lp launch, "
-                                      + TRAFFIC_SUMMARY.get(args.workload, "none"),
-                    "kernel": top["name"], "launches": top["launches"],
-                    "ms_per_launch": top["ms"] / top["launches"], "bytes_per_launch": top["bytes"] / top["launches"],
-                    "peak_source": "measured hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-                    "kernels_ms_per_step": {e["name"]: e["ms"] / args.steps for e in prof if e["launches"] > 0 and not e["name"].startswith("lp_phase")},
-                    "kernels_achieved_gbs": {e["name"]: {"gbs": e["bytes"] / (e["ms"] * 1e-3) / 1e9,
-                                                         "frac": e["bytes"] / (e["ms"] * 1e-3) / 1e9 / peak}
-                                             for e in prof if e["launches"] > 0 and e["bytes"] > 0 and e["ms"] > 0},
-                    "lp_phases_ms_per_step": {e["name"][9:]: e["ms"] / args.steps for e in prof if e["name"].startswith("lp_phase")},
-                    "contest_calls_per_step": {e["name"][11:-6]: e["items"] / args.steps for e in prof if e["name"].startswith("lp_contest")}}
+    roofline, lp_only = lp_roofline(prof, args, peak, peak_kind)
+
+    digest = None
+    if rank == 0 and not args.no_digest:
+        digest = digest_check(gp, args.workload, dg=None if is_batch else dg, part=None if is_batch else part,
+                              res=res, parts=batch_parts)
 
     # ---- pass B: end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
+    e2e_steps = args.steps if ms_step < 2000 else min(args.steps, 3)
     if not args.no_e2e and is_batch:
         # host CSR in pinned memory; every step copies all graphs in, partitions, copies the parts out
         hosts = [(torch.from_numpy(np.ascontiguousarray(x.off)).pin_memory(),
@@ -510,59 +680,65 @@ def main():
         e2e_step()
         barrier(dist)
         t0 = time.perf_counter()
-        for i in range(args.steps):
+        for i in range(e2e_steps):
             e2e_step()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        e2e = {"value": edges_all / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / args.steps}
+        e2e = {"value": lp_edges_step * world * e2e_steps / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps}
     elif not args.no_e2e and params is None:
         hg = gp.HostGraph(g, pin=True)
-        for _ in range(2):
-            gp.partition_host(hg, k, EPS, SEED + rank)
+        gp.partition_host(hg, k, EPS, SEED + rank)
         barrier(dist)
         t0 = time.perf_counter()
-        for i in range(args.steps):
+        for i in range(e2e_steps):
             gp.partition_host(hg, k, EPS, SEED + rank)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-        e2e = {"value": edges_all / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hg.h2d_bytes,
-               "d2h_bytes_per_step": hg.d2h_bytes, "ms_per_step": 1e3 * e2e_s / args.steps}
+        e2e = {"value": lp_edges_step * world * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": hg.h2d_bytes, "d2h_bytes_per_step": hg.d2h_bytes,
+               "ms_per_step": 1e3 * e2e_s / e2e_steps, "steps": e2e_steps}
+        del hg
 
     compare = None
     if rank == 0 and world == 1 and not args.no_compare and not is_batch and args.mode == "plain":
-        compare = {"learned": compare_learned(gp, args.workload, g, dg, k, args.steps, flush,
-                                              ms_total / args.steps, res),
+        nseeds = args.learned_seeds if args.learned_seeds is not None else (10 if ms_step < 2000 else 1)
+        compare = {"learned": compare_learned(gp, args.workload, g, dg, k, min(args.steps, 3), flush, ms_step, res,
+                                              nseeds),
                    "batched": compare_batched(gp, 3, flush)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and is_batch:
-        e, dt, cnt = oracle_batch_sample(specs, graphs, 10.0)
-        cpu = {"value": e / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"the batch's first {cnt} graphs in order, single-threaded ({dt:.1f} s)"}
-    elif rank == 0 and world == 1 and not args.no_cpu_baseline and args.mode == "plain":
-        e, dt, ores = run_oracle_sample(g, k)
-        cpu = {"value": e / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"one full single-threaded oracle partition of the same graph ({dt:.1f} s, cut {ores.cut}, "
-                         f"same cut as the GPU: {ores.cut == res.cut})"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = OraclePool(args.workload)
+        try:
+            e, wall_c, cpu_s = pool.step()
+        finally:
+            pool.close()
+        cpu = {"value": e / wall_c / 1e9, "unit": "GTEPS", "cores": pool.cores, "kind": "oracle",
+               "sample": pool.desc + f" ({wall_c:.1f} s wall, {cpu_s:.0f} s CPU)", **cpu_info()}
 
     if rank == 0:
         shape = ({"graphs": len(graphs), "n_total": int(sum(x.n for x in graphs)),
                   "m_dir_total": int(sum(x.m_dir for x in graphs)), "k": "2, 4 or 8 per graph",
-                  "schedule": {"deg_warp": dw, "deg_cta": dc, "picked_by": "gp_autotune_schedule on the largest graph"}}
-                 if is_batch else {"n": g.n, "m_dir": g.m_dir, "k": k, "mode": args.mode})
+                  "schedule": {"deg_warp": dw, "deg_cta": dc, "verts_per_block": params.verts_per_block,
+                               "hub_batch_slots": params.hub_batch_slots,
+                               "picked_by": "gp_autotune on the largest graph"}}
+                 if is_batch else {"n": g.n, "m_dir": g.m_dir, "k": k, "mode": args.mode,
+                                   "generation_s": round(t_gen, 1)})
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": {"workload": w["desc"], **shape,
                            "lp_edges_per_partition": lp_edges_step, "cut": res.cut,
                            "max_block_weight": res.max_block_weight, "lmax": res.lmax,
                            "imbalanced": res.imbalanced, "levels": res.levels,
-                           "ms_per_partition": ms_total / args.steps,
-                           "l2": "flushed between steps (256 MB write outside the per-step events)",
+                           "level_n": res.level_n, "ms_per_partition": ms_step,
+                           "lp_only_gteps": lp_only,
+                           "l2": "flushed between steps (256 MB write outside the per-step events); inputs "
+                                 + ("larger than L2" if (is_batch or g.m_dir * 4 > 129e6) else "smaller than L2"),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "wall_ms_per_step": 1e3 * wall / args.steps},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "compare": compare}
+                "clocks": clk.summary(), "oracle_digest_match": digest, "compare": compare}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -2007,9 +2007,13 @@ int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, 
 // Statistics, error flags and profile entries of n counter blocks (host copies). vb/eb: algorithmic
 // bytes per visit and per scanned entry of each job; stats: NULL or per-job outputs; edges/moves:
 // NULL or summed totals.
+// Algorithmic bytes per proposed move: the label write (4), the label-weight update (8) and the
+// admission key, written and read (16).
+constexpr int64_t kMoverBytes = 28;
+
 static int account_counters(const LpCounters *hc, int n, const int64_t *vb, const int64_t *eb, gp_lp_stats *const *stats,
-                            int64_t *edges_sum, int64_t *moves_sum) {
-  int64_t tot_edges = 0, tot_vis = 0, tot_bytes = 0, tot_moves = 0;
+                            int64_t *edges_sum, int64_t *moves_sum, const char *const *names) {
+  int64_t tot_edges = 0, tot_moves = 0;
   for (int j = 0; j < n; j++) {
     const LpCounters &h = hc[j];
     if (h.err) {
@@ -2021,11 +2025,12 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
       vis += (int64_t)h.bin_visits[b];
       edg += (int64_t)h.bin_edges[b];
     }
-    // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read;
-    // per scanned entry: adjacency, neighbour label, edge weight (and score)
-    tot_bytes += vis * vb[j] + edg * eb[j];
+    // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read (4);
+    // per scanned entry: adjacency, neighbour label, edge weight (and score); per proposed move its
+    // label write, weight update and admission key
+    prof_add_counts(names ? names[j] : "lp_persistent", vis, edg,
+                    vis * vb[j] + edg * eb[j] + (int64_t)h.movers * kMoverBytes);
     tot_edges += edg;
-    tot_vis += vis;
     tot_moves += (int64_t)h.moves;
     if (stats && stats[j]) {
       stats[j]->rounds = (int64_t)h.rounds;
@@ -2037,7 +2042,6 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
   }
   if (edges_sum) *edges_sum = tot_edges;
   if (moves_sum) *moves_sum = tot_moves;
-  prof_add_counts("lp_persistent", tot_vis, tot_edges, tot_bytes);
   if (profiling()) {
     static const char *names[8] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit",
                                    "lp_phase_contest", "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"};
@@ -2106,10 +2110,11 @@ int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves, 
   GP_TRY(rb.run(s));
   if (def.count == 0) return GP_OK;
   const int st = account_counters(hc.data(), def.count, def.visit_bytes.data(), def.entry_bytes.data(), nullptr, edges,
-                                  moves);
+                                  moves, def.names.data());
   def.count = 0;
   def.visit_bytes.clear();
   def.entry_bytes.clear();
+  def.names.clear();
   return st;
 }
 
@@ -2379,7 +2384,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   GP_CUDA(cudaMemcpyAsync(bs_dev, blk_start.data(), sizeof(int) * blk_start.size(), cudaMemcpyHostToDevice, s));
   GP_CUDA(cudaMemcpyAsync(bl_dev, blk_list.data(), sizeof(int) * blk_list.size(), cudaMemcpyHostToDevice, s));
   {
-    ProfScope ps("lp_persistent", s);
+    ProfScope ps(jobs[0].prof, s);
     int st;
     if (lq) st = ew == 0 ? launch_lp<0, true>(probs_dev, bs_dev, bl_dev, grid, s)
                : ew == 1 ? launch_lp<1, true>(probs_dev, bs_dev, bl_dev, grid, s)
@@ -2400,8 +2405,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     deferred->count += njobs;
     for (int j = 0; j < njobs; j++) {
       const DGraph &g = jobs[j].g;
-      deferred->visit_bytes.push_back(2 * g.offset_bytes() + 4 + g.vw_bytes() + 8);
+      deferred->visit_bytes.push_back(2 * g.offset_bytes() + 4 + g.vw_bytes() + 4);
       deferred->entry_bytes.push_back(8 + g.ew_bytes() + (jobs[j].q ? 4 : 0));
+      deferred->names.push_back(jobs[j].prof);
     }
     return GP_OK;
   }
@@ -2411,18 +2417,21 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   std::vector<int64_t> vb(njobs), eb(njobs);
   for (int j = 0; j < njobs; j++) {
     const DGraph &g = jobs[j].g;
-    vb[j] = 2 * g.offset_bytes() + 4 + g.vw_bytes() + 8;
+    vb[j] = 2 * g.offset_bytes() + 4 + g.vw_bytes() + 4;
     eb[j] = 8 + g.ew_bytes() + (jobs[j].q ? 4 : 0);
   }
   std::vector<gp_lp_stats *> st(njobs);
-  for (int j = 0; j < njobs; j++) st[j] = jobs[j].stats;
-  return account_counters(hc.data(), njobs, vb.data(), eb.data(), st.data(), nullptr, nullptr);
-  return GP_OK;
+  std::vector<const char *> names(njobs);
+  for (int j = 0; j < njobs; j++) {
+    st[j] = jobs[j].stats;
+    names[j] = jobs[j].prof;
+  }
+  return account_counters(hc.data(), njobs, vb.data(), eb.data(), st.data(), nullptr, nullptr, names.data());
 }
 
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U, int rounds,
            uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg, bool singletons,
-           LpClassInfo *classes, LpDeferred *deferred) {
+           LpClassInfo *classes, LpDeferred *deferred, const char *prof) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (g.n == 0 || rounds <= 0) return GP_OK;
   LpJob j;
@@ -2437,6 +2446,7 @@ int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int6
   j.stats = stats;
   j.singletons = singletons;
   j.classes = classes;
+  j.prof = prof;
   return run_lp_multi(&j, 1, s, cfg, deferred);
 }
 

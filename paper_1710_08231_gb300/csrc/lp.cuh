@@ -42,6 +42,7 @@ struct LpDeferred {
   void *dev = nullptr;
   int capacity = 0, count = 0;
   std::vector<int64_t> visit_bytes, entry_bytes;  // algorithmic bytes per visit and per entry, by job
+  std::vector<const char *> names;                // profile entry of each job
 };
 size_t lp_counters_bytes();
 // Reads every deferred counter block back (one synchronisation, shared with the caller's pending
@@ -67,6 +68,8 @@ struct LpJob {
   // label is distinct and no neighbour carries the own label, so connections need no aggregation
   bool singletons = false;
   LpClassInfo *classes = nullptr;  // optional cache of the graph's degree classes (see LpClassInfo)
+  // profile entry the job's counts go to (static string); the launch is timed under jobs[0]'s
+  const char *prof = "lp_persistent";
 };
 
 // Several independent LP runs in one cooperative launch; they must share the edge-weight type and
@@ -80,7 +83,8 @@ LpConfig lp_config_from(const gp_params *p);
 // seed is the run's hash seed. stats (host) may be NULL.
 int run_lp(const DGraph &g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
            int rounds, uint64_t seed, gp_lp_stats *stats, cudaStream_t s, const LpConfig &cfg,
-           bool singletons = false, LpClassInfo *classes = nullptr, LpDeferred *deferred = nullptr);
+           bool singletons = false, LpClassInfo *classes = nullptr, LpDeferred *deferred = nullptr,
+           const char *prof = "lp_persistent");
 
 // Block weights of a partition: bw[k] = sum of c(v) over part[v] = b (device). Sets *bad_dev
 // (device int, may be NULL) when a block id is outside [0,k).

@@ -234,7 +234,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       GP_LAUNCH_CHECK();
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
       GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1),
-                    nullptr, s, cfg, true, &level_cls[l], &lpdef));
+                    nullptr, s, cfg, true, &level_cls[l], &lpdef, l == 0 ? "lp_persistent_level0" : "lp_persistent"));
       Level lev;
       lev.f2c_bytes = sizeof(int32_t) * (size_t)gl.n;
       lev.f2c = (int32_t *)dev_alloc(lev.f2c_bytes, s);
