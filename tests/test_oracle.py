@@ -12,7 +12,8 @@ What pins each oracle function:
 * ``cut``                -- sum of crossing weights over an explicit edge list.
 * ``bisect``/``repair``  -- hand-traced cases (tests/golden/ip_hand.json).
 * ``partition``          -- brute-force optimum on tiny graphs (lower bound), balance, the
-                            closed-form water-filling of the degree-0 vertex rule.
+                            closed-form water-filling of the degree-0 vertex rule; its driver (stop
+                            rule, seeds, try choice, projection) by tests/test_oracle_driver.py.
 * ``mlp_*``              -- a closed-form forward case and central finite differences.
 * ``edge_features``      -- values worked by hand on a small graph.
 """
