@@ -43,6 +43,8 @@ WORKLOADS = {
     "grid256": dict(kind="grid", a=256, b=256, k=2, desc="2D 4-neighbour grid 256x256, unit weights, k=2, eps=0.03, seed 1"),
     "rmat24": dict(kind="rmat", scale=24, ef=16, k=16, weighted=False, desc="R-MAT scale 24, edge factor 16, (0.57,0.19,0.19), symmetrised, unit weights, k=16, eps=0.03, seed 1"),
     "rmat26w": dict(kind="rmat", scale=26, ef=16, k=64, weighted=True, desc="R-MAT scale 26, edge factor 16, edge weights in [1,8], k=64, eps=0.03, seed 1"),
+    # a 1/16-size stand-in of rmat26w for profiler captures
+    "rmat22w": dict(kind="rmat", scale=22, ef=16, k=64, weighted=True, desc="R-MAT scale 22, edge factor 16, edge weights in [1,8], k=64, eps=0.03, seed 1"),
     "batch512": dict(kind="batch", count=512, desc="batch of 512 uneven graphs (grids and RGGs, 1k-200k vertices, log-uniform), unit weights, k in {2,4,8}, eps=0.03, seed 1"),
 }
 EPS, SEED = 0.03, 1
@@ -126,6 +128,24 @@ def compare_learned(gp, name, g, dg, k, steps, flush, plain_ms, plain_res, nseed
             "training": {"graphs": "2 same-family graphs, seeds 101-102", "steps": 300, "lr": 1e-2,
                          "bce_first_last": loss},
             "note": "learned is reported as measured; worse cuts are not hidden"}
+
+
+def compare_ip_tries(gp, name, dg, k, ms_step, flush):
+    """Cut and time against the number of initial-partitioning tries I (Section IV-B runs the tries in
+    parallel; a larger I gave a lower cut in the paper's Section VI). On workloads whose partition
+    takes more than 2 s the sweep runs on the random geometric graph 2^20, k=16 instead."""
+    import graphgen as gg
+    if ms_step > 2000:
+        name, k = "rgg20", 16
+        dg = gp.DeviceGraph.from_host(gg.rgg(1 << 20, 12.0, SEED))
+    out = {"graph": WORKLOADS[name]["desc"], "per_tries": []}
+    for tries in (1, 2, 4, 8, 16):
+        params = gp.default_params(ip_tries=tries)
+        gp.partition(dg, k, EPS, SEED, params)
+        ms, (_, r) = time_steps(lambda: gp.partition(dg, k, EPS, SEED, params), 3, flush)
+        out["per_tries"].append({"ip_tries": tries, "cut": r.cut, "best_try": r.best_try, "imbalanced": r.imbalanced,
+                                 "ms_per_partition": ms / 3, "ms_initial": r.ms_initial})
+    return out
 
 
 def batch_items(gp, graphs):
@@ -363,6 +383,9 @@ SAMPLES = {
     "rmat24": ("one full oracle partition (k=16) per core of an R-MAT scale-17 graph of the same generator and "
                "parameters (seed 101 + core index); a full scale-24 oracle partition takes about 20 minutes",
                lambda i: [(("rmat", 17, 16, 101 + i, False), 16, SEED)]),
+    "rmat22w": ("one full oracle partition (k=64) per core of a weighted R-MAT scale-16 graph of the same generator "
+                "and parameters (seed 101 + core index)",
+                lambda i: [(("rmat", 16, 16, 101 + i, True), 64, SEED)]),
     "rmat26w": ("one full oracle partition (k=64) per core of a weighted R-MAT scale-16 graph of the same generator "
                 "and parameters (seed 101 + core index); one oracle LP round of the scale-26 graph alone takes "
                 "minutes",
@@ -704,7 +727,8 @@ def main():
         nseeds = args.learned_seeds if args.learned_seeds is not None else (10 if ms_step < 2000 else 1)
         compare = {"learned": compare_learned(gp, args.workload, g, dg, k, min(args.steps, 3), flush, ms_step, res,
                                               nseeds),
-                   "batched": compare_batched(gp, 3, flush)}
+                   "batched": compare_batched(gp, 3, flush),
+                   "ip_tries": compare_ip_tries(gp, args.workload, dg, k, ms_step, flush)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -23,7 +23,7 @@ from graphgen import Graph
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "liboracle.so")
-_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp"]
+_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp", "match.cpp"]
 _lib = None
 _lock = threading.Lock()
 
@@ -41,7 +41,11 @@ class OrLpStats(ctypes.Structure):
 class OrParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64),
                 ("coarse_min", I64), ("coarse_per_k", I64), ("stall_pct", I64),
-                ("max_levels", I64), ("ip_tries", I64), ("repair_rounds", I64)]
+                ("max_levels", I64), ("ip_tries", I64), ("repair_rounds", I64), ("coarsen_mode", I64)]
+
+
+class OrMatchStats(ctypes.Structure):
+    _fields_ = [("rounds", I64), ("pairs", I64)]
 
 
 class OrResult(ctypes.Structure):
@@ -81,6 +85,8 @@ def _load():
             lib.or_contract.restype = I32
             lib.or_contract.argtypes = [ctypes.POINTER(OrGraph), VP, I64, ctypes.POINTER(I64),
                                         ctypes.POINTER(I64), VP, VP, VP, VP, VP]
+            lib.or_match.restype = I32
+            lib.or_match.argtypes = [ctypes.POINTER(OrGraph), I64, I64, U64, VP, ctypes.POINTER(OrMatchStats)]
             lib.or_bisect.restype = I32
             lib.or_bisect.argtypes = [ctypes.POINTER(OrGraph), I64, U64, VP]
             lib.or_repair.restype = I64
@@ -189,6 +195,17 @@ def contract(g: Graph, labels, nl: int | None = None):
     assert rc == 0
     n2, m2 = nn.value, mm.value
     return Graph(n2, off[: n2 + 1].copy(), adj[:m2].copy(), vw[:n2].copy(), ew[:m2].copy(), "coarse"), f2c
+
+
+def match(g: Graph, U: int, rounds: int, seed: int):
+    """Matching-based clustering (handshake matching, clusters of one or two vertices); returns
+    (labels int32[n], {"rounds", "pairs"})."""
+    v = _View(g)
+    labels = np.zeros(g.n, dtype=np.int32)
+    st = OrMatchStats()
+    rc = _load().or_match(v.ref(), U, rounds, seed, _p(labels), ctypes.byref(st))
+    assert rc == 0
+    return labels, {"rounds": st.rounds, "pairs": st.pairs}
 
 
 def bisect(g: Graph, k: int, s_try: int) -> np.ndarray:

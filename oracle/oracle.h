@@ -46,7 +46,13 @@ typedef struct or_params {
   int64_t max_levels;
   int64_t ip_tries;
   int64_t repair_rounds;
+  int64_t coarsen_mode;       /* 0: LP clustering (the paper's), 1: matching (or_match) */
 } or_params;
+
+typedef struct or_match_stats {
+  int64_t rounds;             /* rounds run */
+  int64_t pairs;              /* matched pairs */
+} or_match_stats;
 
 typedef struct or_result {
   int64_t cut;
@@ -74,6 +80,11 @@ int64_t or_lmax(int64_t total_weight, int64_t k, double eps);
  * q (per CSR entry, or NULL) adds the learned tie-break and admission key. Returns 0 or -1. */
 int or_lp(const or_graph *g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
           int64_t rounds, uint64_t seed, or_lp_stats *st);
+
+/* Matching-based clustering (clusters of one or two vertices, Section III-A, Section VII): rounds of
+ * deterministic handshake matching under the bound c(u) + c(v) <= U. labels[n] out. */
+int or_match(const or_graph *g, int64_t U, int64_t rounds, uint64_t seed, int32_t *labels,
+             or_match_stats *st);
 
 /* Contraction of labels[n] (values in [0,nl)). Outputs sized for the worst case:
  * off_out[n+1], adj_out[m_dir], vw_out[n], ew_out[m_dir], f2c[n]. Writes n' and m' to *n_out, *m_out. */

@@ -20,7 +20,9 @@
 //     H(s_try, depth, v), a second BFS from the farthest vertex found (ties: smaller id), vertices
 //     ordered by (distance, id) with unreachable ones last, side 0 the shortest prefix whose weight
 //     reaches the ceil(k/2)/k share; then balance repair, then LP refinement;
-//   * the best try is the minimum of (cut, imbalanced, try index).
+//   * the best try is the minimum of (cut, imbalanced, try index);
+//   * with coarsen_mode = 1 the clustering of each level is the matching of match.cpp (same bound U,
+//     rounds_coarsen rounds at most, the same seed H(seed, l, 1)) instead of label propagation.
 // Seeds: coarsening LP at level l uses H(seed, l, 1); refinement at level l uses H(seed, l, 2); IP
 // try t on the coarsest level c uses s_try = H(seed, c, 4 + t) and refines with H(s_try, c, 3).
 #include <algorithm>
@@ -250,6 +252,7 @@ extern "C" void or_default_params(or_params *p) {
   p->max_levels = 64;
   p->ip_tries = 4;
   p->repair_rounds = 16;
+  p->coarsen_mode = 0;
 }
 
 extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t seed,
@@ -316,10 +319,14 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
         if (l >= n_q_levels) return -2;
         q = q_levels[l];
       }
-      or_lp_stats ls;
-      or_lp(&gl, q, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen,
-            or_hash3(seed, (uint64_t)l, 1), &ls);
-      res->lp_edges += ls.edges;
+      if (p.coarsen_mode == 1) {
+        or_match(&gl, U, p.rounds_coarsen, or_hash3(seed, (uint64_t)l, 1), labels.data(), nullptr);
+      } else {
+        or_lp_stats ls;
+        or_lp(&gl, q, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen,
+              or_hash3(seed, (uint64_t)l, 1), &ls);
+        res->lp_edges += ls.edges;
+      }
       OwnedGraph c;
       c.off.resize(gl.n + 1);
       c.adj.resize(gl.m_dir);

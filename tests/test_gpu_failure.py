@@ -82,24 +82,39 @@ gp_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
 gp_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 
-@pytest.mark.parametrize("budget", [0, 1, 3, 8])
-def test_allocator_failure_returns_oom_without_leak(gp, budget):
+def _install(gp, fa):
+    gp.lib().gp_set_allocator(ctypes.cast(fa.alloc, ctypes.c_void_p), ctypes.cast(fa.free, ctypes.c_void_p), None)
+
+
+def test_allocator_failure_returns_oom_without_leak(gp):
     g = gg.rmat(13, 8, seed=2)
     dg = gp.DeviceGraph.from_host(g)
     ref_part, ref_res = gp.partition(dg, 8, 0.03, 1)
     ref_part = ref_part.cpu().numpy()
     L = gp.lib()
-    fa = _FailingAllocator(budget)
-    L.gp_set_allocator(ctypes.cast(fa.alloc, ctypes.c_void_p), ctypes.cast(fa.free, ctypes.c_void_p), None)
+    import torch
+    # the number of allocator calls one partition makes with an empty block cache
+    counting = _FailingAllocator(10**9)
+    _install(gp, counting)
     try:
-        with pytest.raises(gp.GpError) as ei:
-            gp.partition(dg, 8, 0.03, 1)
-        assert ei.value.status == gp.GP_ERR_OOM
-        import torch
+        part, res = gp.partition(dg, 8, 0.03, 1)
+        assert np.array_equal(part.cpu().numpy(), ref_part)
+        need = counting.calls
+        assert need >= 1
+        # every allocation point in turn fails
+        for budget in range(need):
+            fa = _FailingAllocator(budget)
+            _install(gp, fa)  # (returns the previous allocator's cached blocks to it)
+            with pytest.raises(gp.GpError) as ei:
+                gp.partition(dg, 8, 0.03, 1)
+            assert ei.value.status == gp.GP_ERR_OOM, (budget, ei.value)
+            torch.cuda.synchronize()
+            L.gp_free_cached()  # blocks kept for reuse go back to this allocator
+            assert fa.calls >= budget + 1
+            assert not fa.live, f"budget {budget}: {len(fa.live)} blocks leaked"
         torch.cuda.synchronize()
-        L.gp_free_cached()  # blocks kept for reuse go back to this allocator
-        assert fa.calls > budget
-        assert not fa.live, f"{len(fa.live)} blocks leaked"
+        L.gp_free_cached()
+        assert not counting.live
     finally:
         gp._install_torch_allocator(L)
     part, res = gp.partition(dg, 8, 0.03, 1)

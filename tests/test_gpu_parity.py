@@ -302,3 +302,23 @@ def test_autotune_picks_valid_tiles_and_keeps_results(gp):
     part, res = gp.partition(dg, 16, 0.03, 1, params)
     part_o, res_o = O.partition(g, 16, 0.03, 1)
     assert np.array_equal(part.cpu().numpy(), part_o)
+
+
+@pytest.mark.parametrize("tries", [1, 7, 8, 16])
+@pytest.mark.parametrize("name,k", [("rgg15", 16), ("rmat12w", 8)])
+def test_partition_ip_tries_match_oracle(gp, tries, name, k):
+    """More initial-partitioning tries run as more problems of the same launches (Section IV-B: tries in
+    parallel); every try's cut and the try kept equal the oracle's."""
+    g = GRAPHS[name]
+    params = gp.default_params(ip_tries=tries)
+    oparams = O.default_params()
+    oparams.ip_tries = tries
+    if g.n < 20000:
+        params.coarse_min = oparams.coarse_min = 300
+    dg = gp.DeviceGraph.from_host(g)
+    part, res = gp.partition(dg, k, 0.03, 3, params)
+    part_o, res_o = O.partition(g, k, 0.03, 3, oparams)
+    assert res.try_cut == list(res_o.try_cut[:tries])
+    assert res.try_imbalanced == list(res_o.try_imbalanced[:tries])
+    assert res.best_try == res_o.best_try
+    assert np.array_equal(part.cpu().numpy(), part_o) and res.cut == res_o.cut

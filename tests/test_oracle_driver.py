@@ -63,8 +63,11 @@ def restated_partition(g, k, eps, seed, p=None, trace=None):
             gl = G[-1]
             U = max(int(gl.vw.max()), lmax // p.cluster_div)
             s1 = O.hash3(seed, lvl, 1)
-            labels, _, st = O.lp_cluster(gl, U, p.rounds_coarsen, s1)
-            lp_edges += st.edges
+            if p.coarsen_mode == 1:  # matching-based clustering
+                labels, _ = O.match(gl, U, p.rounds_coarsen, s1)
+            else:
+                labels, _, st = O.lp_cluster(gl, U, p.rounds_coarsen, s1)
+                lp_edges += st.edges
             gc, f2c = O.contract(gl, labels)
             t["levels"].append({"n": gl.n, "m_dir": gl.m_dir, "U": U, "seed": s1, "coarse_n": gc.n})
             G.append(gc)
@@ -158,6 +161,8 @@ CASES = [
     ("rgg2000_iso_k4", lambda: _with_isolated(gg.rgg(2000, 8.0, 3), 50), 4, dict(coarse_min=90)),
     ("grid30x30_norefine", lambda: gg.grid(30, 30), 4, dict(coarse_min=50, rounds_refine=0, repair_rounds=0)),
     ("rgg4000_default", lambda: gg.rgg(4000, 10.0, 11), 2, dict()),
+    ("grid40x40_matching", lambda: gg.grid(40, 40), 4, dict(coarse_min=100, coarsen_mode=1)),
+    ("rmat11_matching", lambda: gg.rmat(11, 8, seed=9), 4, dict(coarse_min=150, coarsen_mode=1)),
 ]
 
 
