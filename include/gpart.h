@@ -93,7 +93,7 @@ typedef struct gp_params {
   int32_t mode;           /* GP_MODE_PLAIN, GP_MODE_LEARNED or GP_MODE_BEST_OF */
   int32_t deg_warp;       /* degree-bin thresholds (0 = default); see gp_lp_cluster */
   int32_t deg_cta;
-  int32_t reserved;
+  int32_t coarsen;        /* GP_COARSEN_LP (the paper's clustering, default) or GP_COARSEN_MATCHING */
   const void *mlp;        /* device pointer to a gp_mlp (learned modes), else NULL */
   /* LP tile sizes (0 = default; never change results): hub table slots per batch of the multi-CTA
    * hub path (default 4M, clamped to [4096, 2^28]) and the fewest vertices per CTA of one LP problem
@@ -103,6 +103,9 @@ typedef struct gp_params {
 } gp_params;
 
 enum { GP_MODE_PLAIN = 0, GP_MODE_LEARNED = 1, GP_MODE_BEST_OF = 2 };
+/* Clustering of the coarsening phase: size-constrained LP, or matching (clusters of one or two
+ * vertices, see gp_match; plain mode only). */
+enum { GP_COARSEN_LP = 0, GP_COARSEN_MATCHING = 1 };
 
 /* Result of gp_partition (host struct, written by the call). */
 typedef struct gp_result {
@@ -208,6 +211,25 @@ int gp_lp_cluster(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
 int gp_lp_cluster_noalloc(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
                           const int32_t *edge_q, int32_t *labels_out, gp_lp_stats *stats,
                           gp_stream stream);
+
+/* Matching-based clustering (Section III-A names matchings, clusters of size two, as the other family
+ * of clusterings; Section VII plans a parallel matching for the coarsening of mesh-like graphs). The
+ * library's reading: deterministic handshake matching. Each round, every unmatched vertex v proposes
+ * to its unmatched neighbour u with c(v) + c(u) <= U of largest rating omega(v,u)^2 / (c(v) c(u))
+ * (compared exactly in 128-bit integers), ties to the larger H(seed, min(u,v), max(u,v)), then the
+ * smaller u; two vertices proposing to each other are matched. Rounds stop after one without a new
+ * pair or after `rounds`. Run to convergence this is the greedy matching in decreasing rating order.
+ *   labels_out: n int32 (device, caller-allocated): min(v, mate(v)) for matched v, else v
+ *   stats     : NULL or host struct
+ * Exact for omega < 2^44 and c < 2^40 (128-bit products). */
+typedef struct gp_match_stats {
+  int64_t rounds;  /* rounds run */
+  int64_t pairs;   /* matched pairs */
+  int64_t visits;  /* unmatched-vertex visits */
+  int64_t edges;   /* CSR entries scanned */
+} gp_match_stats;
+int gp_match(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed, int32_t *labels_out,
+             gp_match_stats *stats, gp_stream stream);
 
 /* Degree-bin schedule of gp_lp_cluster and gp_lp_refine (process-wide): vertices with
  * 32 < d <= deg_warp are handled by one warp, deg_warp < d <= deg_cta by one CTA, larger ones by

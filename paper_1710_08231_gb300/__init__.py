@@ -24,6 +24,7 @@ I64, U64, I32, DBL, VP, SZ = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, c
 GP_OK, GP_ERR_INVALID_ARG, GP_ERR_BAD_GRAPH, GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_INTERNAL, \
     GP_ERR_UNSUPPORTED = range(8)
 MODE_PLAIN, MODE_LEARNED, MODE_BEST_OF = 0, 1, 2
+COARSEN_LP, COARSEN_MATCHING = 0, 1
 
 
 class GpGraph(ctypes.Structure):
@@ -38,10 +39,17 @@ class GpLpStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GpMatchStats(ctypes.Structure):
+    _fields_ = [("rounds", I64), ("pairs", I64), ("visits", I64), ("edges", I64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GpParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64), ("coarse_min", I64),
                 ("coarse_per_k", I64), ("stall_pct", I64), ("max_levels", I64), ("ip_tries", I64),
-                ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("reserved", I32),
+                ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("coarsen", I32),
                 ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64)]
 
 
@@ -109,6 +117,8 @@ def lib():
         L.gp_lp_cluster_noalloc.restype = ctypes.c_int
         L.gp_lp_cluster_noalloc.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, VP,
                                             ctypes.POINTER(GpLpStats), VP]
+        L.gp_match.restype = ctypes.c_int
+        L.gp_match.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, ctypes.POINTER(GpMatchStats), VP]
         L.gp_lp_refine.restype = ctypes.c_int
         L.gp_lp_refine.argtypes = [ctypes.POINTER(GpGraph), I32, I64, I32, U64, VP, VP, ctypes.POINTER(GpLpStats), VP]
         L.gp_contract.restype = ctypes.c_int
@@ -273,6 +283,16 @@ def lp_cluster(dg: DeviceGraph, U: int, rounds: int, seed: int, q=None, stream=N
     st = GpLpStats()
     _check(lib().gp_lp_cluster(ctypes.byref(dg.desc), U, rounds, seed, q.data_ptr() if q is not None else None,
                                labels.data_ptr(), ctypes.byref(st), _stream(stream)), "gp_lp_cluster")
+    return labels[: dg.n], st.as_dict()
+
+
+def match(dg: DeviceGraph, U: int, rounds: int, seed: int, stream=None):
+    """Matching-based clustering (handshake matching); returns (labels int32 tensor, stats dict)."""
+    import torch
+    labels = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.adj.device)
+    st = GpMatchStats()
+    _check(lib().gp_match(ctypes.byref(dg.desc), U, rounds, seed, labels.data_ptr(), ctypes.byref(st),
+                          _stream(stream)), "gp_match")
     return labels[: dg.n], st.as_dict()
 
 

@@ -311,6 +311,10 @@ int partition_batch_device(const gp_batch_item *items, int count, const gp_param
     set_error("gp_partition_batch: params out of range");
     return GP_ERR_INVALID_ARG;
   }
+  if (p.coarsen != GP_COARSEN_LP) {
+    set_error("gp_partition_batch: only LP clustering coarsens a batch");
+    return GP_ERR_INVALID_ARG;
+  }
   if (p.mode != GP_MODE_PLAIN && p.mode != GP_MODE_LEARNED) {
     set_error("gp_partition_batch: mode must be plain or learned");
     return GP_ERR_INVALID_ARG;

@@ -18,6 +18,7 @@
 #include "gp_internal.cuh"
 #include "ip.cuh"
 #include "lp.cuh"
+#include "match.cuh"
 #include "mlp.cuh"
 
 namespace gp {
@@ -160,6 +161,10 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     return GP_ERR_INVALID_ARG;
   }
   const bool learned = p.mode == GP_MODE_LEARNED;
+  if (p.coarsen != GP_COARSEN_LP && (p.coarsen != GP_COARSEN_MATCHING || p.mode != GP_MODE_PLAIN)) {
+    set_error("gp_partition: coarsen must be GP_COARSEN_LP, or GP_COARSEN_MATCHING in plain mode");
+    return GP_ERR_INVALID_ARG;
+  }
   if ((p.mode == GP_MODE_LEARNED || p.mode == GP_MODE_BEST_OF) && !p.mlp) {
     set_error("learned modes need params.mlp");
     return GP_ERR_INVALID_ARG;
@@ -233,8 +238,12 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       (::gp::count_launch(), k_vw_to_i64<<<grid_n(gl.n), 256, 0, s>>>(gl, lw));
       GP_LAUNCH_CHECK();
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
-      GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1),
-                    nullptr, s, cfg, true, &level_cls[l], &lpdef, l == 0 ? "lp_persistent_level0" : "lp_persistent"));
+      if (p.coarsen == GP_COARSEN_MATCHING)
+        GP_TRY(run_match(gl, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1), labels, nullptr, s, false));
+      else
+        GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen,
+                      hash3(seed, (uint64_t)l, 1), nullptr, s, cfg, true, &level_cls[l], &lpdef,
+                      l == 0 ? "lp_persistent_level0" : "lp_persistent"));
       Level lev;
       lev.f2c_bytes = sizeof(int32_t) * (size_t)gl.n;
       lev.f2c = (int32_t *)dev_alloc(lev.f2c_bytes, s);
@@ -489,6 +498,27 @@ int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, 
   }
   GP_TRY(run_lp(g, edge_q, labels_out, lw, g.n, U, rounds, seed, stats, s, schedule_for(nullptr), true));
   GP_TRY(prof_flush(s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  return GP_OK;
+}
+
+int gp_match(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, int32_t *labels_out,
+             gp_match_stats *stats, gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if ((!labels_out && gd->n > 0) || rounds < 0 || U < 1) {
+    set_error("gp_match: labels_out, rounds or U out of range");
+    return GP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DGraph g = make_dgraph(gd);
+  MatchStats m;
+  GP_TRY(run_match(g, U, rounds, seed, labels_out, &m, s, stats != nullptr));
+  if (stats) {
+    stats->rounds = m.rounds;
+    stats->pairs = m.pairs;
+    stats->visits = m.visits;
+    stats->edges = m.edges;
+  }
   GP_CUDA(cudaStreamSynchronize(s));
   return GP_OK;
 }
