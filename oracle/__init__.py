@@ -23,7 +23,7 @@ from graphgen import Graph
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "liboracle.so")
-_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp", "match.cpp"]
+_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp", "match.cpp", "mls.cpp"]
 _lib = None
 _lock = threading.Lock()
 
@@ -41,7 +41,17 @@ class OrLpStats(ctypes.Structure):
 class OrParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64),
                 ("coarse_min", I64), ("coarse_per_k", I64), ("stall_pct", I64),
-                ("max_levels", I64), ("ip_tries", I64), ("repair_rounds", I64), ("coarsen_mode", I64)]
+                ("max_levels", I64), ("ip_tries", I64), ("repair_rounds", I64), ("coarsen_mode", I64),
+                ("mls", I64)]
+
+
+class OrMlsParams(ctypes.Structure):
+    _fields_ = [("global_iters", I64), ("alpha_pct", I64), ("max_local", I64), ("max_moves", I64),
+                ("fruitless", I64), ("queue_cap", I64), ("max_degree", I64)]
+
+
+class OrMlsStats(ctypes.Structure):
+    _fields_ = [("gain", I64), ("moves", I64), ("searches", I64), ("local_iters", I64)]
 
 
 class OrMatchStats(ctypes.Structure):
@@ -87,6 +97,11 @@ def _load():
                                         ctypes.POINTER(I64), VP, VP, VP, VP, VP]
             lib.or_match.restype = I32
             lib.or_match.argtypes = [ctypes.POINTER(OrGraph), I64, I64, U64, VP, ctypes.POINTER(OrMatchStats)]
+            lib.or_mls_default_params.restype = None
+            lib.or_mls_default_params.argtypes = [ctypes.POINTER(OrMlsParams)]
+            lib.or_mls.restype = I64
+            lib.or_mls.argtypes = [ctypes.POINTER(OrGraph), I64, I64, U64, ctypes.POINTER(OrMlsParams), VP,
+                                   ctypes.POINTER(OrMlsStats)]
             lib.or_bisect.restype = I32
             lib.or_bisect.argtypes = [ctypes.POINTER(OrGraph), I64, U64, VP]
             lib.or_repair.restype = I64
@@ -206,6 +221,21 @@ def match(g: Graph, U: int, rounds: int, seed: int):
     rc = _load().or_match(v.ref(), U, rounds, seed, _p(labels), ctypes.byref(st))
     assert rc == 0
     return labels, {"rounds": st.rounds, "pairs": st.pairs}
+
+
+def mls_default_params() -> OrMlsParams:
+    p = OrMlsParams()
+    _load().or_mls_default_params(ctypes.byref(p))
+    return p
+
+
+def mls(g: Graph, part, k: int, lmax_: int, seed: int, params: OrMlsParams | None = None):
+    """Multi-try k-way local search on a copy of `part`; returns (part, stats dict)."""
+    v = _View(g)
+    part = np.array(part, dtype=np.int32, copy=True)
+    st = OrMlsStats()
+    _load().or_mls(v.ref(), k, lmax_, seed, ctypes.byref(params) if params else None, _p(part), ctypes.byref(st))
+    return part, {"gain": st.gain, "moves": st.moves, "searches": st.searches, "local_iters": st.local_iters}
 
 
 def bisect(g: Graph, k: int, s_try: int) -> np.ndarray:

@@ -47,6 +47,8 @@ typedef struct or_params {
   int64_t ip_tries;
   int64_t repair_rounds;
   int64_t coarsen_mode;       /* 0: LP clustering (the paper's), 1: matching (or_match) */
+  int64_t mls;                /* 0: off; else MLS (default parameters) after the LP refinement of
+                                 every level, seed H(seed, level, 7) */
 } or_params;
 
 typedef struct or_match_stats {
@@ -85,6 +87,27 @@ int or_lp(const or_graph *g, const int32_t *q, int32_t *labels, int64_t *lw, int
  * deterministic handshake matching under the bound c(u) + c(v) <= U. labels[n] out. */
 int or_match(const or_graph *g, int64_t U, int64_t rounds, uint64_t seed, int32_t *labels,
              or_match_stats *st);
+
+/* Multi-try k-way local search (Section III-C, Section IV-C, Algorithm 1) on a k-way partition,
+ * part[n] in/out; never violates lmax on blocks that satisfy it. Parameters and readings: mls.cpp. */
+typedef struct or_mls_params {
+  int64_t global_iters;  /* 3 (Section VI) */
+  int64_t alpha_pct;     /* 10: a local iteration follows while its gain > 10% of the global one's */
+  int64_t max_local;     /* cap on local iterations per global iteration (16) */
+  int64_t max_moves;     /* moves per search (64) */
+  int64_t fruitless;     /* a search stops after this many moves without a new best prefix (16) */
+  int64_t queue_cap;     /* queued vertices per search (256) */
+  int64_t max_degree;    /* vertices of larger degree are never moved (1024) */
+} or_mls_params;
+typedef struct or_mls_stats {
+  int64_t gain;          /* cut reduction */
+  int64_t moves;         /* applied moves */
+  int64_t searches;      /* searches started */
+  int64_t local_iters;   /* local iterations run */
+} or_mls_stats;
+void or_mls_default_params(or_mls_params *p);
+int64_t or_mls(const or_graph *g, int64_t k, int64_t lmax, uint64_t seed, const or_mls_params *p, int32_t *part,
+               or_mls_stats *st);
 
 /* Contraction of labels[n] (values in [0,nl)). Outputs sized for the worst case:
  * off_out[n+1], adj_out[m_dir], vw_out[n], ew_out[m_dir], f2c[n]. Writes n' and m' to *n_out, *m_out. */

@@ -22,7 +22,9 @@
 //     reaches the ceil(k/2)/k share; then balance repair, then LP refinement;
 //   * the best try is the minimum of (cut, imbalanced, try index);
 //   * with coarsen_mode = 1 the clustering of each level is the matching of match.cpp (same bound U,
-//     rounds_coarsen rounds at most, the same seed H(seed, l, 1)) instead of label propagation.
+//     rounds_coarsen rounds at most, the same seed H(seed, l, 1)) instead of label propagation;
+//   * with mls != 0, multi-try k-way local search (mls.cpp, seed H(seed, l, 7)) follows the LP
+//     refinement of every level, the coarsest one (after the best try is kept) included.
 // Seeds: coarsening LP at level l uses H(seed, l, 1); refinement at level l uses H(seed, l, 2); IP
 // try t on the coarsest level c uses s_try = H(seed, c, 4 + t) and refines with H(s_try, c, 3).
 #include <algorithm>
@@ -253,6 +255,7 @@ extern "C" void or_default_params(or_params *p) {
   p->ip_tries = 4;
   p->repair_rounds = 16;
   p->coarsen_mode = 0;
+  p->mls = 0;
 }
 
 extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t seed,
@@ -370,6 +373,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
         cur = pt;
       }
     }
+    if (p.mls) {
+      const or_graph gcv = G.back().view();
+      or_mls(&gcv, k, lmax, or_hash3(seed, (uint64_t)levels, 7), nullptr, cur.data(), nullptr);
+    }
     // Uncoarsening: project, then refine.
     for (int64_t l = levels - 1; l >= 0; l--) {
       const or_graph gl = G[l].view();
@@ -381,6 +388,7 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       or_lp(&gl, nullptr, fine.data(), bw.data(), k, lmax, p.rounds_refine,
             or_hash3(seed, (uint64_t)l, 2), &ls);
       res->lp_edges += ls.edges;
+      if (p.mls) or_mls(&gl, k, lmax, or_hash3(seed, (uint64_t)l, 7), nullptr, fine.data(), nullptr);
       cur.swap(fine);
     }
     res->levels = levels;

@@ -14,7 +14,9 @@ the composition itself, which no primitive test sees:
 * projection: level l's partition is the coarser level's partition read through level l's map, and
   it has the coarse partition's cut and block weights (Section III-A: the quotient graph keeps cut and
   balance of a partition that does not split clusters);
-* degree-0 vertices: removed before coarsening with ids re-ranked, placed last.
+* degree-0 vertices: removed before coarsening with ids re-ranked, placed last;
+* the options: matching instead of LP clustering, and multi-try local search after every level's
+  LP refinement (seed H(seed, l, 7)).
 
 The check restates the multilevel scheme of Sections III and IV step by step in Python, calling only
 the pinned primitives, exposes every intermediate value (tests/golden/partition_trace.json records
@@ -91,6 +93,8 @@ def restated_partition(g, k, eps, seed, p=None, trace=None):
                       for tr, x in enumerate(tries)]
         t["best_try"] = best[2]
         cur = best[3]
+        if p.mls:  # multi-try local search after the coarsest level's refinement
+            cur, _ = O.mls(gc, cur, k, lmax, O.hash3(seed, c, 7))
         t["uncoarsen"] = []
         for lvl in range(c - 1, -1, -1):
             fine = cur[maps[lvl]]
@@ -100,6 +104,8 @@ def restated_partition(g, k, eps, seed, p=None, trace=None):
             assert cc == cf and np.array_equal(bwc, bwf)
             fine, _, st = O.lp_refine(G[lvl], fine, k, lmax, p.rounds_refine, O.hash3(seed, lvl, 2))
             lp_edges += st.edges
+            if p.mls:
+                fine, _ = O.mls(G[lvl], fine, k, lmax, O.hash3(seed, lvl, 7))
             t["uncoarsen"].append({"level": lvl, "projected_cut": cf, "refined_cut": O.cut(G[lvl], fine, k)[0]})
             cur = fine
     part = np.zeros(n, dtype=np.int32)
@@ -163,6 +169,8 @@ CASES = [
     ("rgg4000_default", lambda: gg.rgg(4000, 10.0, 11), 2, dict()),
     ("grid40x40_matching", lambda: gg.grid(40, 40), 4, dict(coarse_min=100, coarsen_mode=1)),
     ("rmat11_matching", lambda: gg.rmat(11, 8, seed=9), 4, dict(coarse_min=150, coarsen_mode=1)),
+    ("rgg3000_mls", lambda: gg.rgg(3000, 9.0, 7), 8, dict(coarse_min=100, coarse_per_k=8, mls=1)),
+    ("grid30x30_mls_matching", lambda: gg.grid(30, 30), 4, dict(coarse_min=50, mls=1, coarsen_mode=1)),
 ]
 
 
