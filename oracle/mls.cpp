@@ -31,6 +31,10 @@
 //   * the adaptive stopping rule of Osipov and Sanders is replaced by fixed bounds: a search stops after
 //     `max_moves` moves or `fruitless` consecutive moves that do not improve its best prefix; the
 //     queue holds at most `queue_cap` vertices (further insertions are skipped);
+//   * "marked" is read as "queued or already moved by this search": when a vertex moves, each of its
+//     neighbours that is queued gets its key recomputed (and leaves the queue if no longer movable),
+//     and each one that is neither queued nor moved is inserted if movable (the start vertex and its
+//     neighbours are inserted the same way, in row order);
 //   * vertices of degree > `max_degree` are never queued or moved (hubs of power-law graphs would make
 //     a single search cost the square of their degree);
 //   * a search keeps its best prefix only when that prefix has positive gain;
@@ -117,10 +121,9 @@ std::vector<Move> perform_moves(const or_graph *g, int32_t v, const int32_t *par
   auto block_of = [&](int32_t u) { return view.block(u); };
   std::set<Key> pq;
   std::unordered_map<int32_t, Key> queued;  // vertex -> its key while queued
-  std::set<int32_t> touched, done;
+  std::set<int32_t> done;                   // moved by this search
   auto try_insert = [&](int32_t x) {
-    if (touched.count(x) || degree(g, x) > p.max_degree) return;
-    touched.insert(x);
+    if (queued.count(x) || done.count(x) || degree(g, x) > p.max_degree) return;
     if ((int64_t)queued.size() >= p.queue_cap) return;
     const Choice c = best_move(g, x, block_of, bw, lmax, s);
     if (!c.movable) return;
