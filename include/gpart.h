@@ -100,6 +100,10 @@ typedef struct gp_params {
    * (default 64, clamped to [16, 4096]) */
   int64_t hub_batch_slots;
   int64_t verts_per_block;
+  /* multi-try k-way local search after the LP refinement of every level (gp_mls with its default
+   * parameters and this many global iterations; 0 = off, the default; the paper's configuration uses 3).
+   * Plain mode, k <= 256. */
+  int64_t mls_global_iters;
 } gp_params;
 
 enum { GP_MODE_PLAIN = 0, GP_MODE_LEARNED = 1, GP_MODE_BEST_OF = 2 };
@@ -251,6 +255,36 @@ int gp_lp_set_tiles(int64_t hub_batch_slots, int64_t verts_per_block);
  * Returns GP_ERR_INVALID_ARG when a block id is out of range. */
 int gp_lp_refine(const gp_graph *g, int32_t k, int64_t lmax, int32_t rounds, uint64_t seed,
                  int32_t *part_inout, int64_t *block_w_out, gp_lp_stats *stats, gp_stream stream);
+
+/* Multi-try k-way local search, MLS (Section III-C; parallel form Section IV-C, Algorithm 1), on a k-way
+ * partition. Global iterations start from all boundary vertices; in every local iteration one search
+ * per todo vertex (one warp each) runs on the partition of the iteration's start: it queues the start
+ * vertex and its neighbours by gain, moves the vertex of largest gain (negative gains allowed), queues
+ * the neighbours of moved vertices and keeps its best prefix (PerformMoves); the recorded sequences are
+ * then applied in todo order with every gain recomputed on the current partition, each up to its best
+ * prefix (ApplyMoves). Local iterations continue on the moved vertices while their gain exceeds
+ * alpha_pct % of the global iteration's gain. The library's readings where the paper is open: todo
+ * lists ordered by H(s, v, 1); queue order (gain, H(s, w, 0), -w); targets the best adjacent block under
+ * lmax by (connection, H(s, w, b), -b); the adaptive stopping rule replaced by max_moves and fruitless;
+ * vertices of degree > max_degree never move. The cut never grows and no block ends above lmax unless
+ * it started there.
+ *   part_inout: n int32 in [0, k) (device); k <= 256
+ *   params    : NULL for gp_mls_default_params (3 global iterations, alpha 10 %, 16 local iterations,
+ *               64 moves, 16 fruitless moves, a queue of 256, degree bound 1024); max_moves <= 64,
+ *               queue_cap <= 256, else GP_ERR_UNSUPPORTED
+ *   stats     : NULL or host struct */
+typedef struct gp_mls_params {
+  int64_t global_iters, alpha_pct, max_local, max_moves, fruitless, queue_cap, max_degree;
+} gp_mls_params;
+typedef struct gp_mls_stats {
+  int64_t gain;         /* cut reduction */
+  int64_t moves;        /* applied moves */
+  int64_t searches;     /* searches run */
+  int64_t local_iters;  /* local iterations */
+} gp_mls_stats;
+void gp_mls_default_params(gp_mls_params *params);
+int gp_mls(const gp_graph *g, int32_t k, int64_t lmax, uint64_t seed, const gp_mls_params *params,
+           int32_t *part_inout, gp_mls_stats *stats, gp_stream stream);
 
 /* Contraction of a clustering (Section III-A; Section IV-A "Parallel Contraction"): cluster ids
  * are renumbered by their rank among the used ids (prefix sum over a used-flag array), the coarse

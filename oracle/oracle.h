@@ -47,8 +47,8 @@ typedef struct or_params {
   int64_t ip_tries;
   int64_t repair_rounds;
   int64_t coarsen_mode;       /* 0: LP clustering (the paper's), 1: matching (or_match) */
-  int64_t mls;                /* 0: off; else MLS (default parameters) after the LP refinement of
-                                 every level, seed H(seed, level, 7) */
+  int64_t mls;                /* 0: off; else MLS with this many global iterations (other parameters
+                                 default) after the LP refinement of every level, seed H(seed, level, 7) */
 } or_params;
 
 typedef struct or_match_stats {

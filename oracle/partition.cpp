@@ -373,9 +373,12 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
         cur = pt;
       }
     }
+    or_mls_params mp;
+    or_mls_default_params(&mp);
+    mp.global_iters = p.mls;
     if (p.mls) {
       const or_graph gcv = G.back().view();
-      or_mls(&gcv, k, lmax, or_hash3(seed, (uint64_t)levels, 7), nullptr, cur.data(), nullptr);
+      or_mls(&gcv, k, lmax, or_hash3(seed, (uint64_t)levels, 7), &mp, cur.data(), nullptr);
     }
     // Uncoarsening: project, then refine.
     for (int64_t l = levels - 1; l >= 0; l--) {
@@ -388,7 +391,7 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       or_lp(&gl, nullptr, fine.data(), bw.data(), k, lmax, p.rounds_refine,
             or_hash3(seed, (uint64_t)l, 2), &ls);
       res->lp_edges += ls.edges;
-      if (p.mls) or_mls(&gl, k, lmax, or_hash3(seed, (uint64_t)l, 7), nullptr, fine.data(), nullptr);
+      if (p.mls) or_mls(&gl, k, lmax, or_hash3(seed, (uint64_t)l, 7), &mp, fine.data(), nullptr);
       cur.swap(fine);
     }
     res->levels = levels;

@@ -50,7 +50,19 @@ class GpParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64), ("coarse_min", I64),
                 ("coarse_per_k", I64), ("stall_pct", I64), ("max_levels", I64), ("ip_tries", I64),
                 ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("coarsen", I32),
-                ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64)]
+                ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64), ("mls_global_iters", I64)]
+
+
+class GpMlsParams(ctypes.Structure):
+    _fields_ = [("global_iters", I64), ("alpha_pct", I64), ("max_local", I64), ("max_moves", I64),
+                ("fruitless", I64), ("queue_cap", I64), ("max_degree", I64)]
+
+
+class GpMlsStats(ctypes.Structure):
+    _fields_ = [("gain", I64), ("moves", I64), ("searches", I64), ("local_iters", I64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class GpResult(ctypes.Structure):
@@ -117,6 +129,11 @@ def lib():
         L.gp_lp_cluster_noalloc.restype = ctypes.c_int
         L.gp_lp_cluster_noalloc.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, VP,
                                             ctypes.POINTER(GpLpStats), VP]
+        L.gp_mls_default_params.restype = None
+        L.gp_mls_default_params.argtypes = [ctypes.POINTER(GpMlsParams)]
+        L.gp_mls.restype = ctypes.c_int
+        L.gp_mls.argtypes = [ctypes.POINTER(GpGraph), I32, I64, U64, ctypes.POINTER(GpMlsParams), VP,
+                             ctypes.POINTER(GpMlsStats), VP]
         L.gp_match.restype = ctypes.c_int
         L.gp_match.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, ctypes.POINTER(GpMatchStats), VP]
         L.gp_lp_refine.restype = ctypes.c_int
@@ -284,6 +301,24 @@ def lp_cluster(dg: DeviceGraph, U: int, rounds: int, seed: int, q=None, stream=N
     _check(lib().gp_lp_cluster(ctypes.byref(dg.desc), U, rounds, seed, q.data_ptr() if q is not None else None,
                                labels.data_ptr(), ctypes.byref(st), _stream(stream)), "gp_lp_cluster")
     return labels[: dg.n], st.as_dict()
+
+
+def mls_default_params(**overrides) -> GpMlsParams:
+    p = GpMlsParams()
+    lib().gp_mls_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mls(dg: DeviceGraph, part, k: int, lmax_: int, seed: int, params: Optional[GpMlsParams] = None, stream=None):
+    """Multi-try k-way local search on a copy of `part`; returns (part, stats dict)."""
+    import torch
+    part = part.to(torch.int32).clone()
+    st = GpMlsStats()
+    _check(lib().gp_mls(ctypes.byref(dg.desc), k, lmax_, seed, ctypes.byref(params) if params else None,
+                        part.data_ptr(), ctypes.byref(st), _stream(stream)), "gp_mls")
+    return part, st.as_dict()
 
 
 def match(dg: DeviceGraph, U: int, rounds: int, seed: int, stream=None):

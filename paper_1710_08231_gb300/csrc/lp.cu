@@ -259,8 +259,9 @@ __device__ __forceinline__ void write_slot(const LpProblem &P, int64_t idx, int 
 
 __device__ __forceinline__ unsigned slot_hash(int L) { return mix32((unsigned)L); }
 
-// Hub tables: round_up(2 d, 64) slots (a hub row has at most d distinct labels, so the load stays at
-// or below 1/2), indexed by a multiply-shift range reduction of the mixed label.
+// Hub tables: round_up(2 x, 64) slots for x = min(d, number of labels) (a hub row has at most that many
+// distinct labels, so the load stays at or below 1/2), indexed by a multiply-shift range reduction of
+// the mixed label.
 __host__ __device__ __forceinline__ int64_t hub_cap(int64_t d) { return ((2 * d + 63) / 64) * 64; }
 __device__ __forceinline__ uint64_t hub_slot(int L, uint64_t cap) {
   return ((uint64_t)slot_hash(L) * cap) >> 32;
@@ -982,7 +983,8 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     if (valid) {
       const int v = P.bin[6][i];
       d = P.g.row_begin(v + 1) - P.g.row_begin(v);
-      cap = hub_cap(d);
+      // a row has at most min(d, nl) distinct labels (refinement: nl = k blocks)
+      cap = min(hub_cap(d), hub_cap(P.nl));
       ch = (d + kHubChunk - 1) / kHubChunk;
       sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
@@ -1050,114 +1052,22 @@ __device__ __forceinline__ unsigned search_prefix(const T *pre, unsigned lo, uns
   return lo;
 }
 
-// Adds (L, w, q) to the hub table at tb (cap slots): claims L's slot by linear probing from hub_slot.
-// Called by lanes with `on`; the claims of a lane's up to kFlushBatch labels are in flight together.
-constexpr int kFlushBatch = 8;
-
-// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunk entries and every chunk is
-// taken by one warp, with no CTA-wide synchronisation: the warp aggregates its entries, 64 at a time,
-// in its own open-addressing table in shared memory (kWarpCap slots, equal labels of the 32 lanes
-// grouped first), and flushes that table into the hub's table in global memory whenever it holds
-// kWarpCap / 2 labels and at the end of the chunk, so labels that many entries share cost one global
-// claim per flush. The own-label connection is summed per chunk and added with one atomic.
-template <int EW, bool LQ>
-__device__ __forceinline__ void hub_flush(const LpProblem &P, int *keys, unsigned long long *vals, unsigned *qv,
-                                          int64_t tb, uint64_t cap) {
-  const int lane = threadIdx.x & 31;
-  constexpr int kH = kFlushBatch / 2;  // claims in flight per lane (two rounds per flush)
-  static_assert(kWarpCap == 32 * kFlushBatch, "a flush takes kFlushBatch table slots per lane");
-  __syncwarp();  // the lanes' inserts are visible to the whole warp
-#pragma unroll 1
-  for (int half = 0; half < 2; half++) {
-    int Ls[kH];
-    uint64_t sg[kH];
-    unsigned pend = 0;
-#pragma unroll
-    for (int q = 0; q < kH; q++) {
-      Ls[q] = keys[lane + 32 * (half * kH + q)];
-      if (Ls[q] >= 0) pend |= 1u << q;
-      sg[q] = Ls[q] >= 0 ? hub_slot(Ls[q], cap) : 0;
-    }
-    while (pend) {
-      int ks[kH];
-#pragma unroll
-      for (int q = 0; q < kH; q++) ks[q] = (pend >> q & 1) ? atomicCAS(&P.hub_keys[tb + sg[q]], -1, Ls[q]) : 0;
-#pragma unroll
-      for (int q = 0; q < kH; q++) {
-        if (!(pend >> q & 1)) continue;
-        if (ks[q] == -1 || ks[q] == Ls[q]) {
-          const int t = lane + 32 * (half * kH + q);
-          atomicAdd(&P.hub_vals[tb + sg[q]], vals[t]);
-          if (LQ) atomicAdd(&P.hub_qv[tb + sg[q]], qv[t]);
-          pend &= ~(1u << q);
-        } else {
-          sg[q] = sg[q] + 1 == cap ? 0 : sg[q] + 1;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kFlushBatch; q++) {
-    const int t = lane + 32 * q;
-    keys[t] = -1;
-    vals[t] = 0;
-    if (LQ) qv[t] = 0;
-  }
-  __syncwarp();
-}
-
-// warp_insert that also reports how many new labels the warp's lanes put into the table
-template <int EW, bool LQ>
-__device__ __forceinline__ unsigned warp_insert_new(int *keys, unsigned long long *vals, unsigned *qv, unsigned mask,
-                                                    bool on, int L, long long w, unsigned q) {
-  const unsigned peers = __match_any_sync(kFull, on ? L : -1);
-  const bool wide = EW != 0 && __any_sync(kFull, on && (w >= (1ll << 26) || w < 0));
-  long long sum = 0;
-  if (on) {
-    if constexpr (EW == 0) {
-      sum = __popc(peers);
-    } else if (!wide) {
-      sum = (long long)__reduce_add_sync(peers, (unsigned)w);
-    } else {
-      for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, w, __ffs(m) - 1);
-    }
-  }
-  unsigned qs = 0;
-  if (LQ && on) qs = __reduce_add_sync(peers, q);
-  bool fresh = false;
-  if (on && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-    unsigned sl = slot_hash(L) & mask;
-    while (true) {
-      const int k = atomicCAS(&keys[sl], -1, L);
-      if (k == -1 || k == L) {
-        atomicAdd(&vals[sl], (unsigned long long)sum);
-        if (LQ) atomicAdd(&qv[sl], qs);
-        fresh = k == -1;
-        break;
-      }
-      sl = (sl + 1) & mask;
-    }
-  }
-  return __popc(__ballot_sync(kFull, fresh));
-}
-
+// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunk entries. A block aggregates
+// its chunk's labels in a shared-memory table first and then adds one entry per distinct label to the
+// hub's table, so labels that many neighbours share cost one global atomic per chunk.
 template <int EW, bool LQ>
 __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm, unsigned char *dsm) {
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kWarpCap;
-  int *keys = reinterpret_cast<int *>(dsm + kWarps * kWarpCap * 8) + wid * kWarpCap;
-  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kWarps * kWarpCap * 12) + wid * kWarpCap;
-  __syncthreads();  // (the dynamic shared memory was the CTA table of the previous phase)
-  for (int t = lane; t < kWarpCap; t += 32) {
-    keys[t] = -1;
-    vals[t] = 0;
-    if (LQ) qv[t] = 0;
+  unsigned long long *svals = reinterpret_cast<unsigned long long *>(dsm);
+  int *skeys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
+  unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCtaCap * 12);
+  for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
+    skeys[t] = -1;
+    svals[t] = 0;
+    if (LQ) sq[t] = 0;
   }
-  __syncwarp();
-  constexpr unsigned kStep = 64;  // entries per insert step (two per lane)
+  __syncthreads();
   const unsigned c_lo = P.hub_prefix[h0], c_hi = P.hub_prefix[h1];
-  const unsigned gw = (unsigned)lb * kWarps + wid, nw = (unsigned)nb * kWarps;
-  for (unsigned c = c_lo + gw; c < c_hi; c += nw) {
+  for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
     const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
     const int v = P.bin[6][i];
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
@@ -1167,39 +1077,72 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
     const uint64_t cap = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]);
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    unsigned used = 0;
-    for (int64_t e0 = beg; e0 < end; e0 += kStep) {
-      if (used > kWarpCap / 2 - kStep) {
-        hub_flush<EW, LQ>(P, keys, vals, qv, tb, cap);
-        used = 0;
-      }
-      int64_t e[2];
-      int L[2];
-      long long w[2];
-      unsigned q2[2];
-      bool in[2];
+    // a chunk is at most kHubChunk = 4 * kThreads entries: each thread takes four, loads first
+    static_assert(kHubChunk == 4 * kThreads, "one step of four entries per thread covers a chunk");
+    {
+      int64_t e[4];
+      int L[4];
+      long long w[4];
+      unsigned q4[4];
+      bool in[4];
 #pragma unroll
-      for (int u = 0; u < 2; u++) {
-        e[u] = e0 + u * 32 + lane;
+      for (int u = 0; u < 4; u++) {
+        e[u] = beg + u * kThreads + threadIdx.x;
         in[u] = e[u] < end;
         L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
         w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
-        q2[u] = (LQ && in[u]) ? (unsigned)__ldg(P.q + e[u]) : 0u;
+        q4[u] = (LQ && in[u]) ? (unsigned)__ldg(P.q + e[u]) : 0u;
       }
 #pragma unroll
-      for (int u = 0; u < 2; u++) L[u] = in[u] ? P.labels[L[u]] : -1;
+      for (int u = 0; u < 4; u++) L[u] = in[u] ? P.labels[L[u]] : -1;
 #pragma unroll
-      for (int u = 0; u < 2; u++) {
+      for (int u = 0; u < 4; u++) {
         if (in[u] && L[u] == L0) c0 += w[u];
-        used += warp_insert_new<EW, LQ>(keys, vals, qv, kWarpCap - 1, in[u] && L[u] != L0, L[u], w[u], q2[u]);
+        warp_insert<EW, LQ>(skeys, svals, sq, kCtaCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u]);
       }
     }
-    __syncwarp();
-    if (used) hub_flush<EW, LQ>(P, keys, vals, qv, tb, cap);
-    c0 = warp_sum64(c0);
-    if (lane == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
+    c0 = block_sum_of(c0, sm);  // also completes the shared table
+    // flush into the hub's table: each thread claims the slots of four of its labels at once (the
+    // claims are in flight together), then retries the ones that met another label
+    static_assert(kCtaCap % (4 * kThreads) == 0, "the flush takes four table slots per thread per step");
+    for (int t0 = threadIdx.x; t0 < kCtaCap; t0 += 4 * kThreads) {
+      int Ls[4];
+      uint64_t sg[4];
+      bool pend[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        Ls[q] = skeys[t0 + q * kThreads];
+        pend[q] = Ls[q] >= 0;
+        sg[q] = pend[q] ? hub_slot(Ls[q], cap) : 0;
+      }
+      while (pend[0] || pend[1] || pend[2] || pend[3]) {
+        int ks[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) ks[q] = pend[q] ? atomicCAS(&P.hub_keys[tb + sg[q]], -1, Ls[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (!pend[q]) continue;
+          if (ks[q] == -1 || ks[q] == Ls[q]) {
+            const int t = t0 + q * kThreads;
+            atomicAdd(&P.hub_vals[tb + sg[q]], svals[t]);
+            if (LQ) atomicAdd(&P.hub_qv[tb + sg[q]], sq[t]);
+            pend[q] = false;
+          } else {
+            sg[q] = sg[q] + 1 == cap ? 0 : sg[q] + 1;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int t = t0 + q * kThreads;
+        skeys[t] = -1;
+        svals[t] = 0;
+        if (LQ) sq[t] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
   }
-  __syncthreads();
 }
 
 // Choice for batch [h0, h1), part 1: the batch's tables are scanned in items of kSlotChunk slots by all

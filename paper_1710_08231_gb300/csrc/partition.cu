@@ -19,6 +19,7 @@
 #include "ip.cuh"
 #include "lp.cuh"
 #include "match.cuh"
+#include "mls.cuh"
 #include "mlp.cuh"
 
 namespace gp {
@@ -161,6 +162,10 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     return GP_ERR_INVALID_ARG;
   }
   const bool learned = p.mode == GP_MODE_LEARNED;
+  if (p.mls_global_iters < 0 || (p.mls_global_iters > 0 && (p.mode != GP_MODE_PLAIN || k > 256))) {
+    set_error("gp_partition: multi-try local search needs plain mode and k <= 256");
+    return GP_ERR_INVALID_ARG;
+  }
   if (p.coarsen != GP_COARSEN_LP && (p.coarsen != GP_COARSEN_MATCHING || p.mode != GP_MODE_PLAIN)) {
     set_error("gp_partition: coarsen must be GP_COARSEN_LP, or GP_COARSEN_MATCHING in plain mode");
     return GP_ERR_INVALID_ARG;
@@ -292,6 +297,7 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       jobs[t].seed = hash3(s_try, (uint64_t)levels, 3);
       // degree classes of the coarsest graph from the contraction that built it (if any)
       jobs[t].classes = level_cls[levels].valid ? &level_cls[levels] : nullptr;
+      jobs[t].prof = "lp_persistent_ip";
     }
     if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg, &lpdef));
     // cuts of all tries in one pass; their block weights are the label weights the refinement kept
@@ -338,11 +344,22 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     // projection keeps every block's weight (a coarse vertex weighs what its members weigh), so the
     // block weights an LP refinement ends with are those the next finer level starts with
     GP_CUDA(cudaMemcpyAsync(bw, bws + (size_t)best * k, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToDevice, s));
+    MlsParams mp;
+    mls_default_params(&mp);
+    mp.global_iters = p.mls_global_iters;
+    if (mp.global_iters > 0) {
+      GP_TRY(run_mls(gc, k, lmax, hash3(seed, (uint64_t)levels, 7), mp, cur, nullptr, s));
+      GP_TRY(block_weights(gc, cur, k, bw, nullptr, s));
+    }
     for (int l = levels - 1; l >= 0; l--) {
       int32_t *fine = (cur == bufA) ? bufB : bufA;
       GP_TRY(project(cur, f2c[l], G[l].n, fine, s));
       GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), nullptr, s, cfg,
-                    false, &level_cls[l], &lpdef));
+                    false, &level_cls[l], &lpdef, "lp_persistent_refine"));
+      if (mp.global_iters > 0) {
+        GP_TRY(run_mls(G[l], k, lmax, hash3(seed, (uint64_t)l, 7), mp, fine, nullptr, s));
+        GP_TRY(block_weights(G[l], fine, k, bw, nullptr, s));
+      }
       cur = fine;
     }
     res->ms_refine = now_ms() - t_ref0;
@@ -518,6 +535,66 @@ int gp_match(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, int32
     stats->pairs = m.pairs;
     stats->visits = m.visits;
     stats->edges = m.edges;
+  }
+  GP_CUDA(cudaStreamSynchronize(s));
+  return GP_OK;
+}
+
+void gp_mls_default_params(gp_mls_params *q) {
+  if (!q) return;
+  MlsParams m;
+  mls_default_params(&m);
+  q->global_iters = m.global_iters;
+  q->alpha_pct = m.alpha_pct;
+  q->max_local = m.max_local;
+  q->max_moves = m.max_moves;
+  q->fruitless = m.fruitless;
+  q->queue_cap = m.queue_cap;
+  q->max_degree = m.max_degree;
+}
+
+int gp_mls(const gp_graph *gd, int32_t k, int64_t lmax, uint64_t seed, const gp_mls_params *params, int32_t *part,
+           gp_mls_stats *stats, gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if ((!part && gd->n > 0) || k < 1 || lmax < 0) {
+    set_error("gp_mls: part, k or lmax out of range");
+    return GP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DGraph g = make_dgraph(gd);
+  {
+    Workspace ws(s);
+    int64_t *bw;
+    int *bad;
+    GP_TRY(ws.get(&bw, (size_t)k));
+    GP_TRY(ws.zeros(&bad, 1));
+    GP_TRY(block_weights(g, part, k, bw, bad, s));
+    int hbad = 0;
+    GP_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (hbad) {
+      set_error("gp_mls: a block id is outside [0, k)");
+      return GP_ERR_INVALID_ARG;
+    }
+  }
+  MlsParams mp;
+  mls_default_params(&mp);
+  if (params) {
+    mp.global_iters = params->global_iters;
+    mp.alpha_pct = params->alpha_pct;
+    mp.max_local = params->max_local;
+    mp.max_moves = params->max_moves;
+    mp.fruitless = params->fruitless;
+    mp.queue_cap = params->queue_cap;
+    mp.max_degree = params->max_degree;
+  }
+  MlsStats m;
+  GP_TRY(run_mls(g, k, lmax, seed, mp, part, &m, s));
+  if (stats) {
+    stats->gain = m.gain;
+    stats->moves = m.moves;
+    stats->searches = m.searches;
+    stats->local_iters = m.local_iters;
   }
   GP_CUDA(cudaStreamSynchronize(s));
   return GP_OK;

@@ -93,8 +93,10 @@ def restated_partition(g, k, eps, seed, p=None, trace=None):
                       for tr, x in enumerate(tries)]
         t["best_try"] = best[2]
         cur = best[3]
+        mp = O.mls_default_params()
+        mp.global_iters = p.mls
         if p.mls:  # multi-try local search after the coarsest level's refinement
-            cur, _ = O.mls(gc, cur, k, lmax, O.hash3(seed, c, 7))
+            cur, _ = O.mls(gc, cur, k, lmax, O.hash3(seed, c, 7), mp)
         t["uncoarsen"] = []
         for lvl in range(c - 1, -1, -1):
             fine = cur[maps[lvl]]
@@ -105,7 +107,7 @@ def restated_partition(g, k, eps, seed, p=None, trace=None):
             fine, _, st = O.lp_refine(G[lvl], fine, k, lmax, p.rounds_refine, O.hash3(seed, lvl, 2))
             lp_edges += st.edges
             if p.mls:
-                fine, _ = O.mls(G[lvl], fine, k, lmax, O.hash3(seed, lvl, 7))
+                fine, _ = O.mls(G[lvl], fine, k, lmax, O.hash3(seed, lvl, 7), mp)
             t["uncoarsen"].append({"level": lvl, "projected_cut": cf, "refined_cut": O.cut(G[lvl], fine, k)[0]})
             cur = fine
     part = np.zeros(n, dtype=np.int32)
@@ -169,8 +171,8 @@ CASES = [
     ("rgg4000_default", lambda: gg.rgg(4000, 10.0, 11), 2, dict()),
     ("grid40x40_matching", lambda: gg.grid(40, 40), 4, dict(coarse_min=100, coarsen_mode=1)),
     ("rmat11_matching", lambda: gg.rmat(11, 8, seed=9), 4, dict(coarse_min=150, coarsen_mode=1)),
-    ("rgg3000_mls", lambda: gg.rgg(3000, 9.0, 7), 8, dict(coarse_min=100, coarse_per_k=8, mls=1)),
-    ("grid30x30_mls_matching", lambda: gg.grid(30, 30), 4, dict(coarse_min=50, mls=1, coarsen_mode=1)),
+    ("rgg3000_mls", lambda: gg.rgg(3000, 9.0, 7), 8, dict(coarse_min=100, coarse_per_k=8, mls=3)),
+    ("grid30x30_mls_matching", lambda: gg.grid(30, 30), 4, dict(coarse_min=50, mls=2, coarsen_mode=1)),
 ]
 
 
