@@ -237,8 +237,9 @@ int gp_match(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed, int32_
 
 /* Degree-bin schedule of gp_lp_cluster and gp_lp_refine (process-wide): vertices with
  * 32 < d <= deg_warp are handled by one warp, deg_warp < d <= deg_cta by one CTA, larger ones by
- * several CTAs. 0 restores the defaults (128, 1024). deg_warp is clamped to [32, 128] and deg_cta to
- * [deg_warp, 1024]. The schedule never changes results. gp_partition uses params.deg_warp/deg_cta
+ * several CTAs. 0 restores the defaults (128, 2048). deg_warp is clamped to [32, 256] and deg_cta to
+ * [deg_warp, 2048] (runs with scores: [32, 128] and [deg_warp, 1024]). The schedule never changes
+ * results. gp_partition uses params.deg_warp/deg_cta
  * when non-zero, else this schedule. */
 int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta);
 
@@ -361,7 +362,7 @@ int gp_partition_batch(const gp_batch_item *items, int32_t count, const gp_param
                        gp_result *res, gp_stream stream);
 
 /* Degree-bin schedule autotuner: times three LP rounds of g under a fixed set of (deg_warp, deg_cta)
- * candidates and returns the fastest (results never depend on the schedule). ms_out: NULL or the
+ * candidates (32..256, 256..2048) and returns the fastest (results never depend on the schedule). ms_out: NULL or the
  * best time. Pass the result in gp_params.deg_warp/deg_cta or to gp_lp_set_schedule. */
 int gp_autotune_schedule(const gp_graph *g, int32_t *deg_warp_out, int32_t *deg_cta_out, double *ms_out,
                          gp_stream stream);

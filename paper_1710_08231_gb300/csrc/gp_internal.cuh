@@ -260,7 +260,7 @@ __device__ __forceinline__ T block_excl_scan64(T x, T *tmp, T *total) {
 // differs from the value its own addition returned. A block that moves on to the next barrier adds
 // again, but bit 31 cannot flip back before every block has arrived there too. A problem of one block
 // needs only __syncthreads.
-// The wait is bounded in time: a block that has polled for more than `wait_ns` nanoseconds of the
+// The wait is bounded in time: a block that has polled for more than `wait_us` microseconds of the
 // global timer (or that sees another block's timeout) stores GP_ERR_TIMEOUT in `err` and returns false,
 // and so does every other waiting block once it sees the flag, so the kernel ends with every block
 // returned and the host reads the status.
@@ -276,7 +276,7 @@ struct GridBarrier {
   int *err;
   unsigned int nblocks;
   unsigned int rank;    // this block's index among the nblocks
-  unsigned long long wait_ns;
+  unsigned int wait_us; // limit of one wait in microseconds
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -305,7 +305,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier &b) {
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(b.count), "r"(inc) : "memory");
     const unsigned long long t0 = global_ns();
     while (((ld_acquire_u32(b.count) ^ old) & 0x80000000u) == 0) {
-      if (global_ns() - t0 > b.wait_ns || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
+      if (global_ns() - t0 > 1000ull * b.wait_us || *(volatile int *)b.err == GP_ERR_TIMEOUT) {
         atomicExch(b.err, GP_ERR_TIMEOUT);
         s_ok = 0;
         break;

@@ -38,9 +38,19 @@ constexpr int kBins = 7;     // G4, G8, G16, G32, WARP, CTA, HUB
 constexpr int kBinZero = 7;  // degree-0 visits (statistics only)
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kWarpCap = 256;   // table slots per warp (d <= 128)
-constexpr int kCtaCap = 2048;   // table slots per CTA (d <= 1024)
-constexpr int kHubChunk = 1024; // CSR entries per hub work item (pre-aggregated in a 2048-slot table)
+// Shared-memory tables: 12-byte slots (8-byte sum, 4-byte label) without scores, 16-byte slots with
+// (a 4-byte score sum more), in the same 48 KB of dynamic shared memory per CTA: 4096 or 2048 slots per
+// CTA, 512 or 256 per warp. A CTA table serves vertices of degree up to half its slots; a hub chunk of
+// kHubChunkOf<LQ> entries is pre-aggregated in it.
+template <bool LQ>
+constexpr int kWarpCapOf = LQ ? 256 : 512;
+template <bool LQ>
+constexpr int kCtaCapOf = LQ ? 2048 : 4096;
+template <bool LQ>
+constexpr int kHubChunkOf = LQ ? 1024 : 2048;
+constexpr int kWarpCap = kWarpCapOf<false>;  // the larger capacities (bounds of the schedule)
+constexpr int kCtaCap = kCtaCapOf<false>;
+constexpr int kHubChunk = 1024;              // the smaller chunk (bound of the work items)
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
 // Hub table slots per batch and the fewest vertices per block come from LpConfig (tile sizes picked by
@@ -49,7 +59,11 @@ constexpr int kContestSmall = 4096;
 // sub-round.
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
-constexpr size_t kDynSmem = kWarps * kWarpCap * 16 > kCtaCap * 16 ? kWarps * kWarpCap * 16 : kCtaCap * 16;
+constexpr size_t kDynSmem = 48 * 1024;
+static_assert(kWarps * kWarpCapOf<false> * 12 <= (int)kDynSmem && kWarps * kWarpCapOf<true> * 16 <= (int)kDynSmem,
+              "warp tables fit the dynamic shared memory");
+static_assert(kCtaCapOf<false> * 12 <= (int)kDynSmem && kCtaCapOf<true> * 16 <= (int)kDynSmem,
+              "CTA tables fit the dynamic shared memory");
 static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
 
@@ -87,7 +101,11 @@ struct LpProblem {
   int64_t vbase, lbase;
   int64_t nl, U;
   int64_t hub_batch_slots;     // hub table slots per batch (tile size of the hub path)
-  unsigned long long wait_ns;  // limit of every barrier wait
+  int64_t hub_chunk;           // hub row entries per accumulation work item (kHubChunkOf<LQ>)
+  int hub_chunk_shift;         // log2(hub_chunk)
+  int pad_chunk;
+  unsigned wait_us;            // limit of every barrier wait (microseconds)
+  unsigned pad_wait;
   uint64_t smix;  // mix64(seed)
   int rounds;
   int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
@@ -806,10 +824,11 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
   const unsigned cnt = V.bin_count[4];
   if (cnt == 0) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kWarpCap;
-  int *keys = reinterpret_cast<int *>(dsm + kWarps * kWarpCap * 8) + wid * kWarpCap;
-  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kWarps * kWarpCap * 12) + wid * kWarpCap;
-  for (int s = lane; s < kWarpCap; s += 32) {
+  constexpr int kCap = kWarpCapOf<LQ>;
+  unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kCap;
+  int *keys = reinterpret_cast<int *>(dsm + kWarps * kCap * 8) + wid * kCap;
+  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kWarps * kCap * 12) + wid * kCap;
+  for (int s = lane; s < kCap; s += 32) {
     keys[s] = -1;
     vals[s] = 0;
     if (LQ) qv[s] = 0;
@@ -891,11 +910,12 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
                            bool direct) {
   const unsigned cnt = V.bin_count[5];
   if (cnt == 0) return;
+  constexpr int kCap = kCtaCapOf<LQ>;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm);
-  int *keys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
-  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kCtaCap * 12);
+  int *keys = reinterpret_cast<int *>(dsm + kCap * 8);
+  unsigned *qv = reinterpret_cast<unsigned *>(dsm + kCap * 12);
   __syncthreads();
-  for (int s = threadIdx.x; s < kCtaCap; s += kThreads) {
+  for (int s = threadIdx.x; s < kCap; s += kThreads) {
     keys[s] = -1;
     vals[s] = 0;
     if (LQ) qv[s] = 0;
@@ -962,7 +982,7 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
   __syncthreads();
 }
 
-// Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (kHubChunk
+// Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (P.hub_chunk
 // entries), table slots (hub_cap(d) each) and choice items (kSlotChunk slots); cut into batches of
 // about P.hub_batch_slots slots (a hub starts a new batch when its slot prefix crosses a multiple of
 // that size); table base of each hub inside its batch.
@@ -985,7 +1005,7 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
       d = P.g.row_begin(v + 1) - P.g.row_begin(v);
       // a row has at most min(d, nl) distinct labels (refinement: nl = k blocks)
       cap = min(hub_cap(d), hub_cap(P.nl));
-      ch = (d + kHubChunk - 1) / kHubChunk;
+      ch = (d + P.hub_chunk - 1) >> P.hub_chunk_shift;
       sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
       sum_d += d;
@@ -1052,15 +1072,17 @@ __device__ __forceinline__ unsigned search_prefix(const T *pre, unsigned lo, uns
   return lo;
 }
 
-// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunk entries. A block aggregates
+// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunkOf<LQ> entries. A block aggregates
 // its chunk's labels in a shared-memory table first and then adds one entry per distinct label to the
 // hub's table, so labels that many neighbours share cost one global atomic per chunk.
 template <int EW, bool LQ>
 __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm, unsigned char *dsm) {
+  constexpr int kCap = kCtaCapOf<LQ>;
+  constexpr int kChunk = kHubChunkOf<LQ>;
   unsigned long long *svals = reinterpret_cast<unsigned long long *>(dsm);
-  int *skeys = reinterpret_cast<int *>(dsm + kCtaCap * 8);
-  unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCtaCap * 12);
-  for (int t = threadIdx.x; t < kCtaCap; t += kThreads) {
+  int *skeys = reinterpret_cast<int *>(dsm + kCap * 8);
+  unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCap * 12);
+  for (int t = threadIdx.x; t < kCap; t += kThreads) {
     skeys[t] = -1;
     svals[t] = 0;
     if (LQ) sq[t] = 0;
@@ -1071,15 +1093,15 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
     const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
     const int v = P.bin[6][i];
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
-    const int64_t end = min(re, beg + kHubChunk);
+    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kChunk;
+    const int64_t end = min(re, beg + kChunk);
     const int64_t tb = P.hub_tb[i];
     const uint64_t cap = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]);
     const int L0 = P.labels[P.vbase + v];
     long long c0 = 0;
-    // a chunk is at most kHubChunk = 4 * kThreads entries: each thread takes four, loads first
-    static_assert(kHubChunk == 4 * kThreads, "one step of four entries per thread covers a chunk");
-    {
+    // steps of 4 * kThreads entries: each thread takes four, loads first
+    static_assert(kChunk % (4 * kThreads) == 0 && 2 * kChunk <= kCap, "a chunk fills at most half the table");
+    for (int64_t s0 = beg; s0 < end; s0 += 4 * kThreads) {
       int64_t e[4];
       int L[4];
       long long w[4];
@@ -1087,7 +1109,7 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
       bool in[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        e[u] = beg + u * kThreads + threadIdx.x;
+        e[u] = s0 + u * kThreads + threadIdx.x;
         in[u] = e[u] < end;
         L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
         w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
@@ -1098,14 +1120,14 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         if (in[u] && L[u] == L0) c0 += w[u];
-        warp_insert<EW, LQ>(skeys, svals, sq, kCtaCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u]);
+        warp_insert<EW, LQ>(skeys, svals, sq, kCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u]);
       }
     }
     c0 = block_sum_of(c0, sm);  // also completes the shared table
     // flush into the hub's table: each thread claims the slots of four of its labels at once (the
     // claims are in flight together), then retries the ones that met another label
-    static_assert(kCtaCap % (4 * kThreads) == 0, "the flush takes four table slots per thread per step");
-    for (int t0 = threadIdx.x; t0 < kCtaCap; t0 += 4 * kThreads) {
+    static_assert(kCap % (4 * kThreads) == 0, "the flush takes four table slots per thread per step");
+    for (int t0 = threadIdx.x; t0 < kCap; t0 += 4 * kThreads) {
       int Ls[4];
       uint64_t sg[4];
       bool pend[4];
@@ -1220,8 +1242,8 @@ __device__ void hub_direct_part(const LpProblem &P, unsigned cnt, unsigned chunk
     const unsigned i = search_prefix(P.hub_prefix, 0, cnt, c);
     const int v = P.bin[6][i];
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kHubChunk;
-    const int64_t end = min(re, beg + kHubChunk);
+    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * P.hub_chunk;
+    const int64_t end = min(re, beg + P.hub_chunk);
     const int L0 = P.labels[P.vbase + v];
     const long long cv = P.g.vweight(v);
     Best b = no_best();
@@ -1719,7 +1741,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
   __syncthreads();
   const int lb = (int)blockIdx.x - P.block_begin, nb = P.block_count;
   LpCounters *ctr = P.ctr;
-  const GridBarrier bar{P.bar, &ctr->err, (unsigned)nb, (unsigned)lb, P.wait_ns};
+  // (built from the shared problem copy at every use, so that none of it stays in registers)
+#define bar (GridBarrier{P.bar, &P.ctr->err, (unsigned)nb, (unsigned)lb, P.wait_us})
   // block 0 of the problem accumulates barrier-to-barrier time per phase (all blocks meet there) in
   // shared memory and writes the totals once at the end
   __shared__ unsigned long long pacc[8];
@@ -1872,6 +1895,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
     for (int k = 0; k < 8; k++) ctr->phase_ns[k] = pacc[k];
   return true;
 }
+
+#undef bar
 
 // One launch runs every problem: block b runs the problems blk_list[blk_start[b] .. blk_start[b+1])
 // in order. A problem of several blocks is the only problem of each of its blocks; problems of one
@@ -2034,7 +2059,7 @@ int block_weights(const DGraph &g, const int32_t *part, int64_t k, int64_t *bw, 
 constexpr int64_t kMoverBytes = 28;
 
 static int account_counters(const LpCounters *hc, int n, const int64_t *vb, const int64_t *eb, gp_lp_stats *const *stats,
-                            int64_t *edges_sum, int64_t *moves_sum, const char *const *names) {
+                            int64_t *edges_sum, int64_t *moves_sum, const char *const *jnames) {
   int64_t tot_edges = 0, tot_moves = 0;
   for (int j = 0; j < n; j++) {
     const LpCounters &h = hc[j];
@@ -2050,7 +2075,7 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
     // algorithmic bytes: per visit two offsets, own label, own weight, one label-weight read (4);
     // per scanned entry: adjacency, neighbour label, edge weight (and score); per proposed move its
     // label write, weight update and admission key
-    prof_add_counts(names ? names[j] : "lp_persistent", vis, edg,
+    prof_add_counts(jnames ? jnames[j] : "lp_persistent", vis, edg,
                     vis * vb[j] + edg * eb[j] + (int64_t)h.movers * kMoverBytes);
     tot_edges += edg;
     tot_moves += (int64_t)h.moves;
@@ -2065,13 +2090,25 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
   if (edges_sum) *edges_sum = tot_edges;
   if (moves_sum) *moves_sum = tot_moves;
   if (profiling()) {
-    static const char *names[8] = {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit",
-                                   "lp_phase_contest", "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"};
-    for (int ph = 0; ph < 8; ph++) {
-      double ms = 0;
-      for (int j = 0; j < n; j++) ms += hc[j].phase_ns[ph] * 1e-6;
-      prof_add_time(names[ph], ms);
-    }
+    // phase times of refinement calls are kept apart (names with "_refine")
+    static const char *names[2][8] = {
+        {"lp_phase_classify", "lp_phase_choose", "lp_phase_hub_accum", "lp_phase_admit", "lp_phase_contest",
+         "lp_phase_final", "lp_phase_hub_choose", "lp_phase_hub_prefix"},
+        {"lp_phase_classify_refine", "lp_phase_choose_refine", "lp_phase_hub_accum_refine", "lp_phase_admit_refine",
+         "lp_phase_contest_refine", "lp_phase_final_refine", "lp_phase_hub_choose_refine",
+         "lp_phase_hub_prefix_refine"}};
+    for (int r = 0; r < 2; r++)
+      for (int ph = 0; ph < 8; ph++) {
+        double ms = 0;
+        bool any = false;
+        for (int j = 0; j < n; j++) {
+          const bool is_refine = jnames && std::strcmp(jnames[j], "lp_persistent_refine") == 0;
+          if (is_refine != (r == 1)) continue;
+          ms += hc[j].phase_ns[ph] * 1e-6;
+          any = true;
+        }
+        if (any) prof_add_time(names[r][ph], ms);
+      }
     double cs = 0, cp = 0, cl = 0, cli = 0, he = 0, hs = 0;
     for (int j = 0; j < n; j++) {
       cs += hc[j].contest_small;
@@ -2141,10 +2178,16 @@ int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves, 
 }
 
 // Several independent LP runs in one cooperative launch (same edge-weight type and score use).
-int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg, LpDeferred *deferred) {
+int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &cfg_in, LpDeferred *deferred) {
   if (njobs <= 0) return GP_OK;
   const int ew = jobs[0].g.ew_mode();
   const bool lq = jobs[0].q != nullptr;
+  // scored runs have the smaller shared-memory tables (16-byte slots)
+  LpConfig cfg = cfg_in;
+  if (lq) {
+    cfg.deg_warp = std::min(cfg.deg_warp, kWarpCapOf<true> / 2);
+    cfg.deg_cta = std::max(cfg.deg_warp, std::min(cfg.deg_cta, kCtaCapOf<true> / 2));
+  }
   for (int j = 0; j < njobs; j++) {
     if (jobs[j].stats) std::memset(jobs[j].stats, 0, sizeof(gp_lp_stats));
     if (jobs[j].g.ew_mode() != ew || (jobs[j].q != nullptr) != lq) {
@@ -2331,7 +2374,11 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.nl = jb.nl;
     P.U = jb.U;
     P.hub_batch_slots = cfg.hub_batch_slots;
-    P.wait_ns = wait_limit_ns();
+    P.hub_chunk = lq ? kHubChunkOf<true> : kHubChunkOf<false>;
+    P.hub_chunk_shift = lq ? 10 : 11;
+    static_assert(kHubChunkOf<true> == 1 << 10 && kHubChunkOf<false> == 1 << 11, "hub chunks are powers of two");
+    P.wait_us = (unsigned)std::min<unsigned long long>(std::max<unsigned long long>(wait_limit_ns() / 1000, 0),
+                                                        0xffffffffull);
     P.smix = mix64(jb.seed);
     P.rounds = jb.g.n > 0 ? jb.rounds : 0;
     P.singletons = jb.singletons ? 1 : 0;

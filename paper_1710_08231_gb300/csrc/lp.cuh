@@ -8,8 +8,8 @@
 namespace gp {
 
 struct LpConfig {
-  int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 128)
-  int deg_cta = 1024;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 1024)
+  int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 256; 128 with scores)
+  int deg_cta = 2048;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 2048; 1024 with scores)
                         // d > deg_cta: several CTAs per vertex, global-memory hash
   // tile sizes: hub table slots per batch (the hub tables of one batch are reused by the next) and the
   // fewest vertices per block of a problem

@@ -4,7 +4,7 @@
 // quantised score q = round-half-even(s * 2^15) of each CSR entry breaks ties between equally
 // connected labels (larger score sum first) and orders admission after the gain.
 //
-// Features of entry (v,u), symmetric in v and u:
+// Features of entry (v,u), symmetric in v and u (rows of degree above 512 are spread over a CTA):
 //   0 log2(1 + min(d(v), d(u)))        1 log2(1 + max(d(v), d(u)))
 //   2 log2(1 + omega(v,u))             3 log2(1 + min(c(v), c(u)))
 //   4 log2(1 + max(c(v), c(u)))
@@ -56,14 +56,74 @@ __global__ void k_wdeg(DGraph g, float *wdeg) {
   }
 }
 
-// One half-warp (16 lanes) per vertex v; each lane owns one entry (v,u) of a 16-entry step. The
-// shared-neighbour count of an entry: its lane takes the first 64 neighbours of u and looks each up
-// in a set of v's first 64 neighbours (an open-addressing table of 128 slots in shared memory for the
-// half-warp, slot mix32(x) mod 128, linear probing).
+// Features of entry e = (v,u) of v's row (called by one lane per entry; `has` false for the lanes past
+// the row's end). The shared-neighbour count: the lane takes the first 64 neighbours of u and looks
+// each up in `tab`, the set of v's first 64 neighbours (an open-addressing table of kTab slots in shared
+// memory, slot mix32(x) mod kTab, linear probing).
+constexpr int kTab = 128;  // set slots (at most 64 keys)
+constexpr int64_t kFeatSmall = 512;  // rows up to this degree: a half-warp per vertex; longer: a CTA
+
+template <bool BF16>
+__device__ __forceinline__ void feature_entry(const DGraph &g, const float *wdeg, int64_t e, bool has, int64_t dv,
+                                              float cv, float wv, const int *tab, float flevel, float *fout,
+                                              unsigned *bout) {
+  const int u = has ? g.adj[e] : 0;
+  const int64_t bu = has ? g.row_begin(u) : 0;
+  const int64_t eu = has ? g.row_begin(u + 1) : 0;
+  const int lenu = (int)gp_min64(eu - bu, 64);
+  // u's weight, its weighted degree and the entry's weight are loaded before the search
+  const float cu = has ? (float)g.vweight(u) : 0.0f;
+  const float wu = has ? wdeg[u] : 0.0f;
+  const float w = has ? (float)g.eweight(e) : 0.0f;
+  int mine = 0;
+  // eight of u's neighbours are loaded before any is searched (independent loads in flight)
+  constexpr int kBatch = 8;
+  for (int k0 = 0; k0 < lenu; k0 += kBatch) {
+    int xs[kBatch];
+#pragma unroll
+    for (int q = 0; q < kBatch; q++) xs[q] = k0 + q < lenu ? __ldg(g.adj + bu + k0 + q) : 0;
+#pragma unroll
+    for (int q = 0; q < kBatch; q++) {
+      if (k0 + q >= lenu) break;
+      const int x = xs[q];
+      unsigned sl = mix32((unsigned)x) & (kTab - 1);
+      while (true) {
+        const int k = tab[sl];
+        if (k == x) {
+          mine++;
+          break;
+        }
+        if (k == -1) break;
+        sl = (sl + 1) & (kTab - 1);
+      }
+    }
+  }
+  if (!has) return;
+  const float du = (float)(eu - bu);
+  const float dvf = (float)dv;
+  float f[kIn];
+  f[0] = log2f(1.0f + fminf(dvf, du));
+  f[1] = log2f(1.0f + fmaxf(dvf, du));
+  f[2] = log2f(1.0f + w);
+  f[3] = log2f(1.0f + fminf(cv, cu));
+  f[4] = log2f(1.0f + fmaxf(cv, cu));
+  f[5] = (float)mine / 64.0f;
+  f[6] = w / fmaxf(wv, wu);
+  f[7] = flevel;
+  if (BF16) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) bout[e * 4 + i] = pack2(float_to_bf16(f[2 * i]), float_to_bf16(f[2 * i + 1]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < kIn; i++) fout[e * kIn + i] = f[i];
+  }
+}
+
+// Rows of degree <= kFeatSmall: one half-warp (16 lanes) per vertex, each lane one entry of a 16-entry
+// step; the set of v's first 64 neighbours is the half-warp's own table.
 template <bool BF16>
 __global__ void __launch_bounds__(256, 6) k_features(DGraph g, int level, const float *wdeg, float *fout, unsigned *bout) {
-  constexpr int kH = 16;     // lanes per vertex
-  constexpr int kTab = 128;  // set slots (at most 64 keys)
+  constexpr int kH = 16;  // lanes per vertex
   __shared__ int tab_s[8][2][kTab];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane / kH, hl = lane % kH;
   const unsigned hmask = 0xFFFFu << (kH * half);
@@ -74,7 +134,7 @@ __global__ void __launch_bounds__(256, 6) k_features(DGraph g, int level, const 
   for (int64_t v = gh; v < g.n; v += nh) {
     const int64_t beg = g.row_begin(v), end = g.row_begin(v + 1);
     const int64_t dv = end - beg;
-    if (dv == 0) continue;
+    if (dv == 0 || dv > kFeatSmall) continue;  // (uniform over the half-warp)
     const int lenv = (int)gp_min64(dv, 64);
     __syncwarp(hmask);
     for (int t = hl; t < kTab; t += kH) tab[t] = -1;
@@ -88,61 +148,46 @@ __global__ void __launch_bounds__(256, 6) k_features(DGraph g, int level, const 
     const float cv = (float)g.vweight(v);
     const float wv = wdeg[v];
     for (int64_t e0 = beg; e0 < end; e0 += kH) {
-      // lane j takes entry e0 + j: it walks the first (up to) 64 neighbours of u and looks each up in
-      // the set of v's first 64 neighbours
       const int64_t e = e0 + hl;
-      const bool has = e < end;
-      const int u = has ? g.adj[e] : 0;
-      const int64_t bu = has ? g.row_begin(u) : 0;
-      const int64_t eu = has ? g.row_begin(u + 1) : 0;
-      const int lenu = (int)gp_min64(eu - bu, 64);
-      // u's weight, its weighted degree and the entry's weight are loaded before the search
-      const float cu = has ? (float)g.vweight(u) : 0.0f;
-      const float wu = has ? wdeg[u] : 0.0f;
-      const float w = has ? (float)g.eweight(e) : 0.0f;
-      int mine = 0;
-      // eight of u's neighbours are loaded before any is searched (independent loads in flight)
-      constexpr int kBatch = 8;
-      for (int k0 = 0; k0 < lenu; k0 += kBatch) {
-        int xs[kBatch];
-#pragma unroll
-        for (int q = 0; q < kBatch; q++) xs[q] = k0 + q < lenu ? __ldg(g.adj + bu + k0 + q) : 0;
-#pragma unroll
-        for (int q = 0; q < kBatch; q++) {
-          if (k0 + q >= lenu) break;
-          const int x = xs[q];
-          unsigned sl = mix32((unsigned)x) & (kTab - 1);
-          while (true) {
-            const int k = tab[sl];
-            if (k == x) {
-              mine++;
-              break;
-            }
-            if (k == -1) break;
-            sl = (sl + 1) & (kTab - 1);
-          }
-        }
-      }
-      if (!has) continue;
-      const float du = (float)(eu - bu);
-      const float dvf = (float)dv;
-      float f[kIn];
-      f[0] = log2f(1.0f + fminf(dvf, du));
-      f[1] = log2f(1.0f + fmaxf(dvf, du));
-      f[2] = log2f(1.0f + w);
-      f[3] = log2f(1.0f + fminf(cv, cu));
-      f[4] = log2f(1.0f + fmaxf(cv, cu));
-      f[5] = (float)mine / 64.0f;
-      f[6] = w / fmaxf(wv, wu);
-      f[7] = flevel;
-      if (BF16) {
-#pragma unroll
-        for (int i = 0; i < 4; i++) bout[e * 4 + i] = pack2(float_to_bf16(f[2 * i]), float_to_bf16(f[2 * i + 1]));
-      } else {
-#pragma unroll
-        for (int i = 0; i < kIn; i++) fout[e * kIn + i] = f[i];
-      }
+      feature_entry<BF16>(g, wdeg, e, e < end, dv, cv, wv, tab, flevel, fout, bout);
     }
+  }
+}
+
+// Rows of degree > kFeatSmall (hubs of power-law graphs): one CTA per vertex, its 16 half-warps taking
+// 16-entry steps of the row in turn, one shared set of v's first 64 neighbours. A row is thus spread
+// over 256 lanes instead of 16, which keeps the longest rows from deciding the kernel's duration.
+__global__ void k_list_feat_big(DGraph g, int32_t *big, unsigned *nbig) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
+    if (g.row_begin(v + 1) - g.row_begin(v) > kFeatSmall) big[atomicAdd(nbig, 1u)] = (int32_t)v;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_features_big(DGraph g, int level, const float *wdeg, float *fout,
+                                                      unsigned *bout, const int32_t *big, const unsigned *nbig) {
+  __shared__ int tab[kTab];
+  const int hw = threadIdx.x >> 4, hl = threadIdx.x & 15;
+  const float flevel = (float)level / 16.0f;
+  const unsigned cnt = *nbig;
+  for (unsigned i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int v = big[i];
+    const int64_t beg = g.row_begin(v), end = g.row_begin(v + 1);
+    const int64_t dv = end - beg;
+    for (int t = threadIdx.x; t < kTab; t += blockDim.x) tab[t] = -1;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const int x = g.adj[beg + threadIdx.x];  // (dv > 64)
+      unsigned sl = mix32((unsigned)x) & (kTab - 1);
+      while (atomicCAS(&tab[sl], -1, x) != -1) sl = (sl + 1) & (kTab - 1);
+    }
+    __syncthreads();
+    const float cv = (float)g.vweight(v);
+    const float wv = wdeg[v];
+    for (int64_t e0 = beg + hw * 16; e0 < end; e0 += 256) {
+      const int64_t e = e0 + hl;
+      feature_entry<BF16>(g, wdeg, e, e < end, dv, cv, wv, tab, flevel, fout, bout);
+    }
+    __syncthreads();
   }
 }
 
@@ -341,11 +386,21 @@ int features(const DGraph &g, int level, float *fout, unsigned *bout, cudaStream
   float *wdeg;
   GP_TRY(ws.get(&wdeg, (size_t)g.n));
   const int nsm = num_sms();
+  int32_t *big;
+  unsigned *nbig;
+  GP_TRY(ws.get(&big, (size_t)g.n));
+  GP_TRY(ws.zeros(&nbig, 1));
   (::gp::count_launch(), k_wdeg<<<grid_for(g.n * 32, 256, nsm * 8), 256, 0, s>>>(g, wdeg));
+  (::gp::count_launch(), k_list_feat_big<<<grid_for(g.n, 256, nsm * 8), 256, 0, s>>>(g, big, nbig));
   {
     ProfScope ps("mlp_features", s);
-    if (bout) (::gp::count_launch(), k_features<true><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, nullptr, bout));
-    else (::gp::count_launch(), k_features<false><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, fout, nullptr));
+    if (bout) {
+      (::gp::count_launch(), k_features<true><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, nullptr, bout));
+      (::gp::count_launch(), k_features_big<true><<<nsm * 8, 256, 0, s>>>(g, level, wdeg, nullptr, bout, big, nbig));
+    } else {
+      (::gp::count_launch(), k_features<false><<<grid_for(g.n * 16, 256, nsm * 6), 256, 0, s>>>(g, level, wdeg, fout, nullptr));
+      (::gp::count_launch(), k_features_big<false><<<nsm * 8, 256, 0, s>>>(g, level, wdeg, fout, nullptr, big, nbig));
+    }
   }
   GP_LAUNCH_CHECK();
   return GP_OK;

@@ -795,7 +795,8 @@ int gp_autotune_schedule(const gp_graph *gd, int32_t *deg_warp_out, int32_t *deg
     set_error("gp_autotune_schedule: outputs are required");
     return GP_ERR_INVALID_ARG;
   }
-  static const int cand[][2] = {{32, 256}, {64, 256}, {64, 512}, {128, 512}, {128, 1024}, {32, 1024}};
+  static const int cand[][2] = {{32, 256}, {64, 256}, {64, 512}, {128, 512}, {128, 1024}, {32, 1024},
+                                {128, 2048}, {256, 2048}};
   std::vector<gp_params> cs;
   for (const auto &c : cand) {
     gp_params pr;

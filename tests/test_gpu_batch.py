@@ -72,7 +72,8 @@ def test_autotuner_returns_a_candidate_and_results_do_not_change(gp):
     g = gg.rmat(13, 16, seed=8)
     dg = gp.DeviceGraph.from_host(g)
     w, c, ms = gp.autotune_schedule(dg)
-    assert (w, c) in [(32, 256), (64, 256), (64, 512), (128, 512), (128, 1024), (32, 1024)] and ms > 0
+    assert (w, c) in [(32, 256), (64, 256), (64, 512), (128, 512), (128, 1024), (32, 1024), (128, 2048),
+                      (256, 2048)] and ms > 0
     p0, r0 = gp.partition(dg, 16, 0.03, 3)
     p1, r1 = gp.partition(dg, 16, 0.03, 3, gp.default_params(deg_warp=w, deg_cta=c))
     assert np.array_equal(p0.cpu().numpy(), p1.cpu().numpy())
