@@ -23,7 +23,7 @@ from graphgen import Graph
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "liboracle.so")
-_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp", "match.cpp", "mls.cpp"]
+_SRCS = ["lp.cpp", "contract.cpp", "partition.cpp", "mlp.cpp", "match.cpp", "mls.cpp", "lp_async.cpp"]
 _lib = None
 _lock = threading.Lock()
 
@@ -42,7 +42,7 @@ class OrParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64),
                 ("coarse_min", I64), ("coarse_per_k", I64), ("stall_pct", I64),
                 ("max_levels", I64), ("ip_tries", I64), ("repair_rounds", I64), ("coarsen_mode", I64),
-                ("mls", I64)]
+                ("mls", I64), ("lp_async", I64)]
 
 
 class OrMlsParams(ctypes.Structure):
@@ -95,6 +95,8 @@ def _load():
             lib.or_contract.restype = I32
             lib.or_contract.argtypes = [ctypes.POINTER(OrGraph), VP, I64, ctypes.POINTER(I64),
                                         ctypes.POINTER(I64), VP, VP, VP, VP, VP]
+            lib.or_lp_async.restype = I32
+            lib.or_lp_async.argtypes = [ctypes.POINTER(OrGraph), VP, VP, I64, I64, I64, U64, ctypes.POINTER(OrLpStats)]
             lib.or_match.restype = I32
             lib.or_match.argtypes = [ctypes.POINTER(OrGraph), I64, I64, U64, VP, ctypes.POINTER(OrMatchStats)]
             lib.or_mls_default_params.restype = None
@@ -183,6 +185,21 @@ def lp(g: Graph, labels, lw, U: int, rounds: int, seed: int, q=None):
 def lp_cluster(g: Graph, U: int, rounds: int, seed: int, q=None):
     """Size-constrained LP clustering from singletons (C[v] = v)."""
     return lp(g, np.arange(g.n, dtype=np.int32), vertex_weights(g), U, rounds, seed, q)
+
+
+def lp_async(g: Graph, labels, lw, U: int, rounds: int, seed: int):
+    """The paper's sequential in-place LP order ((degree, id) order, moves applied at once)."""
+    v = _View(g)
+    labels = np.array(labels, dtype=np.int32, copy=True)
+    lw = np.array(lw, dtype=np.int64, copy=True)
+    st = OrLpStats()
+    rc = _load().or_lp_async(v.ref(), _p(labels), _p(lw), int(lw.shape[0]), U, rounds, seed, ctypes.byref(st))
+    assert rc == 0
+    return labels, lw, LpStats(st.rounds, st.moves, st.visits, st.edges, st.movers)
+
+
+def lp_cluster_async(g: Graph, U: int, rounds: int, seed: int):
+    return lp_async(g, np.arange(g.n, dtype=np.int32), vertex_weights(g), U, rounds, seed)
 
 
 def block_weights(g: Graph, part, k: int) -> np.ndarray:

@@ -49,6 +49,7 @@ typedef struct or_params {
   int64_t coarsen_mode;       /* 0: LP clustering (the paper's), 1: matching (or_match) */
   int64_t mls;                /* 0: off; else MLS with this many global iterations (other parameters
                                  default) after the LP refinement of every level, seed H(seed, level, 7) */
+  int64_t lp_async;           /* 1: every LP run (coarsening, tries, refinement) in or_lp_async's order */
 } or_params;
 
 typedef struct or_match_stats {
@@ -82,6 +83,11 @@ int64_t or_lmax(int64_t total_weight, int64_t k, double eps);
  * q (per CSR entry, or NULL) adds the learned tie-break and admission key. Returns 0 or -1. */
 int or_lp(const or_graph *g, const int32_t *q, int32_t *labels, int64_t *lw, int64_t nl, int64_t U,
           int64_t rounds, uint64_t seed, or_lp_stats *st);
+
+/* The paper's sequential, in-place LP order (Section III-A; the order of Section IV-A's asynchronous
+ * form): vertices in (degree, id) order, moves applied at once. labels[n], lw[nl] in/out. */
+int or_lp_async(const or_graph *g, int32_t *labels, int64_t *lw, int64_t nl, int64_t U, int64_t rounds,
+                uint64_t seed, or_lp_stats *st);
 
 /* Matching-based clustering (clusters of one or two vertices, Section III-A, Section VII): rounds of
  * deterministic handshake matching under the bound c(u) + c(v) <= U. labels[n] out. */

@@ -256,6 +256,7 @@ extern "C" void or_default_params(or_params *p) {
   p->repair_rounds = 16;
   p->coarsen_mode = 0;
   p->mls = 0;
+  p->lp_async = 0;
 }
 
 extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t seed,
@@ -326,8 +327,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
         or_match(&gl, U, p.rounds_coarsen, or_hash3(seed, (uint64_t)l, 1), labels.data(), nullptr);
       } else {
         or_lp_stats ls;
-        or_lp(&gl, q, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen,
-              or_hash3(seed, (uint64_t)l, 1), &ls);
+        if (p.lp_async)
+          or_lp_async(&gl, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen, or_hash3(seed, (uint64_t)l, 1), &ls);
+        else
+          or_lp(&gl, q, labels.data(), lw.data(), gl.n, U, p.rounds_coarsen, or_hash3(seed, (uint64_t)l, 1), &ls);
         res->lp_edges += ls.edges;
       }
       OwnedGraph c;
@@ -359,8 +362,11 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       std::vector<int64_t> bw(k);
       or_cut(&gc, pt.data(), k, bw.data());
       or_lp_stats ls;
-      or_lp(&gc, nullptr, pt.data(), bw.data(), k, lmax, p.rounds_refine,
-            or_hash3(s_try, (uint64_t)levels, 3), &ls);
+      if (p.lp_async)
+        or_lp_async(&gc, pt.data(), bw.data(), k, lmax, p.rounds_refine, or_hash3(s_try, (uint64_t)levels, 3), &ls);
+      else
+        or_lp(&gc, nullptr, pt.data(), bw.data(), k, lmax, p.rounds_refine, or_hash3(s_try, (uint64_t)levels, 3),
+              &ls);
       res->lp_edges += ls.edges;
       const int64_t cut = or_cut(&gc, pt.data(), k, bw.data());
       const int64_t imb = *std::max_element(bw.begin(), bw.end()) > lmax ? 1 : 0;
@@ -388,8 +394,10 @@ extern "C" int or_partition(const or_graph *g, int64_t k, double eps, uint64_t s
       std::vector<int64_t> bw(k);
       or_cut(&gl, fine.data(), k, bw.data());
       or_lp_stats ls;
-      or_lp(&gl, nullptr, fine.data(), bw.data(), k, lmax, p.rounds_refine,
-            or_hash3(seed, (uint64_t)l, 2), &ls);
+      if (p.lp_async)
+        or_lp_async(&gl, fine.data(), bw.data(), k, lmax, p.rounds_refine, or_hash3(seed, (uint64_t)l, 2), &ls);
+      else
+        or_lp(&gl, nullptr, fine.data(), bw.data(), k, lmax, p.rounds_refine, or_hash3(seed, (uint64_t)l, 2), &ls);
       res->lp_edges += ls.edges;
       if (p.mls) or_mls(&gl, k, lmax, or_hash3(seed, (uint64_t)l, 7), &mp, fine.data(), nullptr);
       cur.swap(fine);
