@@ -104,6 +104,10 @@ typedef struct gp_params {
    * parameters and this many global iterations; 0 = off, the default; the paper's configuration uses 3).
    * Plain mode, k <= 256. */
   int64_t mls_global_iters;
+  /* 1: every LP run of the partition (coarsening, the tries' refinement, uncoarsening) uses
+   * gp_lp_cluster_async's asynchronous order instead of the deterministic Jacobi rounds: the paper's
+   * own scheme, non-deterministic, a comparator for what determinism costs (plain mode). */
+  int64_t lp_async;
 } gp_params;
 
 enum { GP_MODE_PLAIN = 0, GP_MODE_LEARNED = 1, GP_MODE_BEST_OF = 2 };
@@ -196,6 +200,18 @@ int64_t gp_lmax(int64_t total_weight, int64_t k, double eps);
 int gp_lp_cluster(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed,
                   const int32_t *edge_q, int32_t *labels_out, gp_lp_stats *stats,
                   gp_stream stream);
+
+/* The paper's asynchronous size-constrained LP (Section III-A order, Section IV-A parallel form) from
+ * C[v] = v: vertices in increasing order of degree (ties: id) are taken in packets of 32 by warps;
+ * each vertex moves at once to the eligible cluster of strongest connection (own label on ties, then
+ * larger H(seed, v, L), then smaller L), reading labels and cluster weights as they are at that moment,
+ * the target's weight reserved by compare-and-swap so that no cluster exceeds U; neighbours of moved
+ * vertices are queued for the next round. Not deterministic: a comparator for gp_lp_cluster's Jacobi
+ * rounds. With single_warp != 0 one warp runs everything in the sequential order (deterministic).
+ * Arguments as gp_lp_cluster. A vertex may have at most 256 distinct neighbouring labels: graphs of
+ * maximum degree above 256 return GP_ERR_UNSUPPORTED. */
+int gp_lp_cluster_async(const gp_graph *g, int64_t U, int32_t rounds, uint64_t seed, int32_t single_warp,
+                        int32_t *labels_out, gp_lp_stats *stats, gp_stream stream);
 
 /* gp_lp_cluster without any device allocation, for callers that cannot allocate device memory
  * while they run (no cudaMalloc, no caching allocator, no allocator callback). The paper has no

@@ -50,7 +50,8 @@ class GpParams(ctypes.Structure):
     _fields_ = [("cluster_div", I64), ("rounds_coarsen", I64), ("rounds_refine", I64), ("coarse_min", I64),
                 ("coarse_per_k", I64), ("stall_pct", I64), ("max_levels", I64), ("ip_tries", I64),
                 ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("coarsen", I32),
-                ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64), ("mls_global_iters", I64)]
+                ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64), ("mls_global_iters", I64),
+                ("lp_async", I64)]
 
 
 class GpMlsParams(ctypes.Structure):
@@ -134,6 +135,9 @@ def lib():
         L.gp_mls.restype = ctypes.c_int
         L.gp_mls.argtypes = [ctypes.POINTER(GpGraph), I32, I64, U64, ctypes.POINTER(GpMlsParams), VP,
                              ctypes.POINTER(GpMlsStats), VP]
+        L.gp_lp_cluster_async.restype = ctypes.c_int
+        L.gp_lp_cluster_async.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, I32, VP, ctypes.POINTER(GpLpStats),
+                                          VP]
         L.gp_match.restype = ctypes.c_int
         L.gp_match.argtypes = [ctypes.POINTER(GpGraph), I64, I32, U64, VP, ctypes.POINTER(GpMatchStats), VP]
         L.gp_lp_refine.restype = ctypes.c_int
@@ -328,6 +332,16 @@ def match(dg: DeviceGraph, U: int, rounds: int, seed: int, stream=None):
     st = GpMatchStats()
     _check(lib().gp_match(ctypes.byref(dg.desc), U, rounds, seed, labels.data_ptr(), ctypes.byref(st),
                           _stream(stream)), "gp_match")
+    return labels[: dg.n], st.as_dict()
+
+
+def lp_cluster_async(dg: DeviceGraph, U: int, rounds: int, seed: int, single_warp: bool = False, stream=None):
+    """The paper's asynchronous LP from singletons (non-deterministic unless single_warp)."""
+    import torch
+    labels = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.adj.device)
+    st = GpLpStats()
+    _check(lib().gp_lp_cluster_async(ctypes.byref(dg.desc), U, rounds, seed, 1 if single_warp else 0,
+                                     labels.data_ptr(), ctypes.byref(st), _stream(stream)), "gp_lp_cluster_async")
     return labels[: dg.n], st.as_dict()
 
 

@@ -18,6 +18,7 @@
 #include "gp_internal.cuh"
 #include "ip.cuh"
 #include "lp.cuh"
+#include "lp_async.cuh"
 #include "match.cuh"
 #include "mls.cuh"
 #include "mlp.cuh"
@@ -162,6 +163,10 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     return GP_ERR_INVALID_ARG;
   }
   const bool learned = p.mode == GP_MODE_LEARNED;
+  if (p.lp_async && p.mode != GP_MODE_PLAIN) {
+    set_error("gp_partition: asynchronous LP needs plain mode");
+    return GP_ERR_INVALID_ARG;
+  }
   if (p.mls_global_iters < 0 || (p.mls_global_iters > 0 && (p.mode != GP_MODE_PLAIN || k > 256))) {
     set_error("gp_partition: multi-try local search needs plain mode and k <= 256");
     return GP_ERR_INVALID_ARG;
@@ -245,6 +250,9 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       if (learned) GP_TRY(mlp_score(gl, l, static_cast<const gp_mlp *>(p.mlp), nullptr, q, s));
       if (p.coarsen == GP_COARSEN_MATCHING)
         GP_TRY(run_match(gl, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1), labels, nullptr, s, false));
+      else if (p.lp_async)
+        GP_TRY(run_lp_async(gl, labels, lw, gl.n, U, (int)p.rounds_coarsen, hash3(seed, (uint64_t)l, 1), false,
+                            nullptr, s));
       else
         GP_TRY(run_lp(gl, learned ? q : nullptr, labels, lw, gl.n, U, (int)p.rounds_coarsen,
                       hash3(seed, (uint64_t)l, 1), nullptr, s, cfg, true, &level_cls[l], &lpdef,
@@ -299,7 +307,13 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
       jobs[t].classes = level_cls[levels].valid ? &level_cls[levels] : nullptr;
       jobs[t].prof = "lp_persistent_ip";
     }
-    if (gc.n > 0 && p.rounds_refine > 0) GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg, &lpdef));
+    if (gc.n > 0 && p.rounds_refine > 0 && p.lp_async) {
+      for (int t = 0; t < tries; t++)
+        GP_TRY(run_lp_async(gc, jobs[t].labels, jobs[t].lw, k, lmax, (int)p.rounds_refine, jobs[t].seed, false,
+                            nullptr, s));
+    } else if (gc.n > 0 && p.rounds_refine > 0) {
+      GP_TRY(run_lp_multi(jobs.data(), tries, s, cfg, &lpdef));
+    }
     // cuts of all tries in one pass; their block weights are the label weights the refinement kept
     std::vector<unsigned long long> hcut2(tries);
     std::vector<int64_t> hbws((size_t)tries * k);
@@ -354,8 +368,11 @@ int partition_device(const gp_graph *gin, int32_t k, double eps, uint64_t seed, 
     for (int l = levels - 1; l >= 0; l--) {
       int32_t *fine = (cur == bufA) ? bufB : bufA;
       GP_TRY(project(cur, f2c[l], G[l].n, fine, s));
-      GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), nullptr, s, cfg,
-                    false, &level_cls[l], &lpdef, "lp_persistent_refine"));
+      if (p.lp_async)
+        GP_TRY(run_lp_async(G[l], fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), false, nullptr, s));
+      else
+        GP_TRY(run_lp(G[l], nullptr, fine, bw, k, lmax, (int)p.rounds_refine, hash3(seed, (uint64_t)l, 2), nullptr, s,
+                      cfg, false, &level_cls[l], &lpdef, "lp_persistent_refine"));
       if (mp.global_iters > 0) {
         GP_TRY(run_mls(G[l], k, lmax, hash3(seed, (uint64_t)l, 7), mp, fine, nullptr, s));
         GP_TRY(block_weights(G[l], fine, k, bw, nullptr, s));
@@ -515,6 +532,34 @@ int gp_lp_cluster(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, 
   }
   GP_TRY(run_lp(g, edge_q, labels_out, lw, g.n, U, rounds, seed, stats, s, schedule_for(nullptr), true));
   GP_TRY(prof_flush(s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  return GP_OK;
+}
+
+int gp_lp_cluster_async(const gp_graph *gd, int64_t U, int32_t rounds, uint64_t seed, int32_t single_warp,
+                        int32_t *labels_out, gp_lp_stats *stats, gp_stream stream) {
+  GP_TRY(check_graph_desc(gd));
+  if ((!labels_out && gd->n > 0) || rounds < 0 || U < 1) {
+    set_error("gp_lp_cluster_async: labels_out, rounds or U out of range");
+    return GP_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const DGraph g = make_dgraph(gd);
+  Workspace ws(s);
+  int64_t maxc = 0;
+  GP_TRY(vertex_weight_stats(g, &maxc, nullptr, s));
+  if (maxc > U) {
+    set_error("gp_lp_cluster_async: U is below the largest vertex weight");
+    return GP_ERR_INVALID_ARG;
+  }
+  int64_t *lw;
+  GP_TRY(ws.get(&lw, (size_t)std::max<int64_t>(g.n, 1)));
+  if (g.n > 0) {
+    (::gp::count_launch(), k_iota<<<grid_n(g.n), 256, 0, s>>>(labels_out, g.n));
+    (::gp::count_launch(), k_vw_to_i64<<<grid_n(g.n), 256, 0, s>>>(g, lw));
+    GP_LAUNCH_CHECK();
+  }
+  GP_TRY(run_lp_async(g, labels_out, lw, g.n, U, rounds, seed, single_warp != 0, stats, s));
   GP_CUDA(cudaStreamSynchronize(s));
   return GP_OK;
 }
