@@ -38,7 +38,7 @@ GRAPHS = {
     "grid96": lambda: gg.grid(96, 96),
     "rgg2e14": lambda: gg.rgg(1 << 14, 10.0, 3),
     "rgg_weighted": lambda: _weighted_rgg(12000, 4),
-    "rmat13": lambda: gg.rmat(13, 8, seed=5),
+    "rmat11": lambda: gg.rmat(11, 8, seed=5),
 }
 
 
@@ -88,7 +88,7 @@ def test_mls_parameters_equal_oracle(gp, over):
     assert np.array_equal(out.cpu().numpy(), out_o) and st == st_o
 
 
-@pytest.mark.parametrize("name,k", [("rgg2e14", 8), ("rgg_weighted", 4), ("rmat13", 16)])
+@pytest.mark.parametrize("name,k", [("rgg2e14", 8), ("rgg_weighted", 4), ("rmat11", 16)])
 def test_mls_partition_equals_oracle(gp, name, k):
     g = GRAPHS[name]()
     params = gp.default_params(mls_global_iters=3, coarse_min=300)
