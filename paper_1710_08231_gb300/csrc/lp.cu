@@ -38,19 +38,26 @@ constexpr int kBins = 7;     // G4, G8, G16, G32, WARP, CTA, HUB
 constexpr int kBinZero = 7;  // degree-0 visits (statistics only)
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Shared-memory tables: 12-byte slots (8-byte sum, 4-byte label) without scores, 16-byte slots with
-// (a 4-byte score sum more), in the same 48 KB of dynamic shared memory per CTA: 4096 or 2048 slots per
-// CTA, 512 or 256 per warp. A CTA table serves vertices of degree up to half its slots; a hub chunk of
-// kHubChunkOf<LQ> entries is pre-aggregated in it.
-template <bool LQ>
-constexpr int kWarpCapOf = LQ ? 256 : 512;
-template <bool LQ>
-constexpr int kCtaCapOf = LQ ? 2048 : 4096;
-template <bool LQ>
-constexpr int kHubChunkOf = LQ ? 1024 : 2048;
-constexpr int kWarpCap = kWarpCapOf<false>;  // the larger capacities (bounds of the schedule)
-constexpr int kCtaCap = kCtaCapOf<false>;
-constexpr int kHubChunk = 1024;              // the smaller chunk (bound of the work items)
+// Shared-memory tables come in three classes TB, one kernel instance each:
+//   TB = 0  runs with scores: 16-byte slots (8-byte sum, 4-byte label, 4-byte score sum), 256 per warp,
+//           2048 per CTA, hub chunks of 1024 entries, 32 KB of dynamic shared memory;
+//   TB = 1  plain runs on graphs without a vertex of degree above 1024: the same capacities, 32 KB;
+//   TB = 2  plain runs on graphs with such vertices: 12-byte slots, 512 per warp, 4096 per CTA (the CTA
+//           bin reaches degree 2048), hub chunks of 2048 entries, 48 KB.
+// The smaller class leaves more of the SM's unified L1/shared memory to L1, which the label gathers of
+// low-degree graphs use; the larger one pre-aggregates more hub entries per global table claim.
+template <int TB>
+constexpr int kWarpCapT = TB == 2 ? 512 : 256;
+template <int TB>
+constexpr int kCtaCapT = TB == 2 ? 4096 : 2048;
+template <int TB>
+constexpr int kHubChunkT = TB == 2 ? 2048 : 1024;
+template <int TB>
+constexpr size_t kDynSmemT = TB == 2 ? 48 * 1024 : 32 * 1024;
+constexpr int kWarpCap = kWarpCapT<2>;  // the larger capacities (bounds of the schedule)
+constexpr int kCtaCap = kCtaCapT<2>;
+constexpr int kHubChunk = 1024;         // the smaller chunk (bound of the work items)
+constexpr int kWideDeg = 1024;          // degrees above this need the larger tables
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
 // Hub table slots per batch and the fewest vertices per block come from LpConfig (tile sizes picked by
@@ -59,10 +66,10 @@ constexpr int kContestSmall = 4096;
 // sub-round.
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
-constexpr size_t kDynSmem = 48 * 1024;
-static_assert(kWarps * kWarpCapOf<false> * 12 <= (int)kDynSmem && kWarps * kWarpCapOf<true> * 16 <= (int)kDynSmem,
+constexpr size_t kDynSmem = kDynSmemT<0>;  // the smallest class (bound for the contest workspaces)
+static_assert(kWarps * kWarpCapT<2> * 12 <= (int)kDynSmemT<2> && kWarps * kWarpCapT<0> * 16 <= (int)kDynSmemT<0>,
               "warp tables fit the dynamic shared memory");
-static_assert(kCtaCapOf<false> * 12 <= (int)kDynSmem && kCtaCapOf<true> * 16 <= (int)kDynSmem,
+static_assert(kCtaCapT<2> * 12 <= (int)kDynSmemT<2> && kCtaCapT<0> * 16 <= (int)kDynSmemT<0>,
               "CTA tables fit the dynamic shared memory");
 static_assert(kContestSmall * 8 <= (int)kDynSmem, "contest keys must fit the dynamic shared memory");
 static_assert(sizeof(DGraph) % 4 == 0, "graph view is copied word by word");
@@ -101,7 +108,7 @@ struct LpProblem {
   int64_t vbase, lbase;
   int64_t nl, U;
   int64_t hub_batch_slots;     // hub table slots per batch (tile size of the hub path)
-  int64_t hub_chunk;           // hub row entries per accumulation work item (kHubChunkOf<LQ>)
+  int64_t hub_chunk;           // hub row entries per accumulation work item (kHubChunkT<TB>)
   int hub_chunk_shift;         // log2(hub_chunk)
   int pad_chunk;
   unsigned wait_us;            // limit of every barrier wait (microseconds)
@@ -110,6 +117,7 @@ struct LpProblem {
   int rounds;
   int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
   int has_hubs;
+  int hub_dense;  // hub tables indexed by label directly (few labels: refinement with small k)
   int deg_warp, deg_cta;
   int block_begin, block_count;
   int32_t *labels;
@@ -819,12 +827,13 @@ __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals,
 }
 
 // One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
-template <int EW, bool LQ>
+template <int EW, int TB>
 __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, bool direct) {
+  constexpr bool LQ = TB == 0;
   const unsigned cnt = V.bin_count[4];
   if (cnt == 0) return;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int kCap = kWarpCapOf<LQ>;
+  constexpr int kCap = kWarpCapT<TB>;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm) + wid * kCap;
   int *keys = reinterpret_cast<int *>(dsm + kWarps * kCap * 8) + wid * kCap;
   unsigned *qv = reinterpret_cast<unsigned *>(dsm + kWarps * kCap * 12) + wid * kCap;
@@ -905,12 +914,13 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
 }
 
 // One CTA per vertex (deg_warp < d <= deg_cta), table in shared memory.
-template <int EW, bool LQ>
+template <int EW, int TB>
 __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int nb, unsigned char *dsm, Smem &sm,
                            bool direct) {
   const unsigned cnt = V.bin_count[5];
   if (cnt == 0) return;
-  constexpr int kCap = kCtaCapOf<LQ>;
+  constexpr bool LQ = TB == 0;
+  constexpr int kCap = kCtaCapT<TB>;
   unsigned long long *vals = reinterpret_cast<unsigned long long *>(dsm);
   int *keys = reinterpret_cast<int *>(dsm + kCap * 8);
   unsigned *qv = reinterpret_cast<unsigned *>(dsm + kCap * 12);
@@ -1003,8 +1013,9 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     if (valid) {
       const int v = P.bin[6][i];
       d = P.g.row_begin(v + 1) - P.g.row_begin(v);
-      // a row has at most min(d, nl) distinct labels (refinement: nl = k blocks)
-      cap = min(hub_cap(d), hub_cap(P.nl));
+      // a row has at most min(d, nl) distinct labels (refinement: nl = k blocks); with few labels the
+      // table is indexed by the label itself
+      cap = P.hub_dense ? P.nl : min(hub_cap(d), hub_cap(P.nl));
       ch = (d + P.hub_chunk - 1) >> P.hub_chunk_shift;
       sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
@@ -1072,13 +1083,14 @@ __device__ __forceinline__ unsigned search_prefix(const T *pre, unsigned lo, uns
   return lo;
 }
 
-// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunkOf<LQ> entries. A block aggregates
+// Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunkT<TB> entries. A block aggregates
 // its chunk's labels in a shared-memory table first and then adds one entry per distinct label to the
 // hub's table, so labels that many neighbours share cost one global atomic per chunk.
-template <int EW, bool LQ>
+template <int EW, int TB>
 __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm, unsigned char *dsm) {
-  constexpr int kCap = kCtaCapOf<LQ>;
-  constexpr int kChunk = kHubChunkOf<LQ>;
+  constexpr bool LQ = TB == 0;
+  constexpr int kCap = kCtaCapT<TB>;
+  constexpr int kChunk = kHubChunkT<TB>;
   unsigned long long *svals = reinterpret_cast<unsigned long long *>(dsm);
   int *skeys = reinterpret_cast<int *>(dsm + kCap * 8);
   unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCap * 12);
@@ -1089,6 +1101,57 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
   }
   __syncthreads();
   const unsigned c_lo = P.hub_prefix[h0], c_hi = P.hub_prefix[h1];
+  if (!LQ && P.hub_dense) {
+    // few labels: a shared counter per label, flushed into the hub's dense table
+    const int nl = (int)P.nl;
+    for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
+      const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
+      const int v = P.bin[6][i];
+      const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+      const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kChunk;
+      const int64_t end = min(re, beg + kChunk);
+      const int64_t tb = P.hub_tb[i];
+      const int L0 = P.labels[P.vbase + v];
+      long long c0 = 0;
+      for (int64_t s0 = beg; s0 < end; s0 += 4 * kThreads) {
+        int64_t e[4];
+        int L[4];
+        long long w[4];
+        bool in[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          e[u] = s0 + u * kThreads + threadIdx.x;
+          in[u] = e[u] < end;
+          L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
+          w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) L[u] = in[u] ? P.labels[L[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (in[u] && L[u] == L0) c0 += w[u];
+          const bool on = in[u] && L[u] != L0;
+          const unsigned peers = __match_any_sync(kFull, on ? L[u] : -1);
+          long long sum = 0;
+          if (on)
+            for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, w[u], __ffs(m) - 1);
+          if (on && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            atomicAdd(&svals[L[u] - P.lbase], (unsigned long long)sum);
+        }
+      }
+      c0 = block_sum_of(c0, sm);  // also completes the counters
+      for (int t = threadIdx.x; t < nl; t += kThreads) {
+        const unsigned long long x = svals[t];
+        if (x) {
+          atomicAdd(&P.hub_vals[tb + t], x);
+          svals[t] = 0;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
+    }
+    return;
+  }
   for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
     const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
     const int v = P.bin[6][i];
@@ -1191,7 +1254,8 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
 #pragma unroll
       for (int u = 0; u < kU; u++) {
         const int64_t sl = base + u * kThreads + threadIdx.x;
-        L[u] = sl < s1 ? P.hub_keys[tb + sl] : -1;
+        if (P.hub_dense) L[u] = (sl < s1 && P.hub_vals[tb + sl] != 0) ? (int)(P.lbase + sl) : -1;
+        else L[u] = sl < s1 ? P.hub_keys[tb + sl] : -1;
       }
 #pragma unroll
       for (int u = 0; u < kU; u++) {
@@ -1208,7 +1272,7 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
         const int64_t sl = base + u * kThreads + threadIdx.x;
         const Best x = make_cand_lw(P, v, L[u], L0, cw[u], (long long)qq[u], c0, cv, lwL[u]);
         if (better(x, b)) b = x;
-        P.hub_keys[tb + sl] = -1;
+        if (!P.hub_dense) P.hub_keys[tb + sl] = -1;
         P.hub_vals[tb + sl] = 0;
         if (LQ) P.hub_qv[tb + sl] = 0;
       }
@@ -1727,8 +1791,9 @@ __device__ bool contest_large(const LpProblem &P, const SubCounters &C, SubCount
   return true;
 }
 
-template <int EW, bool LQ>
+template <int EW, int TB>
 __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
+  constexpr bool LQ = TB == 0;
   __shared__ __align__(16) unsigned char p_raw[sizeof(LpProblem)];
   __shared__ Smem sm;
   LpProblem &P = *reinterpret_cast<LpProblem *>(p_raw);
@@ -1817,8 +1882,8 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
         choose_groups<EW, LQ>(P, sV, lb, nb);
         // only the first sub-round sees every label as a singleton (the second follows its moves)
         const bool direct = P.singletons && t == 0;
-        choose_warp<EW, LQ>(P, sV, lb, nb, dsm, direct);
-        choose_cta<EW, LQ>(P, sV, lb, nb, dsm, sm, direct);
+        choose_warp<EW, TB>(P, sV, lb, nb, dsm, direct);
+        choose_cta<EW, TB>(P, sV, lb, nb, dsm, sm, direct);
         if (!grid_sync(bar)) return false;
         tick(1);
         if (P.has_hubs && sV.bin_count[6] && direct) {
@@ -1834,7 +1899,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           const unsigned nbat = sV.hub_batches;
           for (unsigned bt = 0; bt < nbat; bt++) {
             const unsigned h0 = P.hub_bstart[bt], h1 = P.hub_bstart[bt + 1];
-            hub_accum<EW, LQ>(P, h0, h1, lb, nb, sm, dsm);
+            hub_accum<EW, TB>(P, h0, h1, lb, nb, sm, dsm);
             if (!grid_sync(bar)) return false;
             tick(2);
             hub_choose_part<LQ>(P, h0, h1, lb, nb, sm);
@@ -1901,11 +1966,11 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
 // One launch runs every problem: block b runs the problems blk_list[blk_start[b] .. blk_start[b+1])
 // in order. A problem of several blocks is the only problem of each of its blocks; problems of one
 // block may share a block with others (small graphs of a batch).
-template <int EW, bool LQ>
+template <int EW, int TB>
 __global__ void __launch_bounds__(kThreads, 4) k_lp(const LpProblem *probs, const int *blk_start, const int *blk_list) {
   extern __shared__ __align__(16) unsigned char dsm[];
   for (int q = blk_start[blockIdx.x]; q < blk_start[blockIdx.x + 1]; q++)
-    if (!lp_problem<EW, LQ>(probs + blk_list[q], dsm)) return;
+    if (!lp_problem<EW, TB>(probs + blk_list[q], dsm)) return;
 }
 
 // ------------------------------------------------------------------------------------ host helpers
@@ -1918,12 +1983,12 @@ constexpr int kClsSmemJobs = 16;
 __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs, int deg_warp, int deg_cta,
                                  unsigned *counts, unsigned long long *entries, unsigned long long *hubstat) {
   __shared__ unsigned s_counts[9 * kClsSmemJobs];
-  __shared__ unsigned long long s_entries[kClsSmemJobs], s_hub[2 * kClsSmemJobs];
+  __shared__ unsigned long long s_entries[kClsSmemJobs], s_hub[3 * kClsSmemJobs];
   const bool local = njobs <= kClsSmemJobs;
   if (local) {
     for (int t = threadIdx.x; t < 9 * kClsSmemJobs; t += blockDim.x) s_counts[t] = 0;
     for (int t = threadIdx.x; t < kClsSmemJobs; t += blockDim.x) s_entries[t] = 0;
-    for (int t = threadIdx.x; t < 2 * kClsSmemJobs; t += blockDim.x) s_hub[t] = 0;
+    for (int t = threadIdx.x; t < 3 * kClsSmemJobs; t += blockDim.x) s_hub[t] = 0;
     __syncthreads();
   }
   unsigned *cnt_out = local ? s_counts : counts;
@@ -1956,9 +2021,10 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
     if (j >= 0 && lane == __ffs(pj) - 1 && dsum) atomicAdd(&ent_out[j], dsum);
     if (bin == 6) {  // hub: table slots hub_cap(d); per job the largest table and their sum
       const unsigned long long cap = (unsigned long long)hub_cap(d);
-      atomicMax(&hub_out[2 * j], cap);
-      atomicAdd(&hub_out[2 * j + 1], cap);
+      atomicMax(&hub_out[3 * j], cap);
+      atomicAdd(&hub_out[3 * j + 1], cap);
     }
+    if (d > kWideDeg) atomicAdd(&hub_out[3 * j + 2], 1ull);  // vertices that need the larger tables
   }
   if (local) {
     __syncthreads();
@@ -1966,9 +2032,9 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
       if (s_counts[t]) atomicAdd(&counts[t], s_counts[t]);
     for (int t = threadIdx.x; t < njobs; t += blockDim.x)
       if (s_entries[t]) atomicAdd(&entries[t], s_entries[t]);
-    for (int t = threadIdx.x; t < 2 * njobs; t += blockDim.x) {
+    for (int t = threadIdx.x; t < 3 * njobs; t += blockDim.x) {
       if (!s_hub[t]) continue;
-      if (t & 1) atomicAdd(&hubstat[t], s_hub[t]);
+      if (t % 3) atomicAdd(&hubstat[t], s_hub[t]);
       else atomicMax(&hubstat[t], s_hub[t]);
     }
   }
@@ -1999,30 +2065,40 @@ __global__ void k_block_weights(DGraph g, const int32_t *part, int64_t k, int64_
   }
 }
 
-template <int EW, bool LQ>
+template <int EW, int TB>
 int max_coop_blocks(int *out) {
-  static int cached[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  if (!cached[EW][LQ]) {
-    GP_CUDA(cudaFuncSetAttribute(k_lp<EW, LQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem));
+  static int cached[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  if (!cached[EW][TB]) {
+    GP_CUDA(cudaFuncSetAttribute(k_lp<EW, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmemT<TB>));
     int per_sm = 0;
-    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp<EW, LQ>, kThreads, kDynSmem));
-    cached[EW][LQ] = std::max(1, per_sm);
+    GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp<EW, TB>, kThreads, kDynSmemT<TB>));
+    cached[EW][TB] = std::max(1, per_sm);
   }
-  *out = cached[EW][LQ] * num_sms();
+  *out = cached[EW][TB] * num_sms();
   return GP_OK;
 }
 
-int coop_capacity(int ew, bool lq, int *out) {
-  if (lq) return ew == 0 ? max_coop_blocks<0, true>(out) : ew == 1 ? max_coop_blocks<1, true>(out) : max_coop_blocks<2, true>(out);
-  return ew == 0 ? max_coop_blocks<0, false>(out) : ew == 1 ? max_coop_blocks<1, false>(out) : max_coop_blocks<2, false>(out);
+template <int TB>
+int coop_capacity_tb(int ew, int *out) {
+  return ew == 0 ? max_coop_blocks<0, TB>(out) : ew == 1 ? max_coop_blocks<1, TB>(out) : max_coop_blocks<2, TB>(out);
 }
 
-template <int EW, bool LQ>
+int coop_capacity(int ew, int tb, int *out) {
+  return tb == 0 ? coop_capacity_tb<0>(ew, out) : tb == 1 ? coop_capacity_tb<1>(ew, out) : coop_capacity_tb<2>(ew, out);
+}
+
+template <int EW, int TB>
 int launch_lp(const LpProblem *probs_dev, const int *blk_start_dev, const int *blk_list_dev, int grid, cudaStream_t s) {
   count_launch();
   void *args[] = {(void *)&probs_dev, (void *)&blk_start_dev, (void *)&blk_list_dev};
-  GP_CUDA(cudaLaunchCooperativeKernel((void *)k_lp<EW, LQ>, grid, kThreads, args, kDynSmem, s));
+  GP_CUDA(cudaLaunchCooperativeKernel((void *)k_lp<EW, TB>, grid, kThreads, args, kDynSmemT<TB>, s));
   return GP_OK;
+}
+
+template <int TB>
+int launch_lp_tb(int ew, const LpProblem *p, const int *bs, const int *bl, int grid, cudaStream_t s) {
+  return ew == 0 ? launch_lp<0, TB>(p, bs, bl, grid, s) : ew == 1 ? launch_lp<1, TB>(p, bs, bl, grid, s)
+                                                                  : launch_lp<2, TB>(p, bs, bl, grid, s);
 }
 
 }  // namespace
@@ -2140,7 +2216,7 @@ int lp_classes_launch(const DGraph &g, const LpConfig &cfg, unsigned long long *
   GP_CUDA(cudaMemcpyAsync(gs_dev, &g, sizeof(DGraph), cudaMemcpyHostToDevice, s));
   GP_CUDA(cudaMemcpyAsync(pre_dev, pre, sizeof(pre), cudaMemcpyHostToDevice, s));
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, num_sms() * 8));
-  // words: [0, 5) the 9 unsigned class counts, [5] entries, [6, 8) hub statistics
+  // words: [0, 5) the 9 unsigned class counts, [5] entries, [6, 9) hub statistics and wide vertices
   (::gp::count_launch(), k_degree_classes<<<grid, 256, 0, s>>>(gs_dev, pre_dev, 1, cfg.deg_warp, cfg.deg_cta,
                                                                  reinterpret_cast<unsigned *>(words_dev),
                                                                  words_dev + 5, words_dev + 6));
@@ -2157,6 +2233,7 @@ void lp_classes_from(const unsigned long long *words, const LpConfig &cfg, LpCla
   ci->entries = words[5];
   ci->hub_max_cap = words[6];
   ci->hub_cap_sum = words[7];
+  ci->wide = words[8];
 }
 
 int lp_collect(LpDeferred &def, cudaStream_t s, int64_t *edges, int64_t *moves, Readback *extra) {
@@ -2185,8 +2262,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   // scored runs have the smaller shared-memory tables (16-byte slots)
   LpConfig cfg = cfg_in;
   if (lq) {
-    cfg.deg_warp = std::min(cfg.deg_warp, kWarpCapOf<true> / 2);
-    cfg.deg_cta = std::max(cfg.deg_warp, std::min(cfg.deg_cta, kCtaCapOf<true> / 2));
+    cfg.deg_warp = std::min(cfg.deg_warp, kWarpCapT<0> / 2);
+    cfg.deg_cta = std::max(cfg.deg_warp, std::min(cfg.deg_cta, kCtaCapT<0> / 2));
   }
   for (int j = 0; j < njobs; j++) {
     if (jobs[j].stats) std::memset(jobs[j].stats, 0, sizeof(gp_lp_stats));
@@ -2200,14 +2277,12 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     }
   }
   Workspace ws(s);
-  int cap_blocks = 0;
-  GP_TRY(coop_capacity(ew, lq, &cap_blocks));
   const int nsm = num_sms();
   // degree classes and entry counts of all jobs (one kernel, one copy back), unless every job brings
   // them from an earlier call on the same graph and schedule
   std::vector<unsigned> hcls(9 * (size_t)njobs);
   std::vector<unsigned long long> hent(njobs);
-  std::vector<unsigned long long> hhub(2 * (size_t)njobs);
+  std::vector<unsigned long long> hhub(3 * (size_t)njobs);
   bool cached = true;
   for (int j = 0; j < njobs; j++) {
     const LpClassInfo *ci = jobs[j].classes;
@@ -2218,8 +2293,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       const LpClassInfo &ci = *jobs[j].classes;
       for (int b = 0; b < 9; b++) hcls[9 * (size_t)j + b] = ci.cls[b];
       hent[j] = ci.entries;
-      hhub[2 * (size_t)j] = ci.hub_max_cap;
-      hhub[2 * (size_t)j + 1] = ci.hub_cap_sum;
+      hhub[3 * (size_t)j] = ci.hub_max_cap;
+      hhub[3 * (size_t)j + 1] = ci.hub_cap_sum;
+      hhub[3 * (size_t)j + 2] = ci.wide;
     }
   } else {
     std::vector<DGraph> hg(njobs);
@@ -2237,7 +2313,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.zeros(&classes, (size_t)9 * njobs));
     GP_TRY(ws.zeros(&entries, (size_t)njobs));
     unsigned long long *hubstat;
-    GP_TRY(ws.zeros(&hubstat, (size_t)2 * njobs));
+    GP_TRY(ws.zeros(&hubstat, (size_t)3 * njobs));
     GP_CUDA(cudaMemcpyAsync(gs_dev, hg.data(), sizeof(DGraph) * njobs, cudaMemcpyHostToDevice, s));
     GP_CUDA(cudaMemcpyAsync(pre_dev, pre.data(), sizeof(int64_t) * (njobs + 1), cudaMemcpyHostToDevice, s));
     if (pre[njobs] > 0) {
@@ -2259,10 +2335,20 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       ci->deg_cta = cfg.deg_cta;
       for (int b = 0; b < 9; b++) ci->cls[b] = hcls[9 * (size_t)j + b];
       ci->entries = hent[j];
-      ci->hub_max_cap = hhub[2 * (size_t)j];
-      ci->hub_cap_sum = hhub[2 * (size_t)j + 1];
+      ci->hub_max_cap = hhub[3 * (size_t)j];
+      ci->hub_cap_sum = hhub[3 * (size_t)j + 1];
+      ci->wide = hhub[3 * (size_t)j + 2];
     }
   }
+  // table class: scored runs 0; plain runs the larger tables only where a vertex of degree above
+  // kWideDeg (or a warp bin above 128) needs them. Without such vertices the classes computed for
+  // deg_cta up to 2048 are those of deg_cta = 1024 as well.
+  bool wide = cfg.deg_warp > kWarpCapT<1> / 2;
+  for (int j = 0; j < njobs; j++) wide = wide || hhub[3 * (size_t)j + 2] > 0;
+  const int tb = lq ? 0 : (wide ? 2 : 1);
+  if (tb == 1) cfg.deg_cta = std::max(cfg.deg_warp, std::min(cfg.deg_cta, kCtaCapT<1> / 2));
+  int cap_blocks = 0;
+  GP_TRY(coop_capacity(ew, tb, &cap_blocks));
   // Blocks: a job gets at most one block per cfg.verts_per_block vertices. When all jobs fit the co-resident
   // capacity that way, they do; otherwise work is balanced by a cost model (entries + 4 per vertex
   // + a fixed per-problem latency term): jobs above twice the mean block load get several blocks,
@@ -2374,9 +2460,10 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.nl = jb.nl;
     P.U = jb.U;
     P.hub_batch_slots = cfg.hub_batch_slots;
-    P.hub_chunk = lq ? kHubChunkOf<true> : kHubChunkOf<false>;
-    P.hub_chunk_shift = lq ? 10 : 11;
-    static_assert(kHubChunkOf<true> == 1 << 10 && kHubChunkOf<false> == 1 << 11, "hub chunks are powers of two");
+    P.hub_chunk = tb == 2 ? kHubChunkT<2> : kHubChunkT<0>;
+    P.hub_chunk_shift = tb == 2 ? 11 : 10;
+    static_assert(kHubChunkT<0> == 1 << 10 && kHubChunkT<1> == 1 << 10 && kHubChunkT<2> == 1 << 11,
+                  "hub chunks are powers of two");
     P.wait_us = (unsigned)std::min<unsigned long long>(std::max<unsigned long long>(wait_limit_ns() / 1000, 0),
                                                         0xffffffffull);
     P.smix = mix64(jb.seed);
@@ -2442,6 +2529,10 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       GP_TRY(ws.get(&P.hub_bstart, (size_t)nhub + 1));
       GP_TRY(ws.get(&P.hub_bbase, (size_t)nhub + 1));
       P.has_hubs = 1;
+      // dense tables need nl <= 2 (deg_cta + 1) <= hub_cap(d) for every hub (the tables are sized by
+      // hub_cap(d)) and the counters in the CTA's shared table
+      P.hub_dense = (!lq && jb.nl <= 2 * ((int64_t)cfg.deg_cta + 1) && jb.nl <= (tb == 2 ? kCtaCapT<2> : kCtaCapT<1>))
+                        ? 1 : 0;
     }
   }
   LpProblem *probs_dev;
@@ -2455,12 +2546,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
   {
     ProfScope ps(jobs[0].prof, s);
     int st;
-    if (lq) st = ew == 0 ? launch_lp<0, true>(probs_dev, bs_dev, bl_dev, grid, s)
-               : ew == 1 ? launch_lp<1, true>(probs_dev, bs_dev, bl_dev, grid, s)
-                         : launch_lp<2, true>(probs_dev, bs_dev, bl_dev, grid, s);
-    else st = ew == 0 ? launch_lp<0, false>(probs_dev, bs_dev, bl_dev, grid, s)
-              : ew == 1 ? launch_lp<1, false>(probs_dev, bs_dev, bl_dev, grid, s)
-                        : launch_lp<2, false>(probs_dev, bs_dev, bl_dev, grid, s);
+    if (tb == 0) st = launch_lp_tb<0>(ew, probs_dev, bs_dev, bl_dev, grid, s);
+    else if (tb == 1) st = launch_lp_tb<1>(ew, probs_dev, bs_dev, bl_dev, grid, s);
+    else st = launch_lp_tb<2>(ew, probs_dev, bs_dev, bl_dev, grid, s);
     GP_TRY(st);
   }
   if (deferred) {

@@ -9,7 +9,8 @@ namespace gp {
 
 struct LpConfig {
   int deg_warp = 128;   // 32 < d <= deg_warp: one warp per vertex, shared-memory hash (<= 256; 128 with scores)
-  int deg_cta = 2048;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 2048; 1024 with scores)
+  int deg_cta = 2048;   // deg_warp < d <= deg_cta: one CTA per vertex, shared-memory hash (<= 2048; 1024 with
+                        // scores or without a vertex of degree above 1024)
                         // d > deg_cta: several CTAs per vertex, global-memory hash
   // tile sizes: hub table slots per batch (the hub tables of one batch are reused by the next) and the
   // fewest vertices per block of a problem
@@ -27,12 +28,13 @@ struct LpClassInfo {
   int deg_warp = 0, deg_cta = 0;
   unsigned cls[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long entries = 0, hub_max_cap = 0, hub_cap_sum = 0;
+  unsigned long long wide = 0;  // vertices of degree above 1024 (they need the larger shared tables)
 };
 
 // Degree classes of one graph computed without a read back: lp_classes_launch writes kLpClassWords
 // words into words_dev (device, caller-owned) on the workspace's stream; after the caller has read
 // them to the host, lp_classes_from fills the LpClassInfo.
-constexpr int kLpClassWords = 8;
+constexpr int kLpClassWords = 9;
 int lp_classes_launch(const DGraph &g, const LpConfig &cfg, unsigned long long *words_dev, Workspace &ws);
 void lp_classes_from(const unsigned long long *words, const LpConfig &cfg, LpClassInfo *ci);
 
