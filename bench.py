@@ -156,6 +156,46 @@ def compare_ip_tries(gp, name, dg, k, ms_step, flush):
     return out
 
 
+def _side_graph(gp, name, dg, k, ms_step):
+    """The workload itself, or the random geometric graph 2^20 (k=16) when a partition of the workload
+    takes more than 2 s (the comparisons below run several partitions each)."""
+    import graphgen as gg
+    if ms_step > 2000 or WORKLOADS[name]["kind"] not in ("rgg", "grid"):
+        return "rgg20", gp.DeviceGraph.from_host(gg.rgg(1 << 20, 12.0, SEED)), 16
+    return name, dg, k
+
+
+def compare_variants(gp, name, dg, k, ms_step, flush, seeds=10):
+    """The §8(f) variants against the plain deterministic partition at seeds 1..seeds on a mesh graph:
+    multi-try local search after every level (3 global iterations), matching coarsening, and the paper's
+    asynchronous LP (non-deterministic: a comparator for what determinism costs). Geometric means of
+    the per-seed cut and time ratios."""
+    import math
+    gname, g2, k2 = _side_graph(gp, name, dg, k, ms_step)
+    variants = {"mls": dict(mls_global_iters=3), "matching": dict(coarsen=gp.COARSEN_MATCHING),
+                "async_lp": dict(lp_async=1)}
+    out = {"graph": WORKLOADS[gname]["desc"], "seeds": seeds}
+    plain = []
+    for sd in range(1, seeds + 1):
+        ms, (_, r) = time_steps(lambda: gp.partition(g2, k2, EPS, sd), 1, flush)
+        plain.append((r.cut, ms))
+    gm = lambda xs: math.exp(sum(math.log(x) for x in xs) / len(xs))
+    for vname, kw in variants.items():
+        params = gp.default_params(**kw)
+        gp.partition(g2, k2, EPS, 1, params)
+        rows = []
+        for sd in range(1, seeds + 1):
+            ms, (_, r) = time_steps(lambda: gp.partition(g2, k2, EPS, sd, params), 1, flush)
+            rows.append((r.cut, ms, r.imbalanced))
+        out[vname] = {"geomean_cut_ratio": gm([a[0] / max(b[0], 1) for a, b in zip(rows, plain)]),
+                      "geomean_time_ratio": gm([a[1] / b[1] for a, b in zip(rows, plain)]),
+                      "better_or_equal": sum(a[0] <= b[0] for a, b in zip(rows, plain)),
+                      "imbalanced": sum(a[2] for a in rows), "ms_per_partition": sum(a[1] for a in rows) / seeds,
+                      "cuts": [a[0] for a in rows]}
+    out["plain"] = {"cuts": [a for a, _ in plain], "ms_per_partition": sum(b for _, b in plain) / seeds}
+    return out
+
+
 def batch_items(gp, graphs):
     return [gp.DeviceGraph.from_host(g) for g in graphs]
 
@@ -735,7 +775,8 @@ def main():
         compare = {"learned": compare_learned(gp, args.workload, g, dg, k, min(args.steps, 3), flush, ms_step, res,
                                               nseeds),
                    "batched": compare_batched(gp, 3, flush),
-                   "ip_tries": compare_ip_tries(gp, args.workload, dg, k, ms_step, flush)}
+                   "ip_tries": compare_ip_tries(gp, args.workload, dg, k, ms_step, flush),
+                   "variants": compare_variants(gp, args.workload, dg, k, ms_step, flush)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -118,6 +118,7 @@ struct LpProblem {
   int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
   int has_hubs;
   int hub_dense;  // hub tables indexed by label directly (few labels: refinement with small k)
+  int64_t hub_table_slots;  // slots allocated for one batch of hub tables
   int deg_warp, deg_cta;
   int block_begin, block_count;
   int32_t *labels;
@@ -795,9 +796,16 @@ __device__ void choose_groups(const LpProblem &P, const SubCounters &V, int lb, 
 // memory (slots keys/vals/qv, `mask` = slots - 1). Lanes are grouped by label first, so each distinct
 // label of the warp costs one insert however many neighbours carry it. All lanes call; lanes with
 // `on` false contribute nothing.
+// A table that is full (an invariant of the sizing broken) ends the probe after one pass over the table,
+// records GP_ERR_INTERNAL with the site in the problem's counters, and drops the label.
+__device__ __forceinline__ void table_full(LpCounters *ctr, int site) {
+  atomicExch(&ctr->err, GP_ERR_INTERNAL);
+  atomicExch(&ctr->pad, site);
+}
+
 template <int EW, bool LQ>
 __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals, unsigned *qv, unsigned mask, bool on,
-                                            int L, long long w, unsigned q) {
+                                            int L, long long w, unsigned q, LpCounters *ctr, int site) {
   const unsigned peers = __match_any_sync(kFull, on ? L : -1);
   // weights below 2^26 sum exactly in 32 bits over at most 32 lanes: one warp reduction
   const bool wide = EW != 0 && __any_sync(kFull, on && (w >= (1ll << 26) || w < 0));
@@ -815,7 +823,7 @@ __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals,
   if constexpr (LQ) qs = __reduce_add_sync(peers, q);
   if ((int)(threadIdx.x & 31) != __ffs(peers) - 1) return;
   unsigned sl = slot_hash(L) & mask;
-  while (true) {
+  for (unsigned probe = 0; probe <= mask; probe++) {
     const int k = atomicCAS(&keys[sl], -1, L);
     if (k == -1 || k == L) {
       atomicAdd(&vals[sl], (unsigned long long)sum);
@@ -824,6 +832,7 @@ __device__ __forceinline__ void warp_insert(int *keys, unsigned long long *vals,
     }
     sl = (sl + 1) & mask;
   }
+  table_full(ctr, site);
 }
 
 // One warp per vertex (32 < d <= deg_warp), open-addressing table in shared memory.
@@ -883,7 +892,8 @@ __device__ void choose_warp(const LpProblem &P, const SubCounters &V, int lb, in
       const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
       if (in && L == L0) c0 += w;
       other |= in && L != L0;
-      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
+      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u,
+                          P.ctr, 1);
     }
     if (!__any_sync(kFull, other)) {
       // every neighbour carries the own label: no candidate, the table is still empty
@@ -968,7 +978,8 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
       const int L = in ? P.labels[__ldg(P.g.adj + e)] : -1;
       const long long w = in ? load_ew<EW>(P.g.ew, e) : 0;
       if (in && L == L0) c0 += w;
-      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u);
+      warp_insert<EW, LQ>(keys, vals, qv, mask, in && L != L0, L, w, (LQ && in) ? (unsigned)__ldg(P.q + e) : 0u,
+                          P.ctr, 2);
     }
     c0 = block_sum_of(c0, sm);  // also completes the table
     const long long cv = P.g.vweight(v);
@@ -1045,7 +1056,11 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
       P.hub_bbase[bx] = capx;
     }
     __syncthreads();
-    if (valid) P.hub_tb[i] = capx - P.hub_bbase[bx + flag - 1];
+    if (valid) {
+      P.hub_tb[i] = capx - P.hub_bbase[bx + flag - 1];
+      // (a sizing invariant: a batch's tables fit the allocation; checked, not assumed)
+      if (P.hub_tb[i] + cap > P.hub_table_slots) table_full(P.ctr, 5);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       s_cap += cap_t;
@@ -1063,6 +1078,19 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     P.hub_bstart[s_nbat] = cnt;
     C.hub_chunks = (unsigned)s_ch;
     C.hub_batches = (unsigned)s_nbat;
+  }
+  __syncthreads();
+  if (*(volatile int *)&P.ctr->err == GP_ERR_INTERNAL) {
+    // tables would not fit: no hub work this sub-round, no hub proposals (the call reports the error)
+    if (threadIdx.x == 0) {
+      C.hub_chunks = 0;
+      C.hub_batches = 0;
+    }
+    for (unsigned i = threadIdx.x; i < cnt; i += kThreads) P.mv_t[P.bin_base[6] + i] = -1;
+    for (unsigned i = threadIdx.x; i <= cnt; i += kThreads) {
+      P.hub_prefix[i] = 0;
+      P.hub_scx[i] = 0;
+    }
   }
   sum_d = block_sum_of(sum_d, sm);
   sum_cap = block_sum_of(sum_cap, sm);
@@ -1183,7 +1211,7 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         if (in[u] && L[u] == L0) c0 += w[u];
-        warp_insert<EW, LQ>(skeys, svals, sq, kCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u]);
+        warp_insert<EW, LQ>(skeys, svals, sq, kCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u], P.ctr, 3);
       }
     }
     c0 = block_sum_of(c0, sm);  // also completes the shared table
@@ -1200,7 +1228,12 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
         pend[q] = Ls[q] >= 0;
         sg[q] = pend[q] ? hub_slot(Ls[q], cap) : 0;
       }
+      uint64_t probes = 0;
       while (pend[0] || pend[1] || pend[2] || pend[3]) {
+        if (++probes > cap) {  // the hub's table is full: record and drop the remaining labels
+          table_full(P.ctr, 4);
+          break;
+        }
         int ks[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) ks[q] = pend[q] ? atomicCAS(&P.hub_keys[tb + sg[q]], -1, Ls[q]) : 0;
@@ -2139,6 +2172,10 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
   int64_t tot_edges = 0, tot_moves = 0;
   for (int j = 0; j < n; j++) {
     const LpCounters &h = hc[j];
+    if (h.err == GP_ERR_INTERNAL) {
+      set_error("label propagation: a table filled up (site " + std::to_string(h.pad) + ")");
+      return GP_ERR_INTERNAL;
+    }
     if (h.err) {
       set_error("label propagation: a bounded device barrier gave up");
       return GP_ERR_TIMEOUT;
@@ -2511,8 +2548,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     const unsigned nhub = hcls[9 * j + 6];
     if (nhub) {
       // tables of one batch of hubs (reused batch after batch), partial choices, per-hub arrays
-      const int64_t max_cap = (int64_t)hhub[2 * j], cap_sum = (int64_t)hhub[2 * j + 1];
+      const int64_t max_cap = (int64_t)hhub[3 * (size_t)j], cap_sum = (int64_t)hhub[3 * (size_t)j + 1];
       const int64_t slots = std::min<int64_t>(cfg.hub_batch_slots, cap_sum) + max_cap;
+      P.hub_table_slots = slots;
       // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub; the
       // round-0 direct path keeps one item per chunk of every hub row
       const int64_t items = std::max<int64_t>(slots / kSlotChunk, (int64_t)(hent[j] / kHubChunk)) + (int64_t)nhub + 16;
