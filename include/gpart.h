@@ -96,7 +96,7 @@ typedef struct gp_params {
   int32_t coarsen;        /* GP_COARSEN_LP (the paper's clustering, default) or GP_COARSEN_MATCHING */
   const void *mlp;        /* device pointer to a gp_mlp (learned modes), else NULL */
   /* LP tile sizes (0 = default; never change results): hub table slots per batch of the multi-CTA
-   * hub path (default 4M, clamped to [4096, 2^28]) and the fewest vertices per CTA of one LP problem
+   * hub path (default 64M, clamped to [4096, 2^28]) and the fewest vertices per CTA of one LP problem
    * (default 64, clamped to [16, 4096]) */
   int64_t hub_batch_slots;
   int64_t verts_per_block;
@@ -385,7 +385,7 @@ int gp_autotune_schedule(const gp_graph *g, int32_t *deg_warp_out, int32_t *deg_
 
 /* Schedule and tile-size autotuner: as gp_autotune_schedule, then, with the best degree bins, times
  * three LP rounds under candidate tile sizes (verts_per_block in {32, 64, 128, 256}; when g has
- * vertices of degree > deg_cta, hub_batch_slots in {1M, 4M, 16M}) and writes the fastest into
+ * vertices of degree > deg_cta, hub_batch_slots in {4M, 16M, 64M}) and writes the fastest into
  * params->deg_warp, deg_cta, verts_per_block and hub_batch_slots (other fields are left as they are).
  * params: host struct (required), typically from gp_default_params. */
 int gp_autotune(const gp_graph *g, gp_params *params, double *ms_out, gp_stream stream);

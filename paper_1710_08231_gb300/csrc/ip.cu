@@ -370,14 +370,52 @@ __global__ void __launch_bounds__(kIpThreads) k_repair(IpArgs a) {
   }
 }
 
+// Rows up to kCutSmall entries: a thread each; longer rows (hubs of power-law graphs, whose walk by one
+// thread would decide the kernel's duration) are left to k_cut_big.
+constexpr int64_t kCutSmall = 256;
+
 __global__ void k_cut(DGraph g, const int32_t *part, unsigned long long *acc) {
   __shared__ long long sh[32];
   long long s = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
     const int pv = part[v];
     const int64_t b = g.row_begin(v), e = g.row_begin(v + 1);
+    if (e - b > kCutSmall) continue;
     for (int64_t j = b; j < e; j++)
       if (part[g.adj[j]] != pv) s += g.eweight(j);
+  }
+  s = warp_sum64(s);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  if (wid == 0) {
+    long long x = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+    x = warp_sum64(x);
+    if (lane == 0 && x) atomicAdd(acc, (unsigned long long)x);
+  }
+}
+
+// Rows above kCutSmall entries, a CTA each: every CTA checks tiles of 256 consecutive vertices, lists the
+// long rows of its tile in shared memory and walks each with all its threads.
+__global__ void k_cut_big(DGraph g, const int32_t *part, unsigned long long *acc) {
+  __shared__ long long sh[32];
+  __shared__ int list[256];
+  __shared__ int cnt;
+  long long s = 0;
+  for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int64_t v = v0 + threadIdx.x;
+    if (v < g.n && g.row_begin(v + 1) - g.row_begin(v) > kCutSmall) list[atomicAdd(&cnt, 1)] = (int)v;
+    __syncthreads();
+    for (int i = 0; i < cnt; i++) {
+      const int x = list[i];
+      const int px = part[x];
+      const int64_t b = g.row_begin(x), e = g.row_begin(x + 1);
+      for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x)
+        if (part[g.adj[j]] != px) s += g.eweight(j);
+    }
+    __syncthreads();
   }
   s = warp_sum64(s);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -643,6 +681,7 @@ int eval_cut_launch(const DGraph &g, const int32_t *part, int64_t k, unsigned lo
   GP_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(unsigned long long), s));
   if (g.n > 0) {
     (::gp::count_launch(), k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc_dev));
+    (::gp::count_launch(), k_cut_big<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc_dev));
     GP_LAUNCH_CHECK();
   }
   if (bw_dev) GP_TRY(block_weights(g, part, k, bw_dev, nullptr, s));

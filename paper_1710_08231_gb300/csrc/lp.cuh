@@ -14,7 +14,7 @@ struct LpConfig {
                         // d > deg_cta: several CTAs per vertex, global-memory hash
   // tile sizes: hub table slots per batch (the hub tables of one batch are reused by the next) and the
   // fewest vertices per block of a problem
-  int64_t hub_batch_slots = int64_t(1) << 22;
+  int64_t hub_batch_slots = int64_t(1) << 26;
   int64_t verts_per_block = 64;
 };
 constexpr int64_t kMinHubBatchSlots = 4096, kMaxHubBatchSlots = int64_t(1) << 28;

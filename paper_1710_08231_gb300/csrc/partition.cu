@@ -889,7 +889,7 @@ int gp_autotune(const gp_graph *gd, gp_params *params, double *ms_out, gp_stream
   }
   std::vector<gp_params> cs;
   static const int64_t vpb[] = {32, 64, 128, 256};
-  static const int64_t hbs[] = {int64_t(1) << 20, int64_t(1) << 22, int64_t(1) << 24};
+  static const int64_t hbs[] = {int64_t(1) << 22, int64_t(1) << 24, int64_t(1) << 26};
   const bool hubs = ci.cls[6] > 0;
   for (int64_t v : vpb)
     for (int h = 0; h < (hubs ? 3 : 1); h++) {

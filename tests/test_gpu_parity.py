@@ -298,7 +298,7 @@ def test_autotune_picks_valid_tiles_and_keeps_results(gp):
     params, ms = gp.autotune(dg)
     assert ms > 0
     assert params.verts_per_block in (32, 64, 128, 256)
-    assert params.hub_batch_slots in (0, 1 << 20, 1 << 22, 1 << 24)
+    assert params.hub_batch_slots in (0, 1 << 22, 1 << 24, 1 << 26)
     part, res = gp.partition(dg, 16, 0.03, 1, params)
     part_o, res_o = O.partition(g, 16, 0.03, 1)
     assert np.array_equal(part.cpu().numpy(), part_o)
