@@ -108,6 +108,11 @@ typedef struct gp_params {
    * gp_lp_cluster_async's asynchronous order instead of the deterministic Jacobi rounds: the paper's
    * own scheme, non-deterministic, a comparator for what determinism costs (plain mode). */
   int64_t lp_async;
+  /* Hub tables (vertices above deg_cta) kept across LP sub-rounds and updated by the moves, instead of
+   * re-accumulated from the hubs' rows every sub-round, when the tables of all hubs of one LP call take
+   * at most this many slots (12 bytes each; runs with scores never keep them). 0 = default 2^32,
+   * negative = never. Never changes results. */
+  int64_t hub_keep_slots;
 } gp_params;
 
 enum { GP_MODE_PLAIN = 0, GP_MODE_LEARNED = 1, GP_MODE_BEST_OF = 2 };
@@ -264,6 +269,14 @@ int gp_lp_set_schedule(int32_t deg_warp, int32_t deg_cta);
  * hub_batch_slots splits the hubs of one sub-round into many batches (each with its own table pass),
  * which the tests use to compare the multi-batch hub path with the oracle on small graphs. */
 int gp_lp_set_tiles(int64_t hub_batch_slots, int64_t verts_per_block);
+
+/* Kept hub tables (process-wide). slots: as gp_params.hub_keep_slots for gp_lp_cluster and
+ * gp_lp_refine (0 restores the default, negative re-accumulates every hub in every sub-round).
+ * max_load_pct (every LP call, gp_partition's too): a kept table whose key bound would pass this share
+ * of its slots goes stale and is accumulated again at the hub's next activation; 0 restores the
+ * default 75, 1 makes every table go stale at its first new label (the tests use both to compare the
+ * update and rebuild paths with the oracle). Range [0, 95]. Never changes results. */
+int gp_lp_set_hub_keep(int64_t slots, int32_t max_load_pct);
 
 /* LP refinement of a k-way partition (Section III-C, Section IV-C): the same rounds with labels
  * = blocks 0..k-1 and U = lmax.

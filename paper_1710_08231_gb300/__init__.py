@@ -51,7 +51,7 @@ class GpParams(ctypes.Structure):
                 ("coarse_per_k", I64), ("stall_pct", I64), ("max_levels", I64), ("ip_tries", I64),
                 ("repair_rounds", I64), ("mode", I32), ("deg_warp", I32), ("deg_cta", I32), ("coarsen", I32),
                 ("mlp", VP), ("hub_batch_slots", I64), ("verts_per_block", I64), ("mls_global_iters", I64),
-                ("lp_async", I64)]
+                ("lp_async", I64), ("hub_keep_slots", I64)]
 
 
 class GpMlsParams(ctypes.Structure):
@@ -174,6 +174,8 @@ def lib():
         L.gp_autotune.argtypes = [ctypes.POINTER(GpGraph), ctypes.POINTER(GpParams), VP, VP]
         L.gp_lp_set_tiles.restype = ctypes.c_int
         L.gp_lp_set_tiles.argtypes = [I64, I64]
+        L.gp_lp_set_hub_keep.restype = ctypes.c_int
+        L.gp_lp_set_hub_keep.argtypes = [I64, I32]
         L.gp_set_wait_limit.restype = ctypes.c_int
         L.gp_set_wait_limit.argtypes = [U64]
         L.gp_pinned_stage_allocs.restype = I64
@@ -504,6 +506,12 @@ def lp_set_schedule(deg_warp: int = 0, deg_cta: int = 0):
 def lp_set_tiles(hub_batch_slots: int = 0, verts_per_block: int = 0):
     """LP tile sizes for gp_lp_cluster/gp_lp_refine (0 = defaults); results never depend on them."""
     _check(lib().gp_lp_set_tiles(hub_batch_slots, verts_per_block), "gp_lp_set_tiles")
+
+
+def lp_set_hub_keep(slots: int = 0, max_load_pct: int = 0):
+    """Kept hub tables: slots for gp_lp_cluster/gp_lp_refine (0 = default budget, negative = never
+    kept); max_load_pct for every LP call (0 = default 75; 1 = stale at the first new label)."""
+    _check(lib().gp_lp_set_hub_keep(slots, max_load_pct), "gp_lp_set_hub_keep")
 
 
 def set_wait_limit(ns: int = 0):

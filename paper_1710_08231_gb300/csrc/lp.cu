@@ -81,7 +81,7 @@ struct __align__(8) SubCounters {
   unsigned int hub_chunks;
   unsigned int n_big;  // marking items of admitted movers of degree > kBigDeg (done by all blocks)
   unsigned int hub_batches;
-  unsigned int pad;
+  unsigned int n_inval;  // kept hub tables that went stale in the sub-round (listed in hub_inval)
   unsigned long long max_gain, max_q;
 };
 
@@ -96,6 +96,7 @@ struct LpCounters {
                                    // hub prefix (block 0's view)
   unsigned long long contest_small, contest_packed, contest_large;
   unsigned long long contest_large_items, hub_entries, hub_slots;
+  unsigned long long hub_built_entries, hub_stale;  // entries of hubs (re)accumulated; kept tables gone stale
   int err;
   int pad;
 };
@@ -118,7 +119,11 @@ struct LpProblem {
   int singletons;  // labels start as singletons (the first sub-round needs no aggregation)
   int has_hubs;
   int hub_dense;  // hub tables indexed by label directly (few labels: refinement with small k)
-  int64_t hub_table_slots;  // slots allocated for one batch of hub tables
+  int hub_keep;   // hub tables kept across sub-rounds and updated by the moves (else one batch pass each)
+  int sub_t;      // the current sub-round 2 r + s (each block's shared copy)
+  int hub_n;      // vertices above deg_cta (kept tables: hub indices 0..hub_n-1)
+  int hub_keep_pct;  // a kept table goes stale when its key bound would pass this share of its slots
+  int64_t hub_table_slots;  // slots allocated for one batch of hub tables (kept: for all hubs)
   int deg_warp, deg_cta;
   int block_begin, block_count;
   int32_t *labels;
@@ -161,6 +166,14 @@ struct LpProblem {
   // 128-byte line per counter so that the blocks' reservations on different bins do not queue on one
   // line
   unsigned int *binres;
+  // kept hub tables (hub_keep): per vertex (global id) its hub index or -1; per hub index its table
+  // base and slots, an upper bound of the keys in its table and whether the table is current; the hubs
+  // whose tables went stale in a sub-round (cleared in the next one, rebuilt at their next activation)
+  int32_t *hub_id;
+  int64_t *hub_pbase, *hub_pcap;
+  unsigned long long *hub_keycnt;
+  int *hub_valid;
+  int *hub_inval;
   LpCounters *ctr;
 };
 
@@ -335,6 +348,126 @@ __device__ __forceinline__ long long block_sum_of(long long x, Smem &sm) {
   return r;
 }
 
+// ------------------------------------------------------------------------------------ kept hub tables
+// With hub_keep, each hub's table persists over the LP call: it is accumulated from the hub's row when
+// the hub is first active (or after it went stale), and every admitted move of a neighbour u from
+// label A to label B then moves w(u, hub) from A's slot to B's. The table stays equal to the hub's
+// connection per label at the start of every sub-round, so the choice reads the same sums as a fresh
+// accumulation would (integer sums: the order of the updates does not matter). A table's key count
+// starts at min(d, labels) after an accumulation (an upper bound of its distinct labels) and grows by
+// one per claimed slot; a table that would pass hub_keep_pct % of its slots (default 75) goes stale: it
+// takes no more updates, is cleared in the next sub-round and accumulated again at the hub's next
+// activation.
+__device__ __forceinline__ bool hub_deltas_on(const LpProblem &P) { return P.hub_keep && P.sub_t + 1 < 2 * P.rounds; }
+
+__device__ void hub_stale(const LpProblem &P, SubCounters &C, int h) {
+  if (atomicExch(&P.hub_valid[h], 0) == 1) {
+    const unsigned pos = atomicAdd(&C.n_inval, 1u);
+    if (pos < (unsigned)P.hub_n) P.hub_inval[pos] = h;  // (each hub goes stale at most once per sub-round)
+    atomicAdd(&P.ctr->hub_stale, 1ull);
+  }
+}
+
+// w moves from label A to label B in hub h's table (h's neighbour moved).
+__device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h, int A, int B, long long w) {
+  if (*(volatile int *)&P.hub_valid[h] == 0) return;
+  const int64_t tb = P.hub_pbase[h];
+  if (P.hub_dense) {
+    atomicAdd(&P.hub_vals[tb + (A - P.lbase)], (unsigned long long)(-w));
+    atomicAdd(&P.hub_vals[tb + (B - P.lbase)], (unsigned long long)w);
+    return;
+  }
+  const uint64_t cap = (uint64_t)P.hub_pcap[h];
+  // A has a slot (the neighbour's weight is in it); slots are only ever claimed, never freed, so the
+  // probe sequence up to A's slot is occupied
+  uint64_t sl = hub_slot(A, cap);
+  for (uint64_t pr = 0;; pr++) {
+    const int k = *(volatile int *)&P.hub_keys[tb + sl];
+    if (k == A) {
+      atomicAdd(&P.hub_vals[tb + sl], (unsigned long long)(-w));
+      break;
+    }
+    if (k == -1 || pr >= cap) {  // (not reachable for a current table)
+      hub_stale(P, C, h);
+      return;
+    }
+    sl = sl + 1 == cap ? 0 : sl + 1;
+  }
+  sl = hub_slot(B, cap);
+  for (uint64_t pr = 0;; pr++) {
+    int k = *(volatile int *)&P.hub_keys[tb + sl];
+    if (k == -1) {
+      if (atomicAdd(&P.hub_keycnt[h], 1ull) >= (cap * (uint64_t)P.hub_keep_pct) / 100) {
+        hub_stale(P, C, h);
+        return;
+      }
+      k = atomicCAS(&P.hub_keys[tb + sl], -1, B);
+      if (k == -1) k = B;
+    }
+    if (k == B) {
+      atomicAdd(&P.hub_vals[tb + sl], (unsigned long long)w);
+      return;
+    }
+    if (pr >= cap) {
+      hub_stale(P, C, h);
+      return;
+    }
+    sl = sl + 1 == cap ? 0 : sl + 1;
+  }
+}
+
+// The neighbour walk of a warp's admitted movers (rows concatenated, one entry per lane per step) with
+// kept hub tables: every neighbour is marked (act_next non-NULL) and every hub neighbour's table
+// follows the move (lane j's mover leaves label A for label B).
+__device__ __forceinline__ void walk_movers_kept(const LpProblem &P, SubCounters &C, uint8_t *act_next, int64_t rb,
+                                              int64_t excl, int64_t total, int A, int B) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t0 = 0; t0 < total; t0 += 32) {
+    const int64_t t = t0 + lane;
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int64_t ex = __shfl_sync(kFull, excl, j + step);
+      if (j + step < 32 && ex <= t) j += step;
+    }
+    const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
+    const int Aj = __shfl_sync(kFull, A, j), Bj = __shfl_sync(kFull, B, j);
+    if (t < total) {
+      const int64_t e = rbj + (t - exj);
+      const int a = __ldg(P.g.adj + e);
+      if (act_next) act_next[a] = 1;
+      const int h = P.hub_id[a];
+      if (h >= 0) hub_delta(P, C, h, Aj, Bj, P.g.eweight(e));
+    }
+  }
+}
+
+// Stale kept tables of the previous sub-round are cleared (a block per hub) before any is rebuilt.
+__device__ void hub_clear_stale(const LpProblem &P, unsigned ninv, int lb, int nb) {
+  ninv = min(ninv, (unsigned)P.hub_n);
+  for (unsigned j = lb; j < ninv; j += nb) {
+    const int h = P.hub_inval[j];
+    const int64_t tb = P.hub_pbase[h], cap = P.hub_pcap[h];
+    for (int64_t x = threadIdx.x; x < cap; x += kThreads) {
+      P.hub_keys[tb + x] = -1;
+      P.hub_vals[tb + x] = 0;
+    }
+  }
+}
+
+// Connection of label L in a hub's table (0 when absent).
+__device__ long long hub_lookup(const LpProblem &P, int64_t tb, uint64_t cap, int L) {
+  if (P.hub_dense) return (long long)P.hub_vals[tb + (L - P.lbase)];
+  uint64_t sl = hub_slot(L, cap);
+  for (uint64_t pr = 0; pr < cap; pr++) {
+    const int k = P.hub_keys[tb + sl];
+    if (k == L) return (long long)P.hub_vals[tb + sl];
+    if (k == -1) return 0;
+    sl = sl + 1 == cap ? 0 : sl + 1;
+  }
+  return 0;
+}
+
 // ------------------------------------------------------------------------------------ moves
 // Applies the admitted movers of a warp (all lanes call; `adm` marks the lanes whose proposal idx of
 // vertex v to target T was admitted): new label, the left label recorded for the weight update of the
@@ -355,7 +488,8 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   }
   const unsigned am = __ballot_sync(kFull, adm);
   if (!am) return 0;
-  if (!act_next) return (unsigned)__popc(am);
+  const bool dl = hub_deltas_on(P);
+  if (!act_next && !dl) return (unsigned)__popc(am);
   const bool big = adm && deg > kBigDeg;
   if (__any_sync(kFull, big)) {
     // one marking item per kBigChunk entries; the warp reserves all of its items with one atomic
@@ -383,6 +517,10 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   }
   const int64_t excl = incl - deg;
   const int64_t total = __shfl_sync(kFull, incl, 31);
+  if (dl) {
+    walk_movers_kept(P, C, act_next, rb, excl, total, L0, T);
+    return (unsigned)__popc(am);
+  }
   // four entries per lane per step: all adjacency loads are issued before any mark is stored
   constexpr int kMarkUnroll = 4;
   for (int64_t t0 = 0; t0 < total; t0 += 32 * kMarkUnroll) {
@@ -420,15 +558,28 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters
 }
 
 // Neighbours of the high-degree movers: every block takes marking items (kBigChunk entries of one
-// mover's row) in turn.
-__device__ void mark_big(const LpProblem &P, unsigned nitems, int r, int lb, int nb) {
-  uint8_t *act_next = P.act[(r + 1) & 1];
+// mover's row) in turn; kept hub tables among them follow the move.
+__device__ void mark_big(const LpProblem &P, SubCounters &C, unsigned nitems, int r, int lb, int nb) {
+  uint8_t *act_next = r + 1 < P.rounds ? P.act[(r + 1) & 1] : nullptr;  // (no marks in the last round)
+  const bool dl = hub_deltas_on(P);
   for (unsigned i = lb; i < nitems; i += nb) {
     const unsigned long long it = P.big[i];
     const int v = (int)(it >> 32);
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
     const int64_t beg = rb + (int64_t)(unsigned)(it & 0xffffffffu) * kBigChunk, end = min(re, beg + kBigChunk);
-    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) act_next[__ldg(P.g.adj + e)] = 1;
+    int A = 0, B = 0;
+    if (dl) {
+      B = P.labels[P.vbase + v];
+      A = P.mv_from[P.mv_of_v[v]];
+    }
+    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
+      const int a = __ldg(P.g.adj + e);
+      if (act_next) act_next[a] = 1;
+      if (dl) {
+        const int h = P.hub_id[a];
+        if (h >= 0) hub_delta(P, C, h, A, B, P.g.eweight(e));
+      }
+    }
   }
 }
 
@@ -1006,8 +1157,10 @@ __device__ void choose_cta(const LpProblem &P, const SubCounters &V, int lb, int
 // Hubs (d > deg_cta), done by block 0 for the sub-round's hub list: prefixes of work chunks (P.hub_chunk
 // entries), table slots (hub_cap(d) each) and choice items (kSlotChunk slots); cut into batches of
 // about P.hub_batch_slots slots (a hub starts a new batch when its slot prefix crosses a multiple of
-// that size); table base of each hub inside its batch.
-__device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm) {
+// that size); table base of each hub inside its batch. With kept tables there is one batch, every hub
+// keeps its own table base, and only hubs whose table is not current get accumulation chunks (the
+// first sub-round of a clustering from singletons scans every row directly: `direct`).
+__device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters &V, Smem &sm, bool direct) {
   const unsigned cnt = V.bin_count[6];
   __shared__ long long s_cap, s_ch, s_sc, s_nbat, s_prev_bid;
   __shared__ long long t_bid[kThreads];
@@ -1016,11 +1169,11 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     s_prev_bid = -1;
   }
   __syncthreads();
-  long long sum_d = 0, sum_cap = 0;
+  long long sum_d = 0, sum_cap = 0, sum_built = 0;
   for (unsigned base = 0; base < cnt; base += kThreads) {
     const unsigned i = base + threadIdx.x;
     const bool valid = i < cnt;
-    long long d = 0, cap = 0, ch = 0, sc = 0;
+    long long d = 0, cap = 0, ch = 0, sc = 0, ktb = 0;
     if (valid) {
       const int v = P.bin[6][i];
       d = P.g.row_begin(v + 1) - P.g.row_begin(v);
@@ -1028,6 +1181,25 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
       // table is indexed by the label itself
       cap = P.hub_dense ? P.nl : min(hub_cap(d), hub_cap(P.nl));
       ch = (d + P.hub_chunk - 1) >> P.hub_chunk_shift;
+      if (P.hub_keep && !direct) {
+        const int h = P.hub_id[P.vbase + v];
+        if (h < 0) {  // (every vertex above deg_cta has a hub index)
+          table_full(P.ctr, 6);
+          ch = 0;
+          cap = 0;
+        } else {
+          ktb = P.hub_pbase[h];
+          if (P.hub_valid[h]) {
+            ch = 0;  // current: no accumulation
+          } else {
+            P.hub_valid[h] = 1;
+            P.hub_keycnt[h] = (unsigned long long)min(d, (long long)P.nl);
+            sum_built += d;
+          }
+        }
+      } else {
+        sum_built += d;
+      }
       sc = (cap + kSlotChunk - 1) / kSlotChunk;
       P.hub_c0[i] = 0;
       sum_d += d;
@@ -1039,7 +1211,7 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     const long long ch_t = sm.tot;
     const long long scx = s_sc + block_excl_scan64(sc, sm.tmp, &sm.tot);
     const long long sc_t = sm.tot;
-    const long long bid = capx / P.hub_batch_slots;
+    const long long bid = P.hub_keep ? 0 : capx / P.hub_batch_slots;
     t_bid[threadIdx.x] = bid;
     __syncthreads();
     const long long prev = threadIdx.x > 0 ? t_bid[threadIdx.x - 1] : s_prev_bid;
@@ -1057,7 +1229,7 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
     }
     __syncthreads();
     if (valid) {
-      P.hub_tb[i] = capx - P.hub_bbase[bx + flag - 1];
+      P.hub_tb[i] = P.hub_keep ? ktb : capx - P.hub_bbase[bx + flag - 1];
       // (a sizing invariant: a batch's tables fit the allocation; checked, not assumed)
       if (P.hub_tb[i] + cap > P.hub_table_slots) table_full(P.ctr, 5);
     }
@@ -1094,9 +1266,11 @@ __device__ void hub_prefix(const LpProblem &P, SubCounters &C, const SubCounters
   }
   sum_d = block_sum_of(sum_d, sm);
   sum_cap = block_sum_of(sum_cap, sm);
+  sum_built = block_sum_of(sum_built, sm);
   if (threadIdx.x == 0) {
     P.ctr->hub_entries += (unsigned long long)sum_d;
     P.ctr->hub_slots += (unsigned long long)sum_cap;
+    P.ctr->hub_built_entries += (unsigned long long)sum_built;
   }
 }
 
@@ -1158,7 +1332,7 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           if (in[u] && L[u] == L0) c0 += w[u];
-          const bool on = in[u] && L[u] != L0;
+          const bool on = in[u] && (P.hub_keep || L[u] != L0);  // kept tables hold the own label too
           const unsigned peers = __match_any_sync(kFull, on ? L[u] : -1);
           long long sum = 0;
           if (on)
@@ -1168,6 +1342,7 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
         }
       }
       c0 = block_sum_of(c0, sm);  // also completes the counters
+      if (P.hub_keep) c0 = 0;       // (kept tables: the choice looks the own label up)
       for (int t = threadIdx.x; t < nl; t += kThreads) {
         const unsigned long long x = svals[t];
         if (x) {
@@ -1211,7 +1386,8 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         if (in[u] && L[u] == L0) c0 += w[u];
-        warp_insert<EW, LQ>(skeys, svals, sq, kCap - 1, in[u] && L[u] != L0, L[u], w[u], q4[u], P.ctr, 3);
+        warp_insert<EW, LQ>(skeys, svals, sq, kCap - 1, in[u] && (P.hub_keep || L[u] != L0), L[u], w[u], q4[u], P.ctr,
+                            3);
       }
     }
     c0 = block_sum_of(c0, sm);  // also completes the shared table
@@ -1259,12 +1435,13 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
+    if (threadIdx.x == 0 && c0 && !P.hub_keep)
+      atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
   }
 }
 
 // Choice for batch [h0, h1), part 1: the batch's tables are scanned in items of kSlotChunk slots by all
-// blocks; each item keeps its best eligible label (and clears its slots).
+// blocks; each item keeps its best eligible label (and clears its slots, unless the tables are kept).
 template <bool LQ>
 __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm) {
   const unsigned s_lo = P.hub_scx[h0], s_hi = P.hub_scx[h1];
@@ -1277,7 +1454,17 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
     const int64_t tb = P.hub_tb[i];
     const int64_t s0 = (int64_t)(it - P.hub_scx[i]) * kSlotChunk, s1 = min(cap, s0 + kSlotChunk);
     const int L0 = P.labels[P.vbase + v];
-    const long long c0 = P.hub_c0[i];
+    long long c0 = P.hub_c0[i];
+    if (P.hub_keep) {
+      // a kept table holds the own label's connection; the hub's first item records it for the final step
+      __shared__ long long s_c0;
+      if (threadIdx.x == 0) {
+        s_c0 = hub_lookup(P, tb, (uint64_t)cap, L0);
+        if (it == P.hub_scx[i]) P.hub_c0[i] = s_c0;
+      }
+      __syncthreads();
+      c0 = s_c0;
+    }
     const long long cv = P.g.vweight(v);
     Best b = no_best();
     for (int64_t base = s0; base < s1; base += kU * kThreads) {
@@ -1305,6 +1492,7 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
         const int64_t sl = base + u * kThreads + threadIdx.x;
         const Best x = make_cand_lw(P, v, L[u], L0, cw[u], (long long)qq[u], c0, cv, lwL[u]);
         if (better(x, b)) b = x;
+        if (P.hub_keep) continue;  // kept tables stay
         if (!P.hub_dense) P.hub_keys[tb + sl] = -1;
         P.hub_vals[tb + sl] = 0;
         if (LQ) P.hub_qv[tb + sl] = 0;
@@ -1892,15 +2080,24 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           Cn.n_movers = 0;
           Cn.n_contested = 0;
           Cn.hub_chunks = 0;
+          Cn.n_inval = 0;
           Cn.n_big = 0;
           Cn.hub_batches = 0;
           Cn.max_gain = 0;
           Cn.max_q = 0;
         }
       }
-      if (threadIdx.x == 0) sVp = sV;  // the counters of sub-round t-1
+      __shared__ unsigned s_stale;
+      if (threadIdx.x == 0) {
+        sVp = sV;  // the counters of sub-round t-1
+        P.sub_t = t;
+        // kept hub tables that went stale in sub-round t-1 (its counters are final: every block has
+        // passed the barrier after its last update)
+        s_stale = (P.hub_keep && t > 0) ? *(volatile unsigned *)&ctr->sc[(t + 2) % 3].n_inval : 0u;
+      }
       __syncthreads();
       phase_classify(P, C, t > 0 ? &sVp : nullptr, r, s, rmix, lb, nb, sm);
+      if (s_stale) hub_clear_stale(P, s_stale, lb, nb);
       if (!grid_sync(bar)) return false;
       load_view(C, t);
       tick(0);
@@ -1908,13 +2105,13 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       unsigned active = 0;
       for (int b = 0; b < kBins; b++) active += sV.bin_count[b];
       if (active > 0) {
+        // only the first sub-round sees every label as a singleton (the second follows its moves)
+        const bool direct = P.singletons && t == 0;
         if (lb == 0 && P.has_hubs && sV.bin_count[6]) {
-          hub_prefix(P, C, sV, sm);
+          hub_prefix(P, C, sV, sm, direct);
           tick(7);
         }
         choose_groups<EW, LQ>(P, sV, lb, nb);
-        // only the first sub-round sees every label as a singleton (the second follows its moves)
-        const bool direct = P.singletons && t == 0;
         choose_warp<EW, TB>(P, sV, lb, nb, dsm, direct);
         choose_cta<EW, TB>(P, sV, lb, nb, dsm, sm, direct);
         if (!grid_sync(bar)) return false;
@@ -1932,8 +2129,11 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           const unsigned nbat = sV.hub_batches;
           for (unsigned bt = 0; bt < nbat; bt++) {
             const unsigned h0 = P.hub_bstart[bt], h1 = P.hub_bstart[bt + 1];
-            hub_accum<EW, TB>(P, h0, h1, lb, nb, sm, dsm);
-            if (!grid_sync(bar)) return false;
+            // (kept tables: only hubs whose table is not current have chunks; none: no pass)
+            if (!P.hub_keep || sV.hub_chunks) {
+              hub_accum<EW, TB>(P, h0, h1, lb, nb, sm, dsm);
+              if (!grid_sync(bar)) return false;
+            }
             tick(2);
             hub_choose_part<LQ>(P, h0, h1, lb, nb, sm);
             if (!grid_sync(bar)) return false;
@@ -1960,7 +2160,7 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
           tick(4);
         }
         if (sV.n_big > 0) {
-          mark_big(P, sV.n_big, r, lb, nb);
+          mark_big(P, C, sV.n_big, r, lb, nb);
           if (!grid_sync(bar)) return false;
           tick(4);
         }
@@ -2073,6 +2273,32 @@ __global__ void k_degree_classes(const DGraph *gs, const int64_t *pre, int njobs
   }
 }
 
+// Hub indices and kept-table bases of one LP problem: every vertex above deg_cta gets an index and a
+// table of `cap` slots (2 min(d, nl) rounded up to 64, or nl for dense tables) at a base taken from a
+// counter (the layout depends on the schedule; results do not). Indices or slots beyond what the launch
+// allocated (against the degree classes' counts) are recorded as an internal error.
+__global__ void k_hub_index(DGraph g, int64_t vbase, int deg_cta, int64_t nl, int dense, int nhub, int64_t slots,
+                            int32_t *hub_id, int64_t *pbase, int64_t *pcap, unsigned long long *next,
+                            LpCounters *ctr) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
+    int h = -1;
+    if (d > deg_cta) {
+      const int64_t cap = dense ? nl : min(hub_cap(d), hub_cap(nl));
+      const unsigned long long x = atomicAdd(&next[0], 1ull);
+      const unsigned long long b = atomicAdd(&next[1], (unsigned long long)cap);
+      if (x < (unsigned long long)nhub && (int64_t)b + cap <= slots) {
+        h = (int)x;
+        pbase[h] = (int64_t)b;
+        pcap[h] = cap;
+      } else {
+        table_full(ctr, 7);
+      }
+    }
+    hub_id[vbase + v] = h;
+  }
+}
+
 constexpr int kSmallK = 2048;
 
 __global__ void k_block_weights(DGraph g, const int32_t *part, int64_t k, int64_t *bw, int *bad) {
@@ -2146,6 +2372,8 @@ LpConfig lp_config_from(const gp_params *p) {
   c.deg_cta = std::max(c.deg_warp, std::min(c.deg_cta, kCtaCap / 2));
   if (p && p->hub_batch_slots > 0) c.hub_batch_slots = p->hub_batch_slots;
   if (p && p->verts_per_block > 0) c.verts_per_block = p->verts_per_block;
+  if (p && p->hub_keep_slots != 0) c.hub_keep_slots = std::max<int64_t>(0, p->hub_keep_slots);
+  c.hub_keep_pct = std::max(1, std::min(c.hub_keep_pct, 95));
   c.hub_batch_slots = std::max<int64_t>(kMinHubBatchSlots, std::min<int64_t>(c.hub_batch_slots, kMaxHubBatchSlots));
   c.verts_per_block = std::max<int64_t>(kMinVertsPerBlock, std::min<int64_t>(c.verts_per_block, kMaxVertsPerBlock));
   return c;
@@ -2235,6 +2463,13 @@ static int account_counters(const LpCounters *hc, int n, const int64_t *vb, cons
     prof_add_counts("lp_contest_packed_calls", (int64_t)cp, 0, 0);
     prof_add_counts("lp_contest_large_calls", (int64_t)cl, (int64_t)cli, 0);  // edges: contested movers
     prof_add_counts("lp_hub_work", (int64_t)hs, (int64_t)he, 0);  // items: table slots, edges: entries
+    double hb = 0, hst = 0;
+    for (int j = 0; j < n; j++) {
+      hb += hc[j].hub_built_entries;
+      hst += hc[j].hub_stale;
+    }
+    // items: kept tables gone stale, edges: hub entries accumulated (the rest followed the moves)
+    prof_add_counts("lp_hub_built", (int64_t)hst, (int64_t)hb, 0);
   }
   return GP_OK;
 }
@@ -2487,6 +2722,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.zeros(&demand_all, total));
   }
   size_t demand_off = 0;
+  int64_t keep_total = 0;  // slots of the kept hub tables of the launch
   for (int j = 0; j < njobs; j++) {
     const LpJob &jb = jobs[j];
     LpProblem &P = hp[j];
@@ -2547,9 +2783,19 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.bar = bar_all + (size_t)j * kBarrierStride;
     const unsigned nhub = hcls[9 * j + 6];
     if (nhub) {
-      // tables of one batch of hubs (reused batch after batch), partial choices, per-hub arrays
+      // dense tables need nl <= 2 (deg_cta + 1) <= hub_cap(d) for every hub (the tables are sized by
+      // hub_cap(d)) and the counters in the CTA's shared table
+      P.hub_dense = (!lq && jb.nl <= 2 * ((int64_t)cfg.deg_cta + 1) && jb.nl <= (tb == 2 ? kCtaCapT<2> : kCtaCapT<1>))
+                        ? 1 : 0;
+      // tables of one batch of hubs (reused batch after batch), or of every hub when they are kept,
+      // partial choices, per-hub arrays
       const int64_t max_cap = (int64_t)hhub[3 * (size_t)j], cap_sum = (int64_t)hhub[3 * (size_t)j + 1];
-      const int64_t slots = std::min<int64_t>(cfg.hub_batch_slots, cap_sum) + max_cap;
+      const int64_t keep_need = P.hub_dense ? (int64_t)nhub * jb.nl : cap_sum;
+      const bool keep = !lq && cfg.hub_keep_slots > 0 && keep_total + keep_need <= cfg.hub_keep_slots;
+      if (keep) keep_total += keep_need;
+      // (kept dense tables take nl slots per hub; hashed ones at most hub_cap(d))
+      const int64_t slots = keep ? std::max<int64_t>(keep_need, 1)
+                                 : std::min<int64_t>(cfg.hub_batch_slots, cap_sum) + max_cap;
       P.hub_table_slots = slots;
       // items of one batch: at most slots / kSlotChunk full items plus one partial item per hub; the
       // round-0 direct path keeps one item per chunk of every hub row
@@ -2567,10 +2813,25 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       GP_TRY(ws.get(&P.hub_bstart, (size_t)nhub + 1));
       GP_TRY(ws.get(&P.hub_bbase, (size_t)nhub + 1));
       P.has_hubs = 1;
-      // dense tables need nl <= 2 (deg_cta + 1) <= hub_cap(d) for every hub (the tables are sized by
-      // hub_cap(d)) and the counters in the CTA's shared table
-      P.hub_dense = (!lq && jb.nl <= 2 * ((int64_t)cfg.deg_cta + 1) && jb.nl <= (tb == 2 ? kCtaCapT<2> : kCtaCapT<1>))
-                        ? 1 : 0;
+      if (keep) {
+        P.hub_keep = 1;
+        P.hub_keep_pct = cfg.hub_keep_pct;
+        P.hub_n = (int)nhub;
+        GP_TRY(ws.get(&P.hub_id, n));
+        P.hub_id -= jb.vbase;  // indexed by global vertex id
+        GP_TRY(ws.get(&P.hub_pbase, (size_t)nhub));
+        GP_TRY(ws.get(&P.hub_pcap, (size_t)nhub));
+        GP_TRY(ws.zeros(&P.hub_keycnt, (size_t)nhub));
+        GP_TRY(ws.zeros(&P.hub_valid, (size_t)nhub));
+        GP_TRY(ws.get(&P.hub_inval, (size_t)nhub));
+        unsigned long long *next;
+        GP_TRY(ws.zeros(&next, 2));
+        const int grid_h = (int)std::max<int64_t>(1, std::min<int64_t>((jb.g.n + 255) / 256, (int64_t)nsm * 8));
+        (::gp::count_launch(), k_hub_index<<<grid_h, 256, 0, s>>>(jb.g, jb.vbase, cfg.deg_cta, jb.nl, P.hub_dense,
+                                                                    (int)nhub, slots, P.hub_id, P.hub_pbase,
+                                                                    P.hub_pcap, next, P.ctr));
+        GP_LAUNCH_CHECK();
+      }
     }
   }
   LpProblem *probs_dev;

@@ -16,6 +16,10 @@ struct LpConfig {
   // fewest vertices per block of a problem
   int64_t hub_batch_slots = int64_t(1) << 26;
   int64_t verts_per_block = 64;
+  // hub tables are kept across sub-rounds (updated by the moves) when all hubs' tables of a launch take
+  // at most this many slots; 0: never
+  int64_t hub_keep_slots = int64_t(1) << 32;
+  int hub_keep_pct = 75;  // a kept table goes stale (rebuilt at the hub's next activation) past this load
 };
 constexpr int64_t kMinHubBatchSlots = 4096, kMaxHubBatchSlots = int64_t(1) << 28;
 constexpr int64_t kMinVertsPerBlock = 16, kMaxVertsPerBlock = 4096;

@@ -96,6 +96,7 @@ __global__ void k_tries_cut(DGraph g, const int32_t *parts, int tries, unsigned 
 }
 
 gp_params g_schedule = {};
+int g_keep_pct = 0;  // stale threshold of kept hub tables (0: default)
 
 LpConfig schedule_for(const gp_params *p) {
   gp_params q = g_schedule;
@@ -103,7 +104,10 @@ LpConfig schedule_for(const gp_params *p) {
   if (p && p->deg_cta > 0) q.deg_cta = p->deg_cta;
   if (p && p->hub_batch_slots > 0) q.hub_batch_slots = p->hub_batch_slots;
   if (p && p->verts_per_block > 0) q.verts_per_block = p->verts_per_block;
-  return lp_config_from(&q);
+  if (p && p->hub_keep_slots != 0) q.hub_keep_slots = p->hub_keep_slots;
+  LpConfig c = lp_config_from(&q);
+  if (g_keep_pct > 0) c.hub_keep_pct = std::max(1, std::min(g_keep_pct, 95));
+  return c;
 }
 
 int grid_n(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, num_sms() * 8)); }
@@ -772,6 +776,16 @@ int gp_lp_set_tiles(int64_t hub_batch_slots, int64_t verts_per_block) {
   }
   g_schedule.hub_batch_slots = hub_batch_slots;
   g_schedule.verts_per_block = verts_per_block;
+  return GP_OK;
+}
+
+int gp_lp_set_hub_keep(int64_t slots, int32_t max_load_pct) {
+  if (max_load_pct < 0 || max_load_pct > 95) {
+    set_error("gp_lp_set_hub_keep: max_load_pct must be in [0, 95]");
+    return GP_ERR_INVALID_ARG;
+  }
+  g_schedule.hub_keep_slots = slots;
+  g_keep_pct = max_load_pct;
   return GP_OK;
 }
 

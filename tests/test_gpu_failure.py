@@ -28,6 +28,7 @@ def gp():
     m.build()
     m.lp_set_schedule(0, 0)
     m.lp_set_tiles(0, 0)
+    m.lp_set_hub_keep(0, 0)
     return m
 
 

@@ -219,17 +219,23 @@ def test_determinism_repeated_runs(gp):
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
-# ---- the multi-batch hub path: a small hub batch size splits the hubs of one sub-round into many
-# batches, each with its own table pass (the path that dominates large power-law graphs)
+# ---- the hub path (vertices above deg_cta, several CTAs each). Three forms must give the oracle's
+# result: tables re-accumulated every sub-round in batches (a small batch size splits the hubs of one
+# sub-round into many batches, each with its own table pass); tables kept across sub-rounds and updated
+# by the moves (the default); kept tables that go stale at their first new label and are accumulated
+# again at the hub's next activation.
 HUB_CASES = [("rmat13", 32, 32, 4096), ("rmat13", 0, 0, 4096), ("rmat12w", 32, 64, 8192),
              ("rmat14", 32, 32, 16384)]
+HUB_FORMS = {"batches": (-1, 0), "kept": (0, 0), "kept_stale": (0, 1)}
 
 
+@pytest.mark.parametrize("form", list(HUB_FORMS))
 @pytest.mark.parametrize("name,dw,dc,slots", HUB_CASES)
-def test_lp_cluster_multi_batch_hubs_match_oracle(gp, name, dw, dc, slots):
+def test_lp_cluster_hub_forms_match_oracle(gp, name, dw, dc, slots, form):
     g = GRAPHS[name] if name in GRAPHS else gg.rmat(14, 16, seed=8)
     gp.lp_set_schedule(dw, dc)
     gp.lp_set_tiles(slots, 0)
+    gp.lp_set_hub_keep(*HUB_FORMS[form])
     try:
         dg = gp.DeviceGraph.from_host(g)
         gp.profile_read(reset=True)
@@ -240,38 +246,50 @@ def test_lp_cluster_multi_batch_hubs_match_oracle(gp, name, dw, dc, slots):
         lab_o, _, st_o = O.lp_cluster(g, 200, 10, 0xBEEF)
         assert np.array_equal(lab.cpu().numpy(), lab_o)
         _stats_eq(st, st_o)
-        # the hub tables of a sub-round with every vertex active are several batches' worth
-        d = np.diff(g.off)
-        hubs = d[d > (dc or 1024)]
-        assert ((2 * hubs + 63) // 64 * 64).sum() > 4 * slots
-        assert prof["lp_hub_work"]["items"] > 0
+        work, built = prof["lp_hub_work"], prof["lp_hub_built"]
+        assert work["items"] > 0
+        if form == "batches":
+            # the hub tables of a sub-round with every vertex active are several batches' worth
+            d = np.diff(g.off)
+            hubs = d[d > (dc or 1024)]
+            assert ((2 * hubs + 63) // 64 * 64).sum() > 4 * slots
+            assert built["edges"] == work["edges"]  # every active hub accumulated every sub-round
+        elif form == "kept":
+            assert built["edges"] < work["edges"]  # some hub sub-rounds followed the moves
+        else:
+            assert built["items"] > 0  # tables went stale and were accumulated again
     finally:
         gp.lp_set_schedule(0, 0)
         gp.lp_set_tiles(0, 0)
+        gp.lp_set_hub_keep(0, 0)
 
 
+@pytest.mark.parametrize("form", ["batches", "kept_stale"])
 @pytest.mark.parametrize("name,k", [("rmat13", 16), ("rmat12w", 8)])
-def test_lp_refine_and_partition_multi_batch_hubs_match_oracle(gp, name, k):
+def test_lp_refine_and_partition_hub_forms_match_oracle(gp, name, k, form):
     import torch
     g = GRAPHS[name]
     c = O.vertex_weights(g)
     lm = O.lmax(int(c.sum()), k, 0.03)
     part = np.random.default_rng(3).integers(0, k, g.n).astype(np.int32)
     dg = gp.DeviceGraph.from_host(g)
-    params = gp.default_params(deg_warp=32, deg_cta=32, hub_batch_slots=4096, coarse_min=300)
+    keep, pct = HUB_FORMS[form]
+    params = gp.default_params(deg_warp=32, deg_cta=32, hub_batch_slots=4096, coarse_min=300, hub_keep_slots=keep)
     oparams = O.default_params()
     oparams.coarse_min = 300
     gp.lp_set_schedule(32, 32)
     gp.lp_set_tiles(4096, 0)
+    gp.lp_set_hub_keep(keep, pct)
     try:
         p, bw, st = gp.lp_refine(dg, torch.from_numpy(part).cuda(), k, lm, 25, 77)
+        pp, res = gp.partition(dg, k, 0.03, 5, params)
     finally:
         gp.lp_set_schedule(0, 0)
         gp.lp_set_tiles(0, 0)
+        gp.lp_set_hub_keep(0, 0)
     p_o, bw_o, st_o = O.lp_refine(g, part, k, lm, 25, 77)
     assert np.array_equal(p.cpu().numpy(), p_o) and np.array_equal(bw.cpu().numpy(), bw_o)
     _stats_eq(st, st_o)
-    pp, res = gp.partition(dg, k, 0.03, 5, params)
     pp_o, res_o = O.partition(g, k, 0.03, 5, oparams)
     assert np.array_equal(pp.cpu().numpy(), pp_o) and res.cut == res_o.cut
 
