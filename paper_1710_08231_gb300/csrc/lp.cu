@@ -65,6 +65,7 @@ constexpr int kContestSmall = 4096;
 // bound by the dependent latency of each phase and more warps (fewer vertices per warp) shorten every
 // sub-round.
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
+constexpr int64_t kBigDegKept = 32;  // (with kept hub tables, whose updates make each entry dearer)
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
 constexpr size_t kDynSmem = kDynSmemT<0>;  // the smallest class (bound for the contest workspaces)
 static_assert(kWarps * kWarpCapT<2> * 12 <= (int)kDynSmemT<2> && kWarps * kWarpCapT<0> * 16 <= (int)kDynSmemT<0>,
@@ -368,76 +369,88 @@ __device__ void hub_stale(const LpProblem &P, SubCounters &C, int h) {
   }
 }
 
-// w moves from label A to label B in hub h's table (h's neighbour moved).
+// w moves from label A to label B in hub h's table (h's neighbour moved). The hub's words and the first
+// probes of both labels are loaded together.
 __device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h, int A, int B, long long w) {
-  if (*(volatile int *)&P.hub_valid[h] == 0) return;
+  const int valid = *(volatile int *)&P.hub_valid[h];
   const int64_t tb = P.hub_pbase[h];
+  const uint64_t cap = (uint64_t)P.hub_pcap[h];
+  if (!valid) return;
   if (P.hub_dense) {
     atomicAdd(&P.hub_vals[tb + (A - P.lbase)], (unsigned long long)(-w));
     atomicAdd(&P.hub_vals[tb + (B - P.lbase)], (unsigned long long)w);
     return;
   }
-  const uint64_t cap = (uint64_t)P.hub_pcap[h];
+  uint64_t sa = hub_slot(A, cap), sb = hub_slot(B, cap);
+  int ka = *(volatile int *)&P.hub_keys[tb + sa];
+  int kb = *(volatile int *)&P.hub_keys[tb + sb];
   // A has a slot (the neighbour's weight is in it); slots are only ever claimed, never freed, so the
   // probe sequence up to A's slot is occupied
-  uint64_t sl = hub_slot(A, cap);
   for (uint64_t pr = 0;; pr++) {
-    const int k = *(volatile int *)&P.hub_keys[tb + sl];
-    if (k == A) {
-      atomicAdd(&P.hub_vals[tb + sl], (unsigned long long)(-w));
+    if (ka == A) {
+      atomicAdd(&P.hub_vals[tb + sa], (unsigned long long)(-w));
       break;
     }
-    if (k == -1 || pr >= cap) {  // (not reachable for a current table)
+    if (ka == -1 || pr >= cap) {  // (not reachable for a current table)
       hub_stale(P, C, h);
       return;
     }
-    sl = sl + 1 == cap ? 0 : sl + 1;
+    sa = sa + 1 == cap ? 0 : sa + 1;
+    ka = *(volatile int *)&P.hub_keys[tb + sa];
   }
-  sl = hub_slot(B, cap);
   for (uint64_t pr = 0;; pr++) {
-    int k = *(volatile int *)&P.hub_keys[tb + sl];
-    if (k == -1) {
+    if (kb == -1) {
       if (atomicAdd(&P.hub_keycnt[h], 1ull) >= (cap * (uint64_t)P.hub_keep_pct) / 100) {
         hub_stale(P, C, h);
         return;
       }
-      k = atomicCAS(&P.hub_keys[tb + sl], -1, B);
-      if (k == -1) k = B;
+      kb = atomicCAS(&P.hub_keys[tb + sb], -1, B);
+      if (kb == -1) kb = B;
     }
-    if (k == B) {
-      atomicAdd(&P.hub_vals[tb + sl], (unsigned long long)w);
+    if (kb == B) {
+      atomicAdd(&P.hub_vals[tb + sb], (unsigned long long)w);
       return;
     }
     if (pr >= cap) {
       hub_stale(P, C, h);
       return;
     }
-    sl = sl + 1 == cap ? 0 : sl + 1;
+    sb = sb + 1 == cap ? 0 : sb + 1;
+    kb = *(volatile int *)&P.hub_keys[tb + sb];
   }
 }
 
-// The neighbour walk of a warp's admitted movers (rows concatenated, one entry per lane per step) with
-// kept hub tables: every neighbour is marked (act_next non-NULL) and every hub neighbour's table
-// follows the move (lane j's mover leaves label A for label B).
+// The neighbour walk of a warp's admitted movers (rows concatenated, two entries per lane per step, loads
+// first) with kept hub tables: every neighbour is marked (act_next non-NULL) and every hub neighbour's
+// table follows the move (lane j's mover leaves label A for label B). Movers of degree above
+// kBigDegKept are left to mark_big, so a warp walks at most 32 kBigDegKept entries.
 __device__ __forceinline__ void walk_movers_kept(const LpProblem &P, SubCounters &C, uint8_t *act_next, int64_t rb,
-                                              int64_t excl, int64_t total, int A, int B) {
+                                                 int64_t excl, int64_t total, int A, int B) {
   const int lane = threadIdx.x & 31;
-  for (int64_t t0 = 0; t0 < total; t0 += 32) {
-    const int64_t t = t0 + lane;
-    int j = 0;
+  for (int64_t t0 = 0; t0 < total; t0 += 64) {
+    int a[2], Ax[2], Bx[2], h[2];
+    int64_t e[2];
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int64_t ex = __shfl_sync(kFull, excl, j + step);
-      if (j + step < 32 && ex <= t) j += step;
+    for (int x = 0; x < 2; x++) {
+      const int64_t t = t0 + 32 * x + lane;
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int64_t ex = __shfl_sync(kFull, excl, j + step);
+        if (j + step < 32 && ex <= t) j += step;
+      }
+      const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
+      Ax[x] = __shfl_sync(kFull, A, j);
+      Bx[x] = __shfl_sync(kFull, B, j);
+      e[x] = rbj + (t - exj);
+      a[x] = t < total ? __ldg(P.g.adj + e[x]) : -1;
     }
-    const int64_t rbj = __shfl_sync(kFull, rb, j), exj = __shfl_sync(kFull, excl, j);
-    const int Aj = __shfl_sync(kFull, A, j), Bj = __shfl_sync(kFull, B, j);
-    if (t < total) {
-      const int64_t e = rbj + (t - exj);
-      const int a = __ldg(P.g.adj + e);
-      if (act_next) act_next[a] = 1;
-      const int h = P.hub_id[a];
-      if (h >= 0) hub_delta(P, C, h, Aj, Bj, P.g.eweight(e));
+#pragma unroll
+    for (int x = 0; x < 2; x++) h[x] = a[x] >= 0 ? P.hub_id[a[x]] : -1;
+#pragma unroll
+    for (int x = 0; x < 2; x++) {
+      if (a[x] >= 0 && act_next) act_next[a[x]] = 1;
+      if (h[x] >= 0) hub_delta(P, C, h[x], Ax[x], Bx[x], P.g.eweight(e[x]));
     }
   }
 }
@@ -490,7 +503,7 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   if (!am) return 0;
   const bool dl = hub_deltas_on(P);
   if (!act_next && !dl) return (unsigned)__popc(am);
-  const bool big = adm && deg > kBigDeg;
+  const bool big = adm && deg > (dl ? kBigDegKept : kBigDeg);
   if (__any_sync(kFull, big)) {
     // one marking item per kBigChunk entries; the warp reserves all of its items with one atomic
     const unsigned nit = big ? (unsigned)((deg + kBigChunk - 1) / kBigChunk) : 0u;
@@ -572,12 +585,24 @@ __device__ void mark_big(const LpProblem &P, SubCounters &C, unsigned nitems, in
       B = P.labels[P.vbase + v];
       A = P.mv_from[P.mv_of_v[v]];
     }
-    for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) {
-      const int a = __ldg(P.g.adj + e);
-      if (act_next) act_next[a] = 1;
-      if (dl) {
-        const int h = P.hub_id[a];
-        if (h >= 0) hub_delta(P, C, h, A, B, P.g.eweight(e));
+    if (!dl) {
+      for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) act_next[__ldg(P.g.adj + e)] = 1;
+      continue;
+    }
+    // four entries per thread in flight: adjacency, then hub indices, then the table updates
+    for (int64_t e0 = beg; e0 < end; e0 += 4 * kThreads) {
+      int a[4], h[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int64_t e = e0 + x * kThreads + threadIdx.x;
+        a[x] = e < end ? __ldg(P.g.adj + e) : -1;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; x++) h[x] = a[x] >= 0 ? P.hub_id[a[x]] : -1;
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        if (a[x] >= 0 && act_next) act_next[a[x]] = 1;
+        if (h[x] >= 0) hub_delta(P, C, h[x], A, B, P.g.eweight(e0 + x * kThreads + threadIdx.x));
       }
     }
   }
@@ -2770,8 +2795,10 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.ct2, n));
     GP_TRY(ws.get(&P.ck, n));
     GP_TRY(ws.get(&P.ck2, n));
-    // marking items: at most one per kBigChunk entries of every row plus one per high-degree vertex
-    GP_TRY(ws.get(&P.big, (size_t)(hent[j] / kBigChunk + hcls[9 * j + 5] + hcls[9 * j + 6] + 1)));
+    // marking items: at most one per kBigChunk entries of every row plus one per vertex above kBigDegKept
+    // (all of them in bins 4-6, which start above 32)
+    static_assert(kBigDegKept >= 32, "big movers lie in the warp, CTA and hub bins");
+    GP_TRY(ws.get(&P.big, (size_t)(hent[j] / kBigChunk + hcls[9 * j + 4] + hcls[9 * j + 5] + hcls[9 * j + 6] + 1)));
     GP_TRY(ws.get(&P.act[0], n));
     GP_TRY(ws.get(&P.act[1], n));
     P.act[0] -= jb.vbase;  // indexed by global vertex id
