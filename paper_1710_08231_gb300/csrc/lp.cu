@@ -65,7 +65,10 @@ constexpr int kContestSmall = 4096;
 // bound by the dependent latency of each phase and more warps (fewer vertices per warp) shorten every
 // sub-round.
 constexpr int64_t kBigDeg = 2048;    // movers above this degree mark their neighbours with every block
-constexpr int64_t kBigDegKept = 32;  // (with kept hub tables, whose updates make each entry dearer)
+// With kept hub tables (whose updates make each entry dearer) movers above degree 32 are listed in items
+// of at most 256 entries, which the warps of all blocks take in turn.
+constexpr int64_t kBigDegKept = 32;
+constexpr int64_t kBigChunkKept = 256;
 constexpr int64_t kBigChunk = 4096;  // entries per marking item of such a mover
 constexpr size_t kDynSmem = kDynSmemT<0>;  // the smallest class (bound for the contest workspaces)
 static_assert(kWarps * kWarpCapT<2> * 12 <= (int)kDynSmemT<2> && kWarps * kWarpCapT<0> * 16 <= (int)kDynSmemT<0>,
@@ -505,8 +508,10 @@ __device__ __forceinline__ unsigned apply_movers_pre(const LpProblem &P, SubCoun
   if (!act_next && !dl) return (unsigned)__popc(am);
   const bool big = adm && deg > (dl ? kBigDegKept : kBigDeg);
   if (__any_sync(kFull, big)) {
-    // one marking item per kBigChunk entries; the warp reserves all of its items with one atomic
-    const unsigned nit = big ? (unsigned)((deg + kBigChunk - 1) / kBigChunk) : 0u;
+    // one marking item per kBigChunk (kept tables: kBigChunkKept) entries; the warp reserves all of its
+    // items with one atomic
+    const int64_t chunk = dl ? kBigChunkKept : kBigChunk;
+    const unsigned nit = big ? (unsigned)((deg + chunk - 1) / chunk) : 0u;
     unsigned ex = nit;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -571,30 +576,34 @@ __device__ __forceinline__ unsigned apply_movers(const LpProblem &P, SubCounters
 }
 
 // Neighbours of the high-degree movers: every block takes marking items (kBigChunk entries of one
-// mover's row) in turn; kept hub tables among them follow the move.
+// mover's row) in turn. With kept hub tables the items hold kBigChunkKept entries and every warp takes
+// items in turn (four entries per lane in flight); the hub neighbours' tables follow the move.
 __device__ void mark_big(const LpProblem &P, SubCounters &C, unsigned nitems, int r, int lb, int nb) {
   uint8_t *act_next = r + 1 < P.rounds ? P.act[(r + 1) & 1] : nullptr;  // (no marks in the last round)
-  const bool dl = hub_deltas_on(P);
-  for (unsigned i = lb; i < nitems; i += nb) {
+  if (!hub_deltas_on(P)) {
+    for (unsigned i = lb; i < nitems; i += nb) {
+      const unsigned long long it = P.big[i];
+      const int v = (int)(it >> 32);
+      const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+      const int64_t beg = rb + (int64_t)(unsigned)(it & 0xffffffffu) * kBigChunk, end = min(re, beg + kBigChunk);
+      for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) act_next[__ldg(P.g.adj + e)] = 1;
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const unsigned nw = (unsigned)nb * kWarps;
+  for (unsigned i = (unsigned)lb * kWarps + (threadIdx.x >> 5); i < nitems; i += nw) {
     const unsigned long long it = P.big[i];
     const int v = (int)(it >> 32);
     const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-    const int64_t beg = rb + (int64_t)(unsigned)(it & 0xffffffffu) * kBigChunk, end = min(re, beg + kBigChunk);
-    int A = 0, B = 0;
-    if (dl) {
-      B = P.labels[P.vbase + v];
-      A = P.mv_from[P.mv_of_v[v]];
-    }
-    if (!dl) {
-      for (int64_t e = beg + threadIdx.x; e < end; e += kThreads) act_next[__ldg(P.g.adj + e)] = 1;
-      continue;
-    }
-    // four entries per thread in flight: adjacency, then hub indices, then the table updates
-    for (int64_t e0 = beg; e0 < end; e0 += 4 * kThreads) {
+    const int64_t beg = rb + (int64_t)(unsigned)(it & 0xffffffffu) * kBigChunkKept, end = min(re, beg + kBigChunkKept);
+    const int B = P.labels[P.vbase + v];
+    const int A = P.mv_from[P.mv_of_v[v]];
+    for (int64_t e0 = beg; e0 < end; e0 += 128) {
       int a[4], h[4];
 #pragma unroll
       for (int x = 0; x < 4; x++) {
-        const int64_t e = e0 + x * kThreads + threadIdx.x;
+        const int64_t e = e0 + 32 * x + lane;
         a[x] = e < end ? __ldg(P.g.adj + e) : -1;
       }
 #pragma unroll
@@ -602,7 +611,7 @@ __device__ void mark_big(const LpProblem &P, SubCounters &C, unsigned nitems, in
 #pragma unroll
       for (int x = 0; x < 4; x++) {
         if (a[x] >= 0 && act_next) act_next[a[x]] = 1;
-        if (h[x] >= 0) hub_delta(P, C, h[x], A, B, P.g.eweight(e0 + x * kThreads + threadIdx.x));
+        if (h[x] >= 0) hub_delta(P, C, h[x], A, B, P.g.eweight(e0 + 32 * x + lane));
       }
     }
   }
@@ -2795,10 +2804,12 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     GP_TRY(ws.get(&P.ct2, n));
     GP_TRY(ws.get(&P.ck, n));
     GP_TRY(ws.get(&P.ck2, n));
-    // marking items: at most one per kBigChunk entries of every row plus one per vertex above kBigDegKept
+    // marking items: at most one per kBigChunkKept entries of every row plus one per vertex above kBigDegKept
     // (all of them in bins 4-6, which start above 32)
     static_assert(kBigDegKept >= 32, "big movers lie in the warp, CTA and hub bins");
-    GP_TRY(ws.get(&P.big, (size_t)(hent[j] / kBigChunk + hcls[9 * j + 4] + hcls[9 * j + 5] + hcls[9 * j + 6] + 1)));
+    static_assert(kBigChunkKept <= kBigChunk, "the kept-table items bound the others");
+    GP_TRY(ws.get(&P.big,
+                  (size_t)(hent[j] / kBigChunkKept + hcls[9 * j + 4] + hcls[9 * j + 5] + hcls[9 * j + 6] + 1)));
     GP_TRY(ws.get(&P.act[0], n));
     GP_TRY(ws.get(&P.act[1], n));
     P.act[0] -= jb.vbase;  // indexed by global vertex id
