@@ -110,7 +110,7 @@ typedef struct gp_params {
   int64_t lp_async;
   /* Hub tables (vertices above deg_cta) kept across LP sub-rounds and updated by the moves, instead of
    * re-accumulated from the hubs' rows every sub-round, when the tables of all hubs of one LP call take
-   * at most this many slots (12 bytes each; runs with scores never keep them). 0 = default 2^32,
+   * at most this many slots (12 bytes each, 20 with scores). 0 = default 2^32,
    * negative = never. Never changes results. */
   int64_t hub_keep_slots;
 } gp_params;

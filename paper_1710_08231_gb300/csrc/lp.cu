@@ -161,7 +161,7 @@ struct LpProblem {
   // one batch's tables (reused by every batch; cleared by the choice scan) and partial choices
   int32_t *hub_keys;
   unsigned long long *hub_vals;
-  unsigned int *hub_qv;
+  unsigned long long *hub_qv;  // score sums (runs with scores; 64-bit: a hub row can hold 2^17+ scores)
   unsigned char *hub_part;
   unsigned int *hist;        // block_count * 256
   unsigned long long *hoff;  // block_count * 256 + 256
@@ -372,9 +372,11 @@ __device__ void hub_stale(const LpProblem &P, SubCounters &C, int h) {
   }
 }
 
-// w moves from label A to label B in hub h's table (h's neighbour moved). The hub's words and the first
-// probes of both labels are loaded together.
-__device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h, int A, int B, long long w) {
+// w (and, with scores, the entry's score q: scores are symmetric, q(u, h) = q(h, u)) moves from label A
+// to label B in hub h's table (h's neighbour moved). The hub's words and the first probes of both labels
+// are loaded together.
+__device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h, int A, int B, long long w,
+                                       long long q) {
   const int valid = *(volatile int *)&P.hub_valid[h];
   const int64_t tb = P.hub_pbase[h];
   const uint64_t cap = (uint64_t)P.hub_pcap[h];
@@ -392,6 +394,7 @@ __device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h
   for (uint64_t pr = 0;; pr++) {
     if (ka == A) {
       atomicAdd(&P.hub_vals[tb + sa], (unsigned long long)(-w));
+      if (P.hub_qv) atomicAdd(&P.hub_qv[tb + sa], (unsigned long long)(-q));
       break;
     }
     if (ka == -1 || pr >= cap) {  // (not reachable for a current table)
@@ -412,6 +415,7 @@ __device__ __noinline__ void hub_delta(const LpProblem &P, SubCounters &C, int h
     }
     if (kb == B) {
       atomicAdd(&P.hub_vals[tb + sb], (unsigned long long)w);
+      if (P.hub_qv) atomicAdd(&P.hub_qv[tb + sb], (unsigned long long)q);
       return;
     }
     if (pr >= cap) {
@@ -453,7 +457,7 @@ __device__ __forceinline__ void walk_movers_kept(const LpProblem &P, SubCounters
 #pragma unroll
     for (int x = 0; x < 2; x++) {
       if (a[x] >= 0 && act_next) act_next[a[x]] = 1;
-      if (h[x] >= 0) hub_delta(P, C, h[x], Ax[x], Bx[x], P.g.eweight(e[x]));
+      if (h[x] >= 0) hub_delta(P, C, h[x], Ax[x], Bx[x], P.g.eweight(e[x]), P.q ? (long long)P.q[e[x]] : 0);
     }
   }
 }
@@ -467,6 +471,7 @@ __device__ void hub_clear_stale(const LpProblem &P, unsigned ninv, int lb, int n
     for (int64_t x = threadIdx.x; x < cap; x += kThreads) {
       P.hub_keys[tb + x] = -1;
       P.hub_vals[tb + x] = 0;
+      if (P.hub_qv) P.hub_qv[tb + x] = 0;
     }
   }
 }
@@ -611,7 +616,10 @@ __device__ void mark_big(const LpProblem &P, SubCounters &C, unsigned nitems, in
 #pragma unroll
       for (int x = 0; x < 4; x++) {
         if (a[x] >= 0 && act_next) act_next[a[x]] = 1;
-        if (h[x] >= 0) hub_delta(P, C, h[x], A, B, P.g.eweight(e0 + 32 * x + lane));
+        if (h[x] >= 0) {
+          const int64_t e = e0 + 32 * x + lane;
+          hub_delta(P, C, h[x], A, B, P.g.eweight(e), P.q ? (long long)P.q[e] : 0);
+        }
       }
     }
   }
@@ -1453,7 +1461,7 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
           if (ks[q] == -1 || ks[q] == Ls[q]) {
             const int t = t0 + q * kThreads;
             atomicAdd(&P.hub_vals[tb + sg[q]], svals[t]);
-            if (LQ) atomicAdd(&P.hub_qv[tb + sg[q]], sq[t]);
+            if (LQ) atomicAdd(&P.hub_qv[tb + sg[q]], (unsigned long long)sq[t]);
             pend[q] = false;
           } else {
             sg[q] = sg[q] + 1 == cap ? 0 : sg[q] + 1;
@@ -1504,7 +1512,7 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
     for (int64_t base = s0; base < s1; base += kU * kThreads) {
       int L[kU];
       long long cw[kU], lwL[kU];
-      unsigned qq[kU];
+      unsigned long long qq[kU];
 #pragma unroll
       for (int u = 0; u < kU; u++) {
         const int64_t sl = base + u * kThreads + threadIdx.x;
@@ -1515,7 +1523,7 @@ __device__ __noinline__ void hub_choose_part(const LpProblem &P, unsigned h0, un
       for (int u = 0; u < kU; u++) {
         const int64_t sl = base + u * kThreads + threadIdx.x;
         cw[u] = L[u] >= 0 ? (long long)P.hub_vals[tb + sl] : 0;
-        qq[u] = (LQ && L[u] >= 0) ? P.hub_qv[tb + sl] : 0u;
+        qq[u] = (LQ && L[u] >= 0) ? P.hub_qv[tb + sl] : 0ull;
       }
       // label weights only of labels that could win (more connection than the own label)
 #pragma unroll
@@ -2829,7 +2837,7 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
       // partial choices, per-hub arrays
       const int64_t max_cap = (int64_t)hhub[3 * (size_t)j], cap_sum = (int64_t)hhub[3 * (size_t)j + 1];
       const int64_t keep_need = P.hub_dense ? (int64_t)nhub * jb.nl : cap_sum;
-      const bool keep = !lq && cfg.hub_keep_slots > 0 && keep_total + keep_need <= cfg.hub_keep_slots;
+      const bool keep = cfg.hub_keep_slots > 0 && keep_total + keep_need <= cfg.hub_keep_slots;
       if (keep) keep_total += keep_need;
       // (kept dense tables take nl slots per hub; hashed ones at most hub_cap(d))
       const int64_t slots = keep ? std::max<int64_t>(keep_need, 1)

@@ -264,6 +264,31 @@ def test_lp_cluster_hub_forms_match_oracle(gp, name, dw, dc, slots, form):
         gp.lp_set_hub_keep(0, 0)
 
 
+@pytest.mark.parametrize("form", list(HUB_FORMS))
+@pytest.mark.parametrize("name", ["rmat13", "rmat12w"])
+def test_lp_cluster_scored_hub_forms_match_oracle(gp, name, form):
+    """Runs with scores (symmetric, up to 2^20 so that a label's score sum can pass 2^32 only in 64 bits
+    on larger graphs) through every hub form: kept tables move the score sums with the weights."""
+    import torch
+    g = GRAPHS[name]
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    key = np.minimum(src, g.adj).astype(np.int64) * g.n + np.maximum(src, g.adj)
+    q = (np.vectorize(lambda x: O.mix64(int(x) ^ 0x3C3C) & 0xFFFFF, otypes=[np.int64])(key)).astype(np.int32)
+    dg = gp.DeviceGraph.from_host(g)
+    gp.lp_set_schedule(32, 32)
+    gp.lp_set_tiles(4096, 0)
+    gp.lp_set_hub_keep(*HUB_FORMS[form])
+    try:
+        lab, st = gp.lp_cluster(dg, 150, 10, 23, q=torch.from_numpy(q).cuda())
+    finally:
+        gp.lp_set_schedule(0, 0)
+        gp.lp_set_tiles(0, 0)
+        gp.lp_set_hub_keep(0, 0)
+    lab_o, _, st_o = O.lp_cluster(g, 150, 10, 23, q=q)
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    _stats_eq(st, st_o)
+
+
 @pytest.mark.parametrize("form", ["batches", "kept_stale"])
 @pytest.mark.parametrize("name,k", [("rmat13", 16), ("rmat12w", 8)])
 def test_lp_refine_and_partition_hub_forms_match_oracle(gp, name, k, form):
