@@ -395,27 +395,46 @@ __global__ void k_cut(DGraph g, const int32_t *part, unsigned long long *acc) {
   }
 }
 
-// Rows above kCutSmall entries, a CTA each: every CTA checks tiles of 256 consecutive vertices, lists the
-// long rows of its tile in shared memory and walks each with all its threads.
-__global__ void k_cut_big(DGraph g, const int32_t *part, unsigned long long *acc) {
+// Rows above kCutSmall entries are cut into items of kCutChunk entries, listed first so that every CTA
+// takes items in turn (the long rows of power-law graphs sit at small ids: tiles of vertices would leave
+// them to a few CTAs).
+constexpr int64_t kCutChunk = 4096;
+
+__global__ void k_cut_list(DGraph g, unsigned long long *items, unsigned long long cap, unsigned long long *cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = g.row_begin(v + 1) - g.row_begin(v);
+    if (d <= kCutSmall) continue;
+    const unsigned long long nch = (unsigned long long)((d + kCutChunk - 1) / kCutChunk);
+    const unsigned long long base = atomicAdd(cnt, nch);
+    for (unsigned long long c = 0; c < nch && base + c < cap; c++) items[base + c] = ((unsigned long long)v << 32) | c;
+  }
+}
+
+__global__ void k_cut_items(DGraph g, const int32_t *part, const unsigned long long *items, unsigned long long cap,
+                            const unsigned long long *cnt, unsigned long long *acc) {
   __shared__ long long sh[32];
-  __shared__ int list[256];
-  __shared__ int cnt;
+  const unsigned long long nit = min(*cnt, cap);  // (the list is sized for every row of the graph)
   long long s = 0;
-  for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < g.n; v0 += (int64_t)gridDim.x * blockDim.x) {
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    const int64_t v = v0 + threadIdx.x;
-    if (v < g.n && g.row_begin(v + 1) - g.row_begin(v) > kCutSmall) list[atomicAdd(&cnt, 1)] = (int)v;
-    __syncthreads();
-    for (int i = 0; i < cnt; i++) {
-      const int x = list[i];
-      const int px = part[x];
-      const int64_t b = g.row_begin(x), e = g.row_begin(x + 1);
-      for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x)
-        if (part[g.adj[j]] != px) s += g.eweight(j);
+  for (unsigned long long i = blockIdx.x; i < nit; i += gridDim.x) {
+    const unsigned long long it = items[i];
+    const int64_t v = (int64_t)(it >> 32);
+    const int pv = part[v];
+    const int64_t b = g.row_begin(v) + (int64_t)(it & 0xffffffffull) * kCutChunk;
+    const int64_t e = min(g.row_begin(v + 1), b + kCutChunk);
+    // four entries per thread in flight
+    for (int64_t j0 = b; j0 < e; j0 += 4 * (int64_t)blockDim.x) {
+      int a[4];
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int64_t j = j0 + x * (int64_t)blockDim.x + threadIdx.x;
+        a[x] = j < e ? __ldg(g.adj + j) : -1;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; x++) {
+        const int64_t j = j0 + x * (int64_t)blockDim.x + threadIdx.x;
+        if (a[x] >= 0 && part[a[x]] != pv) s += g.eweight(j);
+      }
     }
-    __syncthreads();
   }
   s = warp_sum64(s);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -680,8 +699,15 @@ int eval_cut_launch(const DGraph &g, const int32_t *part, int64_t k, unsigned lo
                     cudaStream_t s) {
   GP_CUDA(cudaMemsetAsync(acc_dev, 0, sizeof(unsigned long long), s));
   if (g.n > 0) {
+    Workspace ws(s);
+    unsigned long long *items, *cnt;
+    // items: at most one per kCutChunk entries plus one per row above kCutSmall
+    const unsigned long long cap = (unsigned long long)(g.m / kCutChunk + g.m / (kCutSmall + 1) + 1);
+    GP_TRY(ws.get(&items, (size_t)cap));
+    GP_TRY(ws.zeros(&cnt, 1));
     (::gp::count_launch(), k_cut<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc_dev));
-    (::gp::count_launch(), k_cut_big<<<grid_for_n(g.n), 256, 0, s>>>(g, part, acc_dev));
+    (::gp::count_launch(), k_cut_list<<<grid_for_n(g.n), 256, 0, s>>>(g, items, cap, cnt));
+    (::gp::count_launch(), k_cut_items<<<num_sms() * 8, 256, 0, s>>>(g, part, items, cap, cnt, acc_dev));
     GP_LAUNCH_CHECK();
   }
   if (bw_dev) GP_TRY(block_weights(g, part, k, bw_dev, nullptr, s));

@@ -2149,13 +2149,18 @@ __device__ bool lp_problem(const LpProblem *prob, unsigned char *dsm) {
       if (active > 0) {
         // only the first sub-round sees every label as a singleton (the second follows its moves)
         const bool direct = P.singletons && t == 0;
-        if (lb == 0 && P.has_hubs && sV.bin_count[6]) {
+        const bool hubs_now = P.has_hubs && sV.bin_count[6];
+        if (lb == 0 && hubs_now) {
           hub_prefix(P, C, sV, sm, direct);
           tick(7);
         }
-        choose_groups<EW, LQ>(P, sV, lb, nb);
-        choose_warp<EW, TB>(P, sV, lb, nb, dsm, direct);
-        choose_cta<EW, TB>(P, sV, lb, nb, dsm, sm, direct);
+        // while block 0 prepares the hub list, the other blocks take its share of the choice
+        const int clb = (hubs_now && nb > 1) ? lb - 1 : lb, cnb = (hubs_now && nb > 1) ? nb - 1 : nb;
+        if (clb >= 0) {
+          choose_groups<EW, LQ>(P, sV, clb, cnb);
+          choose_warp<EW, TB>(P, sV, clb, cnb, dsm, direct);
+          choose_cta<EW, TB>(P, sV, clb, cnb, dsm, sm, direct);
+        }
         if (!grid_sync(bar)) return false;
         tick(1);
         if (P.has_hubs && sV.bin_count[6] && direct) {
