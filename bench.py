@@ -526,6 +526,54 @@ class OraclePool:
             p.join(timeout=10)
 
 
+def levels_report(gp, dg, k, args):
+    """Level by level: one gp_lp_cluster (the partition's coarsening bound U = Lmax / 14 and 10 rounds;
+    one warm-up call per level) and one gp_contract of its labels, each timed with CUDA events, with the
+    LP call's phase times and hub work. Isolated vertices stay in (the partition strips them first)."""
+    import torch
+
+    class _Coarse:  # a library-owned coarse graph seen as a DeviceGraph
+        def __init__(self, cg):
+            self.cg, self.desc, self.n = cg, cg.desc, cg.n
+            self.adj = torch.empty(1, device="cuda")
+
+    gp.lp_set_hub_keep(args.hub_keep, 0)
+    U = max(1, gp.lmax(dg.n if dg.vw is None else int(dg.vw.sum()), k, EPS) // 14)
+    cur = dg
+    rows = []
+    for lev in range(args.levels):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(2):  # warm-up, then the profiled call
+            gp.profile_read(reset=True)
+            gp.profile_enable(True)
+            ev[0].record()
+            labels, st = gp.lp_cluster(cur, U, 10, 1000 + lev)
+            ev[1].record()
+            torch.cuda.synchronize()
+            prof = gp.profile_read(reset=True)
+            gp.profile_enable(False)
+        ev[2].record()
+        cg, _ = gp.contract(cur, labels)
+        ev[3].record()
+        torch.cuda.synchronize()
+        hub = {e["name"]: e for e in prof if e["name"] in ("lp_hub_work", "lp_hub_built")}
+        row = {"level": lev, "n": cur.n, "m_dir": int(cur.desc.m_dir), "lp_ms": ev[0].elapsed_time(ev[1]),
+               "rounds": st["rounds"], "moves": st["moves"], "lp_edges": st["edges"],
+               "contract_ms": ev[2].elapsed_time(ev[3]),
+               "hub_entries": hub.get("lp_hub_work", {}).get("edges", 0),
+               "hub_entries_accumulated": hub.get("lp_hub_built", {}).get("edges", 0),
+               "hub_tables_stale": hub.get("lp_hub_built", {}).get("items", 0),
+               "phases_ms": {e["name"][9:]: round(e["ms"], 2) for e in prof if e["name"].startswith("lp_phase")}}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        cur = _Coarse(cg)
+        if cg.n < 4000:
+            break
+    gp.lp_set_hub_keep(0, 0)
+    print(json.dumps({"levels": len(rows), "lp_ms": sum(r["lp_ms"] for r in rows),
+                      "contract_ms": sum(r["contract_ms"] for r in rows), "hub_keep": args.hub_keep}))
+
+
 def cpu_info() -> dict:
     model = None
     try:
@@ -636,6 +684,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-digest", action="store_true")
     ap.add_argument("--once", action="store_true", help="one untimed partition (for profiler launch lists)")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="per-level profile instead of the bench line: this many levels of gp_lp_cluster (the "
+                         "coarsening bound and rounds of a partition) and gp_contract, timed one by one")
+    ap.add_argument("--hub-keep", type=int, default=0,
+                    help="kept hub tables for --levels (0: default budget, -1: every hub re-accumulated every sub-round)")
     ap.add_argument("--mode", default="plain", choices=["plain", "learned"])
     ap.add_argument("--no-compare", action="store_true", help="skip the learned and batched comparisons")
     ap.add_argument("--learned-seeds", type=int, default=None,
@@ -699,6 +752,9 @@ def main():
             _, res = gp.partition(dg, k, EPS, SEED + rank, params, out=part)
             return res
 
+    if args.levels:
+        levels_report(gp, dg, k, args)
+        return
     if args.once:
         res = step()
         torch.cuda.synchronize()

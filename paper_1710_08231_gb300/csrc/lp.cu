@@ -51,12 +51,20 @@ constexpr int kWarpCapT = TB == 2 ? 512 : 256;
 template <int TB>
 constexpr int kCtaCapT = TB == 2 ? 4096 : 2048;
 template <int TB>
-constexpr int kHubChunkT = TB == 2 ? 2048 : 1024;
+constexpr int kHubChunkT = 1024;  // hub row entries per accumulation chunk
 template <int TB>
 constexpr size_t kDynSmemT = TB == 2 ? 48 * 1024 : 32 * 1024;
 constexpr int kWarpCap = kWarpCapT<2>;  // the larger capacities (bounds of the schedule)
 constexpr int kCtaCap = kCtaCapT<2>;
-constexpr int kHubChunk = 1024;         // the smaller chunk (bound of the work items)
+constexpr int kHubChunk = 1024;         // (bound of the work items)
+// Hub accumulation: a 2048-slot shared table (a 1024-entry chunk fills at most half of it). With the
+// larger class (TB = 2) the rest of the 48 KB holds two staging buffers, each the 16-byte-aligned part
+// of one chunk's adjacency (4 KB) and edge weights (up to 8 KB), filled by bulk copies (cp.async.bulk
+// with an mbarrier) one chunk ahead of the one being aggregated.
+constexpr int kHubCap = 2048;
+constexpr int kStageOff = kHubCap * 12, kStageAdj = 4096, kStageBuf = 4096 + 8192;
+static_assert(kStageOff + 2 * kStageBuf <= (int)kDynSmemT<2>, "staging buffers fit the larger class");
+static_assert(kHubCap * 16 <= (int)kDynSmemT<0> && kHubCap * 12 <= (int)kDynSmemT<1>, "hub tables fit every class");
 constexpr int kWideDeg = 1024;          // degrees above this need the larger tables
 constexpr int kSlotChunk = 8192;                      // hub table slots per choice work item
 constexpr int kContestSmall = 4096;
@@ -1327,35 +1335,213 @@ __device__ __forceinline__ unsigned search_prefix(const T *pre, unsigned lo, uns
   return lo;
 }
 
+// ------------------------------------------------------------------------------------ bulk-copy staging
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// the issuing thread's arrival, announcing `bytes` of copies that complete the phase
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for a phase of `bar` (limit_ns of %globaltimer, and at most 2^30 polls).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < (1u << 30); it++) {
+    if (mbar_test(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+// One hub chunk [beg, end) in a staging buffer: its adjacency and edge weights from the first 16-byte
+// boundary at or before `beg` up to the last one at or before `end` (a bulk copy starts and ends on
+// 16-byte boundaries and never reaches past `end`); the few entries after the last boundary are read
+// directly.
+template <int EW>
+struct HubChunk {
+  static constexpr int kEsz = EW == 2 ? 8 : 4;
+  const int32_t *sadj;
+  const unsigned char *sew;
+  int64_t beg, na, ne;  // entries beg .. beg + na - 1 (weights: + ne - 1) are staged
+  int aoff, eoff;       // position of entry beg in the buffer (entries)
+
+  __device__ __forceinline__ static void geometry(const LpProblem &P, int64_t beg, int64_t end, uintptr_t *alo,
+                                                  unsigned *ab, uintptr_t *elo, unsigned *eb) {
+    const uintptr_t a0 = (uintptr_t)(P.g.adj + beg), a1 = (uintptr_t)(P.g.adj + end);
+    *alo = a0 & ~(uintptr_t)15;
+    *ab = (unsigned)((a1 & ~(uintptr_t)15) - *alo);
+    *elo = 0;
+    *eb = 0;
+    if (EW) {
+      const uintptr_t e0 = (uintptr_t)P.g.ew + (uintptr_t)beg * kEsz, e1 = (uintptr_t)P.g.ew + (uintptr_t)end * kEsz;
+      *elo = e0 & ~(uintptr_t)15;
+      *eb = (unsigned)((e1 & ~(uintptr_t)15) - *elo);
+    }
+  }
+  // thread 0: the copies of chunk [beg, end) into buffer `buf`, completing the barrier's next phase
+  __device__ __forceinline__ static void issue(const LpProblem &P, int64_t beg, int64_t end, unsigned char *buf,
+                                               unsigned long long *bar) {
+    uintptr_t alo, elo;
+    unsigned ab, eb;
+    geometry(P, beg, end, &alo, &ab, &elo, &eb);
+    mbar_expect(bar, ab + eb);
+    if (ab) bulk_copy_g2s(buf, (const void *)alo, ab, bar);
+    if (eb) bulk_copy_g2s(buf + kStageAdj, (const void *)elo, eb, bar);
+  }
+  __device__ __forceinline__ void view(const LpProblem &P, int64_t b, int64_t end, const unsigned char *buf) {
+    uintptr_t alo, elo;
+    unsigned ab, eb;
+    geometry(P, b, end, &alo, &ab, &elo, &eb);
+    beg = b;
+    sadj = reinterpret_cast<const int32_t *>(buf);
+    sew = buf + kStageAdj;
+    const uintptr_t a0 = (uintptr_t)(P.g.adj + b);
+    aoff = (int)((a0 - alo) >> 2);
+    na = (int64_t)ab / 4 - aoff;
+    if (na < 0) na = 0;
+    ne = 0;
+    eoff = 0;
+    if (EW) {
+      const uintptr_t e0 = (uintptr_t)P.g.ew + (uintptr_t)b * kEsz;
+      eoff = (int)((e0 - elo) / kEsz);
+      ne = (int64_t)eb / kEsz - eoff;
+      if (ne < 0) ne = 0;
+    }
+  }
+  __device__ __forceinline__ int adj(const LpProblem &P, int64_t e) const {
+    const int64_t x = e - beg;
+    return x < na ? sadj[aoff + x] : __ldg(P.g.adj + e);
+  }
+  __device__ __forceinline__ long long ew(const LpProblem &P, int64_t e) const {
+    if (EW == 0) return 1;
+    const int64_t x = e - beg;
+    if (x >= ne) return load_ew<EW>(P.g.ew, e);
+    if (EW == 1) return (long long)reinterpret_cast<const int32_t *>(sew)[eoff + x];
+    return reinterpret_cast<const long long *>(sew)[eoff + x];
+  }
+};
+
 // Accumulation of batch [h0, h1): hub rows are cut into chunks of kHubChunkT<TB> entries. A block aggregates
 // its chunk's labels in a shared-memory table first and then adds one entry per distinct label to the
-// hub's table, so labels that many neighbours share cost one global atomic per chunk.
+// hub's table, so labels that many neighbours share cost one global atomic per chunk. With the larger
+// table class the block's next chunk is copied into a staging buffer (bulk copy, thread 0) while it
+// aggregates the current one. A staging wait that runs out records GP_ERR_TIMEOUT; the block then stops
+// (uniformly, after the chunk's block-wide sum), waits once more for its copies in flight and returns.
 template <int EW, int TB>
 __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned h1, int lb, int nb, Smem &sm, unsigned char *dsm) {
   constexpr bool LQ = TB == 0;
-  constexpr int kCap = kCtaCapT<TB>;
+  constexpr bool kStage = TB == 2;
+  constexpr int kCap = kHubCap;
   constexpr int kChunk = kHubChunkT<TB>;
   unsigned long long *svals = reinterpret_cast<unsigned long long *>(dsm);
   int *skeys = reinterpret_cast<int *>(dsm + kCap * 8);
   unsigned *sq = reinterpret_cast<unsigned *>(dsm + kCap * 12);
+  unsigned char *stage = dsm + kStageOff;
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ int s_to;
   for (int t = threadIdx.x; t < kCap; t += kThreads) {
     skeys[t] = -1;
     svals[t] = 0;
     if (LQ) sq[t] = 0;
   }
-  __syncthreads();
   const unsigned c_lo = P.hub_prefix[h0], c_hi = P.hub_prefix[h1];
+  // chunk c of the batch: its hub position and entries
+  auto chunk_of = [&](unsigned c, unsigned *ip, int64_t *bp, int64_t *ep) {
+    const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
+    const int v = P.bin[6][i];
+    const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
+    *ip = i;
+    *bp = rb + (int64_t)(c - P.hub_prefix[i]) * kChunk;
+    *ep = min(re, *bp + kChunk);
+  };
+  if (kStage) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar[0]);
+      mbar_init(&s_bar[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_to = 0;
+    }
+    // this thread's earlier writes of the staging area (other phases' tables) before the bulk copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (kStage && threadIdx.x == 0 && c_lo + lb < c_hi) {
+    unsigned i;
+    int64_t b, e;
+    chunk_of(c_lo + lb, &i, &b, &e);
+    HubChunk<EW>::issue(P, b, e, stage, &s_bar[0]);
+  }
+  // a chunk's staged view (the direct loads when not staging)
+  auto stage_next = [&](unsigned c, unsigned j) {
+    if (kStage && threadIdx.x == 0 && c + nb < c_hi) {
+      unsigned i;
+      int64_t b, e;
+      chunk_of(c + nb, &i, &b, &e);
+      HubChunk<EW>::issue(P, b, e, stage + ((j + 1) & 1) * kStageBuf, &s_bar[(j + 1) & 1]);
+    }
+  };
+  auto stage_wait = [&](unsigned j) -> bool {
+    if (!kStage) return true;
+    if (mbar_wait(&s_bar[j & 1], (j >> 1) & 1, 1000ull * P.wait_us)) return true;
+    s_to = 1;
+    return false;
+  };
+  // after a wait ran out (s_to, read after a block barrier): the copies in flight are waited for once
+  // more (one second at most) and the call reports the timeout
+  auto stage_abort = [&](unsigned j, unsigned c) {
+    if (threadIdx.x == 0) {
+      bool idle = mbar_wait(&s_bar[j & 1], (j >> 1) & 1, 1000000000ull);
+      if (c + nb < c_hi) idle = mbar_wait(&s_bar[(j + 1) & 1], ((j + 1) >> 1) & 1, 1000000000ull) && idle;
+      if (idle) {
+        mbar_inval(&s_bar[0]);
+        mbar_inval(&s_bar[1]);
+      }
+      atomicExch(&P.ctr->err, GP_ERR_TIMEOUT);
+    }
+  };
+  auto stage_done = [&]() {
+    if (kStage) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        mbar_inval(&s_bar[0]);
+        mbar_inval(&s_bar[1]);
+      }
+    }
+  };
   if (!LQ && P.hub_dense) {
     // few labels: a shared counter per label, flushed into the hub's dense table
     const int nl = (int)P.nl;
-    for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
-      const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
+    unsigned j = 0;
+    for (unsigned c = c_lo + lb; c < c_hi; c += nb, j++) {
+      unsigned i;
+      int64_t beg, end;
+      chunk_of(c, &i, &beg, &end);
       const int v = P.bin[6][i];
-      const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-      const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kChunk;
-      const int64_t end = min(re, beg + kChunk);
       const int64_t tb = P.hub_tb[i];
       const int L0 = P.labels[P.vbase + v];
+      stage_next(c, j);
+      const bool ok = stage_wait(j);
+      HubChunk<EW> hc;
+      if (kStage) hc.view(P, beg, end, stage + (j & 1) * kStageBuf);
       long long c0 = 0;
       for (int64_t s0 = beg; s0 < end; s0 += 4 * kThreads) {
         int64_t e[4];
@@ -1365,9 +1551,9 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           e[u] = s0 + u * kThreads + threadIdx.x;
-          in[u] = e[u] < end;
-          L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
-          w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
+          in[u] = ok && e[u] < end;
+          L[u] = in[u] ? (kStage ? hc.adj(P, e[u]) : __ldg(P.g.adj + e[u])) : 0;
+          w[u] = in[u] ? (kStage ? hc.ew(P, e[u]) : load_ew<EW>(P.g.ew, e[u])) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) L[u] = in[u] ? P.labels[L[u]] : -1;
@@ -1383,8 +1569,12 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
             atomicAdd(&svals[L[u] - P.lbase], (unsigned long long)sum);
         }
       }
-      c0 = block_sum_of(c0, sm);  // also completes the counters
-      if (P.hub_keep) c0 = 0;       // (kept tables: the choice looks the own label up)
+      c0 = block_sum_of(c0, sm);  // also completes the counters (and makes s_to visible)
+      if (kStage && s_to) {
+        stage_abort(j, c);
+        return;
+      }
+      if (P.hub_keep) c0 = 0;  // (kept tables: the choice looks the own label up)
       for (int t = threadIdx.x; t < nl; t += kThreads) {
         const unsigned long long x = svals[t];
         if (x) {
@@ -1392,20 +1582,26 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
           svals[t] = 0;
         }
       }
+      if (kStage) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // (the buffer is refilled next)
       __syncthreads();
       if (threadIdx.x == 0 && c0) atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
     }
+    stage_done();
     return;
   }
-  for (unsigned c = c_lo + lb; c < c_hi; c += nb) {
-    const unsigned i = search_prefix(P.hub_prefix, h0, h1, c);
+  unsigned j = 0;
+  for (unsigned c = c_lo + lb; c < c_hi; c += nb, j++) {
+    unsigned i;
+    int64_t beg, end;
+    chunk_of(c, &i, &beg, &end);
     const int v = P.bin[6][i];
-    const int64_t rb = P.g.row_begin(v), re = P.g.row_begin(v + 1);
-    const int64_t beg = rb + (int64_t)(c - P.hub_prefix[i]) * kChunk;
-    const int64_t end = min(re, beg + kChunk);
     const int64_t tb = P.hub_tb[i];
     const uint64_t cap = (uint64_t)(P.hub_capx[i + 1] - P.hub_capx[i]);
     const int L0 = P.labels[P.vbase + v];
+    stage_next(c, j);
+    const bool ok = stage_wait(j);
+    HubChunk<EW> hc;
+    if (kStage) hc.view(P, beg, end, stage + (j & 1) * kStageBuf);
     long long c0 = 0;
     // steps of 4 * kThreads entries: each thread takes four, loads first
     static_assert(kChunk % (4 * kThreads) == 0 && 2 * kChunk <= kCap, "a chunk fills at most half the table");
@@ -1418,9 +1614,9 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         e[u] = s0 + u * kThreads + threadIdx.x;
-        in[u] = e[u] < end;
-        L[u] = in[u] ? __ldg(P.g.adj + e[u]) : 0;
-        w[u] = in[u] ? load_ew<EW>(P.g.ew, e[u]) : 0;
+        in[u] = ok && e[u] < end;
+        L[u] = in[u] ? (kStage ? hc.adj(P, e[u]) : __ldg(P.g.adj + e[u])) : 0;
+        w[u] = in[u] ? (kStage ? hc.ew(P, e[u]) : load_ew<EW>(P.g.ew, e[u])) : 0;
         q4[u] = (LQ && in[u]) ? (unsigned)__ldg(P.q + e[u]) : 0u;
       }
 #pragma unroll
@@ -1432,7 +1628,11 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
                             3);
       }
     }
-    c0 = block_sum_of(c0, sm);  // also completes the shared table
+    c0 = block_sum_of(c0, sm);  // also completes the shared table (and makes s_to visible)
+    if (kStage && s_to) {
+      stage_abort(j, c);
+      return;
+    }
     // flush into the hub's table: each thread claims the slots of four of its labels at once (the
     // claims are in flight together), then retries the ones that met another label
     static_assert(kCap % (4 * kThreads) == 0, "the flush takes four table slots per thread per step");
@@ -1476,10 +1676,12 @@ __device__ __noinline__ void hub_accum(const LpProblem &P, unsigned h0, unsigned
         if (LQ) sq[t] = 0;
       }
     }
+    if (kStage) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // (the buffer is refilled next)
     __syncthreads();
     if (threadIdx.x == 0 && c0 && !P.hub_keep)
       atomicAdd(reinterpret_cast<unsigned long long *>(&P.hub_c0[i]), (unsigned long long)c0);
   }
+  stage_done();
 }
 
 // Choice for batch [h0, h1), part 1: the batch's tables are scanned in items of kSlotChunk slots by all
@@ -2780,9 +2982,9 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     P.nl = jb.nl;
     P.U = jb.U;
     P.hub_batch_slots = cfg.hub_batch_slots;
-    P.hub_chunk = tb == 2 ? kHubChunkT<2> : kHubChunkT<0>;
-    P.hub_chunk_shift = tb == 2 ? 11 : 10;
-    static_assert(kHubChunkT<0> == 1 << 10 && kHubChunkT<1> == 1 << 10 && kHubChunkT<2> == 1 << 11,
+    P.hub_chunk = kHubChunkT<0>;
+    P.hub_chunk_shift = 10;
+    static_assert(kHubChunkT<0> == 1 << 10 && kHubChunkT<1> == 1 << 10 && kHubChunkT<2> == 1 << 10,
                   "hub chunks are powers of two");
     P.wait_us = (unsigned)std::min<unsigned long long>(std::max<unsigned long long>(wait_limit_ns() / 1000, 0),
                                                         0xffffffffull);
@@ -2836,8 +3038,8 @@ int run_lp_multi(const LpJob *jobs, int njobs, cudaStream_t s, const LpConfig &c
     if (nhub) {
       // dense tables need nl <= 2 (deg_cta + 1) <= hub_cap(d) for every hub (the tables are sized by
       // hub_cap(d)) and the counters in the CTA's shared table
-      P.hub_dense = (!lq && jb.nl <= 2 * ((int64_t)cfg.deg_cta + 1) && jb.nl <= (tb == 2 ? kCtaCapT<2> : kCtaCapT<1>))
-                        ? 1 : 0;
+      // (the counters take the value half of the 2048-slot shared table)
+      P.hub_dense = (!lq && jb.nl <= 2 * ((int64_t)cfg.deg_cta + 1) && jb.nl <= kHubCap) ? 1 : 0;
       // tables of one batch of hubs (reused batch after batch), or of every hub when they are kept,
       // partial choices, per-hub arrays
       const int64_t max_cap = (int64_t)hhub[3 * (size_t)j], cap_sum = (int64_t)hhub[3 * (size_t)j + 1];
