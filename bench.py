@@ -256,8 +256,7 @@ def peaks():
 
 # committed ncu summaries giving DRAM bytes per k_lp launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid while the LP sources hash to the value recorded in them
-TRAFFIC_SUMMARY = {"rgg20": "profiles/k_lp_rgg20_dram_per_launch.md",
-                   "rmat26w": "profiles/k_lp_rmat_level0_dram.md"}
+TRAFFIC_SUMMARY = {"rmat26w": "profiles/k_lp_rmat_level0_dram.md"}
 LP_SOURCES = ["paper_1710_08231_gb300/csrc/lp.cu", "paper_1710_08231_gb300/csrc/lp.cuh",
               "paper_1710_08231_gb300/csrc/gp_internal.cuh"]
 

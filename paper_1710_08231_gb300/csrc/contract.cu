@@ -495,19 +495,38 @@ __global__ void k_large_heads(const unsigned long long *keys, int64_t N, int kb,
   }
 }
 
+// Sorted large-row pairs to coarse entries: every pair of a non-self run adds its weight to the run's
+// output slot (the run's rank among its row's runs, from the head scan), a warp adding once per run it
+// holds; the run's head writes the neighbour id. oval must be zero on entry.
 __global__ void k_large_write(const unsigned long long *keys, const unsigned long long *vals, int64_t N, int kb,
                               const int32_t *list, const int64_t *uidx, const int64_t *lofs, const int64_t *tstart,
                               int32_t *okey, int64_t *oval) {
   const unsigned long long mask = (1ull << kb) - 1;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-    if (uidx[j + 1] == uidx[j]) continue;  // not a head
-    const unsigned long long k = keys[j];
-    const int64_t i = (int64_t)(k >> kb);
-    long long sum = 0;
-    for (int64_t q = j; q < N && keys[q] == k; q++) sum += (long long)vals[q];
-    const int64_t out = tstart[list[i]] + (uidx[j] - uidx[lofs[i]]);
-    okey[out] = (int32_t)(k & mask);
-    oval[out] = sum;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < N; j0 += stride) {
+    const int64_t j = j0 + lane;
+    bool on = false;
+    unsigned long long out = ~0ull;
+    long long v = 0;
+    if (j < N) {
+      const unsigned long long k = keys[j];
+      const int64_t i = (int64_t)(k >> kb);
+      const int cu = (int)(k & mask), cv = list[i];
+      if (cu != cv) {
+        on = true;
+        const int64_t u1 = uidx[j + 1];
+        out = (unsigned long long)(tstart[cv] + (u1 - 1 - uidx[lofs[i]]));
+        v = (long long)vals[j];
+        if (u1 != uidx[j]) okey[out] = cu;
+      }
+    }
+    const unsigned peers = __match_any_sync(kFull, out);
+    if (on) {
+      long long sum = 0;
+      for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
+      if (lane == __ffs(peers) - 1) atomicAdd(reinterpret_cast<unsigned long long *>(&oval[out]), (unsigned long long)sum);
+    }
   }
 }
 
@@ -524,6 +543,11 @@ __global__ void k_large_sizes(const int32_t *list, const unsigned *count, const 
     sz[i] = dsum[list[i]];
 }
 
+// Compaction of the rows into the coarse CSR: a warp per row of at most kCompactLong entries; longer
+// rows (the large clusters of power-law graphs) are cut into items of kCompactLong entries that the
+// CTAs take in turn, so that no single warp copies a row of millions of entries.
+constexpr int64_t kCompactLong = 4096;
+
 __global__ void k_compact_rows(int64_t nc, const int64_t *tstart, const int64_t *rowcnt, const int64_t *off,
                                const int32_t *okey, const int64_t *oval, int32_t *adj, int64_t *ew) {
   const int lane = threadIdx.x & 31;
@@ -531,7 +555,38 @@ __global__ void k_compact_rows(int64_t nc, const int64_t *tstart, const int64_t 
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = gw; c < nc; c += nw) {
     const int64_t src = tstart[c], dst = off[c], len = rowcnt[c];
+    if (len > kCompactLong) continue;
     for (int64_t t = lane; t < len; t += 32) {
+      adj[dst + t] = okey[src + t];
+      ew[dst + t] = oval[src + t];
+    }
+  }
+}
+
+// the long rows among the large ones: (coarse id << 32) | item, at most cap items
+__global__ void k_compact_list(const int32_t *list, const unsigned *count, const int64_t *rowcnt,
+                               unsigned long long *items, unsigned long long cap, unsigned long long *nitems) {
+  const unsigned cnt = *count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int c = list[i];
+    const int64_t len = rowcnt[c];
+    if (len <= kCompactLong) continue;
+    const unsigned long long nch = (unsigned long long)((len + kCompactLong - 1) / kCompactLong);
+    const unsigned long long base = atomicAdd(nitems, nch);
+    for (unsigned long long x = 0; x < nch && base + x < cap; x++) items[base + x] = ((unsigned long long)c << 32) | x;
+  }
+}
+
+__global__ void k_compact_items(const unsigned long long *items, unsigned long long cap, const unsigned long long *nitems,
+                                const int64_t *tstart, const int64_t *rowcnt, const int64_t *off, const int32_t *okey,
+                                const int64_t *oval, int32_t *adj, int64_t *ew) {
+  const unsigned long long nit = min(*nitems, cap);
+  for (unsigned long long it = blockIdx.x; it < nit; it += gridDim.x) {
+    const int64_t c = (int64_t)(items[it] >> 32);
+    const int64_t b = (int64_t)(items[it] & 0xffffffffull) * kCompactLong;
+    const int64_t e = min(rowcnt[c], b + kCompactLong);
+    const int64_t src = tstart[c], dst = off[c];
+    for (int64_t t = b + threadIdx.x; t < e; t += blockDim.x) {
       adj[dst + t] = okey[src + t];
       ew[dst + t] = oval[src + t];
     }
@@ -737,6 +792,8 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
     GP_TRY(ws.get(&uidx, (size_t)N + 1));
     (::gp::count_launch(), k_large_heads<<<grid_n(N), 256, 0, s>>>(ks, N, kbits, lists[2], flag));
     GP_TRY(scan_excl_i64(flag, uidx, N, uidx + N, ws));
+    // (the large rows' weights are summed into zeroed slots)
+    GP_CUDA(cudaMemsetAsync(a.oval, 0, sizeof(int64_t) * (size_t)std::max<int64_t>(g.m, 1), s));
     (::gp::count_launch(), k_large_write<<<grid_n(N), 256, 0, s>>>(ks, vs, N, kbits, lists[2], uidx, lofs, tstart,
                                                                    a.okey, a.oval));
     (::gp::count_launch(), k_large_counts<<<grid_n(R), 256, 0, s>>>(lists[2], counts_dev + 2, uidx, lofs, a.rowcnt));
@@ -776,6 +833,17 @@ int contract_graph(const DGraph &g, const int32_t *labels, int64_t nl, OwnedGrap
   {
     ProfScope ps("contract_compact", s);
     (::gp::count_launch(), k_compact_rows<<<grid_n(nc * 32), 256, 0, s>>>(nc, tstart, a.rowcnt, out->off, a.okey, a.oval, out->adj, out->ew));
+    if (counts[2]) {
+      // items: at most one per kCompactLong coarse entries plus one per large row
+      const unsigned long long cap = (unsigned long long)(mc / kCompactLong + counts[2] + 1);
+      unsigned long long *items, *nitems;
+      GP_TRY(ws.get(&items, (size_t)cap));
+      GP_TRY(ws.zeros(&nitems, 1));
+      (::gp::count_launch(), k_compact_list<<<grid_n(counts[2]), 256, 0, s>>>(lists[2], counts_dev + 2, a.rowcnt, items,
+                                                                              cap, nitems));
+      (::gp::count_launch(), k_compact_items<<<num_sms() * 8, 256, 0, s>>>(items, cap, nitems, tstart, a.rowcnt,
+                                                                         out->off, a.okey, a.oval, out->adj, out->ew));
+    }
   }
   GP_LAUNCH_CHECK();
   if (profiling()) {
