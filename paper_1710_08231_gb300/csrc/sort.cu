@@ -14,7 +14,7 @@ namespace gp {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = 8;
 constexpr int64_t kSortTile = (int64_t)kSortThreads * kSortItems;
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const unsigned long long *keys, int64_t n, int shift,
