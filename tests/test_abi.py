@@ -45,3 +45,19 @@ def test_host_only_entry_points():
     p = gp.GpParams()
     lib.gp_default_params(ctypes.byref(p))
     assert (p.rounds_coarsen, p.rounds_refine, p.ip_tries, p.cluster_div) == (10, 25, 4, 14)
+
+
+def test_host_setters_validate_and_restore():
+    """Process-wide LP settings are host state: out-of-range values are refused, 0 restores a default."""
+    import paper_1710_08231_gb300 as gp
+    gp.build()
+    L = gp.lib()
+    assert L.gp_lp_set_hub_keep(0, 96) == gp.GP_ERR_INVALID_ARG
+    assert L.gp_lp_set_hub_keep(0, -1) == gp.GP_ERR_INVALID_ARG
+    assert L.gp_lp_set_hub_keep(-1, 1) == 0 and L.gp_lp_set_hub_keep(0, 0) == 0
+    assert L.gp_lp_set_tiles(-1, 0) == gp.GP_ERR_INVALID_ARG
+    assert L.gp_lp_set_tiles(4096, 16) == 0 and L.gp_lp_set_tiles(0, 0) == 0
+    assert L.gp_lp_set_schedule(-1, 0) == gp.GP_ERR_INVALID_ARG and L.gp_lp_set_schedule(0, 0) == 0
+    p = gp.GpParams()
+    L.gp_default_params(ctypes.byref(p))
+    assert (p.hub_batch_slots, p.verts_per_block, p.hub_keep_slots) == (0, 0, 0)  # defaults chosen by the library
